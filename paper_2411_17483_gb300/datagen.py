@@ -1,0 +1,107 @@
+"""Seeded synthetic workloads shaped like the paper's benchmark (Sec. V, Table I).
+
+This module holds only input generators: no part of the search method.  Both
+the CUDA path and the CPU oracle receive the very same arrays from it.  The
+paper's 17 datasets are not available, so these stand in for them:
+
+* random walks ............ cumsum of N(0, 1) steps, FP64 cumsum cast to fp32
+* noisy random walks ...... a random walk plus N(0, 0.5^2) white noise per point
+* sinusoid mixtures ....... sum of 8 sinusoids, frequency U(0, n/2) cycles per
+                            series, phase U(0, 2pi), amplitude LogNormal(0, 1),
+                            plus N(0, 0.3^2) noise (high-frequency stress)
+* perturbed members ....... a uniformly chosen dataset row plus N(0, 0.1^2)
+
+Every generator is deterministic for (seed, device): rows are produced in
+fixed chunks, each chunk drawing from its own torch.Generator seeded with
+(seed, chunk index).
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+CHUNK = 1 << 14
+
+
+def _gen(seed: int, chunk: int, device) -> torch.Generator:
+    g = torch.Generator(device=device)
+    g.manual_seed((int(seed) * 1_000_003 + int(chunk) * 7919 + 17) & ((1 << 63) - 1))
+    return g
+
+
+def random_walks(N: int, n: int, seed: int = 0, device="cpu", out: torch.Tensor | None = None,
+                 noise_sigma: float = 0.0, row0: int = 0) -> torch.Tensor:
+    """N x n fp32 random walks; rows row0..row0+N-1 of the seeded stream."""
+    device = torch.device(device)
+    if out is None:
+        out = torch.empty((N, n), dtype=torch.float32, device=device)
+    done = 0
+    while done < N:
+        r = row0 + done
+        c = r // CHUNK
+        start_in_chunk = r - c * CHUNK
+        rows = min(CHUNK - start_in_chunk, N - done)
+        g = _gen(seed, c, device)
+        steps = torch.randn((CHUNK, n), generator=g, dtype=torch.float64, device=device)
+        steps = steps[start_in_chunk:start_in_chunk + rows]
+        walk = torch.cumsum(steps, dim=1)
+        if noise_sigma > 0.0:
+            g2 = _gen(seed + 101, c, device)
+            noise = torch.randn((CHUNK, n), generator=g2, dtype=torch.float64, device=device)
+            walk = walk + noise_sigma * noise[start_in_chunk:start_in_chunk + rows]
+        out[done:done + rows] = walk.to(torch.float32)
+        done += rows
+    return out
+
+
+def mixed_walks(N: int, n: int, seed: int = 0, device="cpu") -> torch.Tensor:
+    """First half random walks, second half random walks plus N(0, 0.5^2) noise."""
+    out = torch.empty((N, n), dtype=torch.float32, device=torch.device(device))
+    h = N // 2
+    random_walks(h, n, seed, device, out=out[:h])
+    random_walks(N - h, n, seed + 1, device, out=out[h:], noise_sigma=0.5)
+    return out
+
+
+def sinusoid_mix(N: int, n: int, seed: int = 0, device="cpu", n_waves: int = 8,
+                 noise_sigma: float = 0.3) -> torch.Tensor:
+    """Sum of n_waves sinusoids with non-integer frequencies in (0, n/2) cycles
+    per series, uniform phases, LogNormal(0, 1) amplitudes, plus white noise."""
+    device = torch.device(device)
+    out = torch.empty((N, n), dtype=torch.float32, device=device)
+    t = torch.arange(n, dtype=torch.float64, device=device)
+    done = 0
+    c = 0
+    while done < N:
+        rows = min(CHUNK, N - done)
+        g = _gen(seed, c, device)
+        f = torch.rand((rows, n_waves), generator=g, dtype=torch.float64, device=device) * (n / 2)
+        ph = torch.rand((rows, n_waves), generator=g, dtype=torch.float64, device=device) * (2 * math.pi)
+        amp = torch.exp(torch.randn((rows, n_waves), generator=g, dtype=torch.float64, device=device))
+        x = torch.zeros((rows, n), dtype=torch.float64, device=device)
+        for i in range(n_waves):
+            x += amp[:, i:i + 1] * torch.sin(2 * math.pi * f[:, i:i + 1] * t[None, :] / n + ph[:, i:i + 1])
+        x += noise_sigma * torch.randn((rows, n), generator=g, dtype=torch.float64, device=device)
+        out[done:done + rows] = x.to(torch.float32)
+        done += rows
+        c += 1
+    return out
+
+
+def perturbed_members(data: torch.Tensor, count: int, seed: int = 1, sigma: float = 0.1):
+    """count queries: a uniformly drawn row of data plus N(0, sigma^2) per point
+    (before z-normalisation).  Returns (queries, source row ids)."""
+    g = _gen(seed, 0, data.device)
+    rows = torch.randint(0, data.shape[0], (count,), generator=g, device=data.device)
+    noise = torch.randn((count, data.shape[1]), generator=g, dtype=torch.float64, device=data.device)
+    q = (data[rows].to(torch.float64) + sigma * noise).to(torch.float32)
+    return q, rows
+
+
+def half_perturbed_queries(data: torch.Tensor, count: int, seed: int = 1):
+    """Half perturbed dataset members, half fresh random walks."""
+    h = count // 2
+    q1, _ = perturbed_members(data, h, seed)
+    q2 = random_walks(count - h, data.shape[1], seed=seed + 7, device=data.device)
+    return torch.cat([q1, q2], dim=0)

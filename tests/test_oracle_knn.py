@@ -1,0 +1,93 @@
+"""Pins of the oracle's exact k-NN, tie rule and GEMINI search."""
+import numpy as np
+import pytest
+
+from oracle import sofa_oracle as orc
+
+
+def rw(N, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.standard_normal((N, n)), axis=1).astype(np.float32)
+
+
+def test_sqdist_matches_numpy():
+    z, _, _ = orc.znorm(rw(300, 48, 0))
+    d = orc.sqdist(z, z[5])
+    ref = ((z.astype(np.float64) - z[5].astype(np.float64)) ** 2).sum(axis=1)
+    assert np.allclose(d, ref, rtol=1e-13)
+    assert d[5] == 0.0
+
+
+def test_query_equal_to_member_is_its_own_nn():
+    z, _, _ = orc.znorm(rw(500, 32, 1))
+    idx, dist = orc.knn(z, z[[7, 100, 499]], 1)
+    assert list(idx[:, 0]) == [7, 100, 499]
+    assert np.all(dist == 0)
+
+
+def test_tie_rule_duplicates_and_near_ties():
+    rng = np.random.default_rng(3)
+    n = 16
+    z = rng.standard_normal((40, n)).astype(np.float32)
+    q = rng.standard_normal(n).astype(np.float32)
+    # exact duplicates of a near point at rows 30, 4, 17: the lowest index first
+    near = q + np.float32(0.01)
+    for r in (30, 4, 17):
+        z[r] = near
+    idx, dist = orc.knn_full(z, q[None, :], 3)
+    assert list(idx[0]) == [4, 17, 30]
+    assert dist[0, 0] == dist[0, 1] == dist[0, 2]
+
+
+def test_tie_window_is_one_millionth_relative():
+    """Distances d0 < d1 with d1/d0 - 1 = 5e-7 form one run (index order);
+    with 5e-6 they stay in distance order."""
+    d0 = 2.0
+    for rel, expect in ((5e-7, [3, 9]), (5e-6, [9, 3])):
+        d2 = np.array([d0 ** 2, (d0 * (1 + rel)) ** 2])
+        ids = np.array([9, 3])
+        oi, od = orc.tie_order(d2, ids)
+        assert list(oi) == expect
+
+
+def test_run_is_anchored_at_first_element():
+    # 1.0, 1.0+0.8e-6 (in run), 1.0+1.6e-6 (outside: > 1e-6 from the run's first)
+    d = np.array([1.0, 1.0 + 0.8e-6, 1.0 + 1.6e-6])
+    ids = np.array([5, 1, 0])
+    oi, _ = orc.tie_order(d ** 2, ids)
+    assert list(oi) == [1, 5, 0]
+
+
+@pytest.mark.parametrize("k", [1, 5, 50])
+def test_window_knn_equals_full_sort(k):
+    rng = np.random.default_rng(k)
+    z, _, _ = orc.znorm(rw(2000, 32, 5))
+    q = z[:10].copy()
+    q += 1e-3 * rng.standard_normal(q.shape).astype(np.float32)
+    # plant near ties
+    z[1500] = z[1]
+    z[1501] = z[2] * np.float32(1 + 1e-8)
+    a = orc.knn_full(z, q, k)
+    b = orc.knn(z, q, k)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("n,alpha,k", [(8, 2, 1), (16, 4, 5), (64, 256, 50), (64, 4, 1), (16, 256, 5)])
+def test_gemini_equals_bruteforce(n, alpha, k):
+    """GEMINI (Sec. II-A) with the SFA bound returns exactly the brute-force
+    answer: a failure here means some LB exceeded a true distance."""
+    N = 1500
+    x = rw(N, n, n + alpha)
+    x[700] = x[3]                                   # a duplicate pair
+    summ = orc.learn_summary(x, l=min(8, n - 1), alpha=alpha, ratio=0.1)
+    z, _, _ = orc.znorm(x)
+    W = orc.words(z, summ)
+    qx = rw(6, n, 99)
+    qx[0] = x[3]
+    zq, _, _ = orc.znorm(qx)
+    gi, gd, refined = orc.gemini_knn(z, W, zq, summ, k)
+    bi, bd = orc.knn_full(z, zq, k)
+    assert np.array_equal(gi, bi)
+    assert np.array_equal(gd, bd)
+    assert refined.min() >= k
