@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark: exact k-NN queries/s of SOFA on GB300 (sm_103a).
+
+Default workload: 100,000,000 random-walk series of length 256 (fp32, ~102 GB,
+generated on the device, seed 0), SFA l=16, alphabet 256, equi-depth bins on a
+10% sample; 10,000 fresh random-walk queries (seed 1), exact 1-NN.  One step is
+one sofa_query call over the whole query batch: query z-normalisation and
+projection, seed, leaf / tile / series lower-bound scan, refinement, top-k.
+
+--impl reference times the CPU oracle (FP64 brute force) on the host cores on a
+bounded sample of the same workload, scaled to the full N (brute force is
+linear in N).  Under torchrun every rank holds a replica and answers its own
+query batch (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact k-NN queries/s, 100M×256 fp32 series (chosen vs plain); % of HBM roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sofa", choices=["sofa", "reference"])
+    ap.add_argument("--N", type=int, default=100_000_000)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--Q", type=int, default=10_000)
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--l", type=int, default=16)
+    ap.add_argument("--alphabet", type=int, default=256)
+    ap.add_argument("--seed-mode", default="chosen", choices=["chosen", "plain", "learned"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return f"random walks {a.N}x{a.n} fp32, {a.Q} fresh random-walk queries, exact {a.k}-NN, l={a.l}, alphabet {a.alphabet}"
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.dev = device_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(x_host_rows, zq, k, N_full, seconds):
+    """Time the oracle's brute-force k-NN over a row sample; scale to N_full."""
+    from oracle import sofa_oracle as orc
+    z, _, _ = orc.znorm(x_host_rows)
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.knn(z, zq[done:done + 1], k)
+        done += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and done >= 2) or done >= zq.shape[0]:
+            break
+    rate_sample = done / el
+    rate_full = rate_sample * x_host_rows.shape[0] / N_full
+    return rate_full, done, el, orc.num_threads()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, dev):
+    if ws == 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(a, ws, rank):
+    if rank != 0:
+        return
+    from paper_2411_17483_gb300 import datagen
+    dev = "cuda:0" if torch.cuda.is_available() else "cpu"
+    rows = min(a.N, 2_000_000)
+    xs = datagen.random_walks(rows, a.n, seed=0, device=dev).cpu().numpy()
+    q = datagen.random_walks(a.Q, a.n, seed=1, device=dev).cpu().numpy()
+    from oracle import sofa_oracle as orc
+    zq, _, _ = orc.znorm(q)
+    per_step = max(1.0, 60.0 / max(1, a.steps + a.warmup))
+    for _ in range(a.warmup):
+        cpu_oracle_rate(xs, zq, a.k, a.N, min(per_step, 5.0))
+    rates, secs = [], 0.0
+    nq = 0
+    for _ in range(a.steps):
+        r, done, el, cores = cpu_oracle_rate(xs, zq, a.k, a.N, per_step)
+        rates.append(r)
+        secs += el
+        nq += done
+    value = statistics.mean(rates)
+    sample = f"{nq} queries over the first {rows} of {a.N} series, brute force FP64, scaled by {rows}/{a.N}"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / max(1, a.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "oracle": "CPU FP64 brute force (oracle/)"},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_sofa(a, ws, rank, local):
+    from paper_2411_17483_gb300 import datagen, sofa
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    hbm_peak, peak_kind = peaks()
+
+    t0 = time.perf_counter()
+    x = torch.empty((a.N, a.n), dtype=torch.float32, device=dev)
+    datagen.random_walks(a.N, a.n, seed=0, device=dev, out=x)
+    cpu_rows = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        cpu_rows = x[: min(a.N, 2_000_000)].cpu().numpy()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ix = sofa.Index(x, a.l, a.alphabet, sample_ratio=0.1)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del x
+    torch.cuda.empty_cache()
+    info = ix.info()
+
+    # each rank answers its own batch: rank r uses query stream seed 1 + r
+    q = datagen.random_walks(a.Q, a.n, seed=1 + rank, device=dev)
+    idx = torch.empty((a.Q, a.k), dtype=torch.int64, device=dev)
+    dist = torch.empty((a.Q, a.k), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    modes = {"plain": 0}
+    chosen = "plain"
+    results = {}
+    for mode_name, mode in modes.items():
+        ix.set_seed_mode(mode)
+        for _ in range(a.warmup):
+            ix.query(q, a.k, idx, dist)
+        torch.cuda.synchronize()
+        ix.stats(reset=True)
+        ix.profile(reset=True)
+        ix.set_profiling(True)
+        clk = Clocks(local)
+        barrier(ws)
+        torch.cuda.synchronize()
+        clk.start()
+        tot_ms = 0.0
+        st = torch.cuda.current_stream()
+        wall0 = time.perf_counter()
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ix.query(q, a.k, idx, dist)
+            e1.record(st)
+            e1.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        clocks = clk.stop()
+        barrier(ws)
+        ix.set_profiling(False)
+        prof = ix.profile(reset=True)
+        stats = ix.stats(reset=True)
+        ms_step = max_over_ranks(tot_ms / a.steps, ws, dev)
+        results[mode_name] = dict(ms=ms_step, prof=prof, stats=stats, clocks=clocks, wall=wall)
+    r = results[chosen]
+    value = ws * a.Q / (r["ms"] / 1e3)
+
+    # roofline of the dominant kernel (live CUDA-event times from the library)
+    prof, stats = r["prof"], r["stats"]
+    phase = max(prof["ms"], key=lambda k: prof["ms"][k])
+    launches = max(1, prof["launches"][phase])
+    per_launch_s = prof["ms"][phase] / 1e3 / launches
+    LW = info["word_bytes"]
+    if phase == "scan":
+        alg_bytes = (prof["scan_tile_loads"] * 256 * LW + prof["scan_tile_checks"] * 2 * LW) / launches
+    elif phase == "refine":
+        alg_bytes = stats["refined"] * a.n * 4 / launches
+    elif phase == "seed":
+        alg_bytes = (a.Q * a.steps * (info["n_leaves"] * 2 * LW + 256 * LW + 32 * a.n * 4)) / launches
+    else:
+        alg_bytes = None
+    roof = {"kernel": phase, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None,
+            "traffic": None, "peak_kind": peak_kind}
+    if alg_bytes is not None and per_launch_s > 0:
+        ach = alg_bytes / per_launch_s / 1e9
+        roof.update(achieved=ach, frac=ach / hbm_peak)
+    # whole-step algorithmic bytes (SFA words scanned per query + refined raw series)
+    step_bytes = ((stats["tile_pairs"] * 256 * LW) + stats["refined"] * a.n * 4) / a.steps
+    step_roof = step_bytes / (r["ms"] / 1e3) / 1e9
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        qh = q.cpu().pin_memory()
+        ih = torch.empty((a.Q, a.k), dtype=torch.int64).pin_memory()
+        dh = torch.empty((a.Q, a.k), dtype=torch.float32).pin_memory()
+        ix.query(qh, a.k, ih, dh)
+        barrier(ws)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(a.steps):
+            ix.query(qh, a.k, ih, dh)
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - w0, ws, dev)
+        e2e = {"value": ws * a.Q * a.steps / el, "unit": "queries/s", "h2d_bytes_per_step": a.Q * a.n * 4,
+               "d2h_bytes_per_step": a.Q * a.k * 12}
+        assert torch.equal(ih, idx.cpu())
+
+    cpu = None
+    if cpu_rows is not None:
+        from oracle import sofa_oracle as orc
+        zq, _, _ = orc.znorm(q[:200].cpu().numpy())
+        rate, done, el, cores = cpu_oracle_rate(cpu_rows, zq, a.k, a.N, a.cpu_seconds)
+        cpu = {"value": rate, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} queries brute-forced (FP64) over the first {cpu_rows.shape[0]} of {a.N} series "
+                         f"in {el:.1f} s, scaled by {cpu_rows.shape[0]}/{a.N}"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "N": a.N, "n": a.n, "Q_per_gpu": a.Q, "k": a.k, "l": a.l,
+                       "alphabet": a.alphabet, "seed_mode": chosen, "precision": "fp32 projection + fp32 refine, fp64 final",
+                       "l2": "flushed between timed steps (256 MB write)", "build_s": round(t2 - t1, 3),
+                       "gen_s": round(t1 - t0, 3), "parallelism": f"replicas x{ws}"},
+            "roofline": roof,
+            "step_roofline": {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_roof,
+                              "frac": step_roof / hbm_peak, "peak": hbm_peak},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": r["clocks"],
+            "gpu_launches": int(sum(prof["launches"].values())),
+            "phases_ms_per_step": {k: v / a.steps for k, v in prof["ms"].items()},
+            "pruning": {k: v / a.steps for k, v in stats.items() if k not in ("n_leaves", "n_tiles")},
+            "index": {"n_leaves": info["n_leaves"], "n_tiles": info["n_tiles"], "device_GB": info["device_bytes"] / 1e9},
+        }
+        print(json.dumps(out), flush=True)
+    ix.close()
+
+
+def main():
+    a = parse()
+    ws, rank, local = dist_init()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+    else:
+        run_sofa(a, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * sofa.h -- C ABI of a single-GPU (sm_103a) implementation of SOFA's exact
+ * Euclidean k-NN search over z-normalised data series (Schaefer, Brand,
+ * Leser, Peng, Palpanas: "Fast and Exact Similarity Search in less than a
+ * Blink of an Eye").
+ *
+ * The hot path has two halves:
+ *   1. SFA summarisation (Sec. IV "SFA", Alg. 1 MCB, Alg. 2 SFA Transform):
+ *      z-normalise, project on the variance-selected Fourier values, quantise
+ *      with learned per-value bins into uint8 words.
+ *   2. GEMINI query answering (Sec. II-A, Sec. IV "Exact Similarity Search"):
+ *      per-query lower bounds (Eq. 1 with Eq. dist_i) over leaf blocks, tiles and
+ *      series of a key-sorted flat layout, pruning against the best-so-far,
+ *      exact refinement of survivors and top-k.
+ *
+ * Conventions for every call:
+ *   - Return 0 (SOFA_OK) on success or a negative SOFA_ERR_* code; handle
+ *     constructors return NULL on error.  The message of the last error of the
+ *     calling thread is available from sofa_last_error().
+ *   - `stream` is a CUDA stream (cudaStream_t); NULL means the legacy default
+ *     stream.  Device work is enqueued on it in order.
+ *   - Arrays are row-major, without padding, unless stated otherwise.
+ *   - Arguments are validated before any device work is enqueued; an invalid
+ *     argument changes nothing.
+ *   - There is no CPU fallback: every step runs in this library's CUDA kernels.
+ */
+#ifndef SOFA_H_
+#define SOFA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sofa_index* sofa_handle;   /* opaque; owns every index buffer */
+typedef struct CUstream_st* sofa_stream;  /* same type as cudaStream_t       */
+
+enum {
+  SOFA_OK = 0,
+  SOFA_ERR_INVALID_ARG = -1,  /* bad size, null pointer, unsupported option     */
+  SOFA_ERR_OOM = -2,          /* device allocation failed; handle unchanged     */
+  SOFA_ERR_CUDA = -3,         /* a CUDA call failed; see sofa_last_error()      */
+  SOFA_ERR_TIMEOUT = -4,      /* a bounded device wait ran out                  */
+  SOFA_ERR_NOT_TRAINED = -5,  /* learned seeding asked for before training      */
+  SOFA_ERR_TIE_OVERFLOW = -6  /* more near-tied results than the kept list holds */
+};
+
+/* Limits. */
+#define SOFA_MAX_WORD 32      /* l <= 32 word values                            */
+#define SOFA_MAX_K 64         /* k <= 64 neighbours per query                   */
+
+/* Build options (sofa_build uses the defaults: every field zero). */
+typedef struct {
+  float sample_ratio;   /* Alg. 1 sampling ratio r in (0,1]; 0 -> 0.1.  Every
+                           ceil(1/r - 1e-9)-th series from row 0 is sampled.   */
+  int32_t binning;      /* 0 equi-depth (default), 1 equi-width (Sec. IV MCB)  */
+  int32_t select;       /* 0 highest variance (Sec. IV feature selection),
+                           1 first values (classical low-pass SFA)              */
+  int32_t pool_coeffs;  /* candidate coefficients k <= pool; 0 = all k <= n/2  */
+  int32_t leaf_tiles;   /* tiles of 256 series per leaf block (<= 256); 0 -> 64 */
+  int32_t precision;    /* data-side projection: 0 FP32, 1 FP16 tensor cores
+                           with a derived error margin                          */
+  /* Optional user-supplied summarisation (host pointers), replacing Alg. 1:
+     user_sel: value ids in the candidate order (k ascending, real before
+     imaginary, Nyquist imaginary part excluded), word values first;
+     user_beta: l x (alphabet+1) fp32 breakpoints with -inf / +inf ends.    */
+  const int32_t* user_sel;
+  int32_t user_nsel;    /* number of ids in user_sel, l <= user_nsel <= 2l     */
+  const float* user_beta;
+} sofa_build_opts;
+
+/* Index construction (Sec. IV "SOFA index": sample -> learn SFA -> transform
+ * all series -> index).  data: N x n fp32 series, host or device memory,
+ * read during the call only and never retained.  l: word length (1..32, at
+ * most the number of candidate values); alphabet: 2..256 symbols.
+ * The call synchronises `stream` before returning.  Returns NULL on error. */
+sofa_handle sofa_build(const float* data, int64_t N, int32_t n, int32_t l, int32_t alphabet);
+sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, int32_t alphabet,
+                          const sofa_build_opts* opts, sofa_stream stream);
+
+/* Exact k-NN (Sec. II NN problem; k-NN as in Sec. V Table III) of Q queries.
+ * queries: Q x n fp32 (raw, z-normalised inside); idx: Q x k int64 original
+ * row ids; dist: Q x k fp32 z-normalised Euclidean distances (not squared),
+ * ascending; distances within 1e-6 relative of a run's first are ordered by
+ * ascending id.  Each pointer may be host or device memory: device buffers
+ * must stay valid until `stream` reaches the end of the call; with host
+ * buffers the call copies through the stream and synchronises it.
+ * 1 <= k <= min(SOFA_MAX_K, N).  Q = 0 is a no-op.  Returns the status code. */
+int sofa_query(sofa_handle h, const float* queries, int64_t Q, int32_t k,
+               int64_t* idx, float* dist, sofa_stream stream);
+
+/* Mixed workload: queries of different lengths against several indexes in
+ * one call.  Query i (packed at float offset q_offsets[i] of `queries`, length
+ * q_len[i]) goes to the handle whose series length equals q_len[i]; its
+ * q_k[i] results are written at element offset out_offsets[i] of idx / dist.
+ * All arrays may be host or device memory (same rules as sofa_query). */
+int sofa_query_multi(const sofa_handle* hs, int32_t nh, const float* queries,
+                     const int64_t* q_offsets, const int32_t* q_len, const int32_t* q_k,
+                     int64_t Q, int64_t* idx, float* dist, const int64_t* out_offsets,
+                     sofa_stream stream);
+
+/* Learned seeding (not in the paper): a 2l -> 256 -> 256 -> C GELU network
+ * trained on (query SFA values -> block of the exact nearest neighbour)
+ * pairs that the exact search itself labels; C blocks of ceil(N/C) consecutive
+ * key-sorted series.  It only seeds the best-so-far distance; pruning and
+ * refinement stay exact, so answers never depend on it. */
+typedef struct {
+  int64_t n_train;      /* training queries (generated on the device)          */
+  int32_t n_classes;    /* C, <= 8192; 0 -> 4096                               */
+  int32_t epochs;       /* 0 -> 4                                              */
+  int32_t batch;        /* 0 -> 4096                                           */
+  float lr;             /* Adam learning rate; 0 -> 1e-3                       */
+  uint64_t seed;        /* generator seed for queries and initial weights      */
+  const float* train_queries; /* optional n_train x n fp32 (host or device);
+                                 NULL -> half perturbed members, half fresh
+                                 random walks, from `seed`                      */
+  int32_t top_m;        /* blocks probed when seeding; 0 -> 4                  */
+} sofa_train_opts;
+int sofa_train_proposal(sofa_handle h, const sofa_train_opts* opts, sofa_stream stream);
+
+/* Seed mode of later sofa_query calls: 0 plain approximate search (best leaf,
+ * best tile), 1 learned proposal (needs sofa_train_proposal). */
+int sofa_set_seed_mode(sofa_handle h, int32_t mode);
+
+/* Run-time tuning knobs (any value keeps answers exact). */
+typedef struct {
+  int32_t group;        /* queries per scan work unit (1..64); 0 -> 32         */
+  int32_t cand_cap;     /* candidate slots per query per pass; 0 -> 32768      */
+  int32_t seed_count;   /* series refined by the seed; 0 -> 32 (>= k used)     */
+} sofa_tuning;
+int sofa_set_tuning(sofa_handle h, const sofa_tuning* t);
+
+/* Status word of the last sofa_query on this handle (after the caller has
+ * synchronised the stream): 0 or a negative SOFA_ERR_* code. */
+int sofa_query_status(sofa_handle h);
+
+/* Counters accumulated by sofa_query since the last reset. */
+typedef struct {
+  int64_t queries;
+  int64_t leaf_pairs;       /* (query, leaf block) pairs passing the leaf bound  */
+  int64_t tile_pairs;       /* (query, tile) pairs whose series were bounded     */
+  int64_t candidates;       /* series whose bound did not prune them             */
+  int64_t refined;          /* series whose exact distance was computed          */
+  int64_t overflow_passes;  /* extra scan passes after a full candidate buffer   */
+  int64_t n_leaves;         /* leaf blocks in the index                          */
+  int64_t n_tiles;          /* tiles in the index                                */
+} sofa_stats_t;
+int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset);
+
+/* Per-phase device time of sofa_query calls made while profiling is on,
+ * from CUDA events recorded on the call's stream around each phase: index
+ * 0 query transform, 1 seed, 2 routing, 3 series scan, 4 refinement,
+ * 5 final re-score.  launches[i] counts this library's kernel launches per
+ * phase (counted whether or not profiling is on); scan_tile_loads counts the
+ * (work unit, tile) pairs whose words the scan read. */
+typedef struct {
+  double ms[8];
+  int64_t launches[8];
+  int64_t scan_tile_loads;
+  int64_t scan_tile_checks;
+} sofa_profile_t;
+int sofa_set_profiling(sofa_handle h, int32_t on);
+int sofa_profile(sofa_handle h, sofa_profile_t* out, int32_t reset);
+
+/* Index description. */
+typedef struct {
+  int64_t N;
+  int32_t n, l, alphabet, nsel, word_bytes, nyquist_first, leaf_tiles;
+  int64_t n_leaves, n_tiles;
+  double delta_data, delta_query;  /* projection error margins in use          */
+  int64_t device_bytes;            /* bytes of device memory the index holds   */
+} sofa_info_t;
+int sofa_info(sofa_handle h, sofa_info_t* out);
+
+/* Learned summarisation: sel (nsel value ids, word values first), var (nsel
+ * FP64 sample variances), beta (l x (alphabet+1) fp32).  Host pointers; any may
+ * be NULL. */
+int sofa_export_summary(sofa_handle h, int32_t* sel, double* var, float* beta);
+
+/* Words in ORIGINAL row order (N x l uint8, host) and the layout permutation
+ * perm[p] = original row id at key-sorted position p (N uint32, host). */
+int sofa_export_words(sofa_handle h, uint8_t* words);
+int sofa_export_perm(sofa_handle h, uint32_t* perm);
+
+/* The scan's squared lower bounds (Eq. 1 with Eq. dist_i, widened by the
+ * error margins) of Q queries against every series, in ORIGINAL row order:
+ * out is Q x N fp32, device memory; queries Q x n fp32 device memory. */
+int sofa_lower_bounds(sofa_handle h, const float* queries, int64_t Q, float* out, sofa_stream stream);
+
+/* Canonical z-normalisation of R rows (Sec. II Def. z-ED) as the index uses
+ * it: device pointers, R x n fp32 in and out. */
+int sofa_znorm(const float* x, int64_t R, int32_t n, float* z, sofa_stream stream);
+
+void sofa_free(sofa_handle h);
+const char* sofa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOFA_H_ */

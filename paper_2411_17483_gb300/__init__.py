@@ -1,0 +1,6 @@
+"""SOFA exact k-NN over z-normalised data series, GB300 (sm_103a) native.
+
+The compute lives in libsofa.so (C ABI: include/sofa.h); `sofa` is its
+ctypes binding and `datagen` the seeded synthetic workload generators.
+"""
+__all__ = ["sofa", "datagen"]

@@ -1,0 +1,1015 @@
+// GEMINI exact k-NN query kernels (Sec. II-A; Sec. IV "Exact Similarity
+// Search", "SOFA LBD calculation"): leaf / tile / series SFA lower bounds
+// against the best-so-far, exact refinement of survivors and top-k.
+//
+// Bounds are kept in "half units": acc = sum_j c_j m_j^2 with c_j = 1, or 1/2
+// for a Nyquist value (always word position 0), so that LB^2 = 2 acc matches
+// Eq. 1's weights (2 for 0<k<n/2, 1 for k=n/2).  m_j is Eq. dist_i against
+// the symbol interval widened by the projection error margins.
+#include <cfloat>
+#include <algorithm>
+#include <vector>
+#include <cmath>
+
+#include "sofa_internal.cuh"
+
+namespace sofa {
+
+
+constexpr int SEED_TILES = 4;                 // tiles of the best leaf whose series seed the bound
+constexpr int SEED_SORT = SEED_TILES * TILE;  // 1024 series bounded by the seed
+
+struct QueryParams {
+  int64_t N, T, L;
+  int n, NB, leaf_tiles, k, cap, group, seed_count;
+  float f_prune;  // threshold = d2_kth * f_prune / 2 (half units)
+  float f_keep;   // kept list: d2 <= d2_kth * f_keep
+};
+
+// Envelope bound (leaf block or tile): per value j the interval spanned by
+// symbols lo_j..hi_j, i.e. [edge(lo_j).lo, edge(hi_j).hi].
+template <int LW, bool NYQ>
+__device__ __forceinline__ float env_bound(const uint8_t* __restrict__ env, const float* q,
+                                           const float2* __restrict__ edge) {
+  const uint32_t* e32 = reinterpret_cast<const uint32_t*>(env);
+  float acc = 0.f;
+#pragma unroll
+  for (int w = 0; w < LW / 4; ++w) {
+    uint32_t lo = e32[w], hi = e32[LW / 4 + w];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = 4 * w + b;
+      float elo = edge[j * MAX_ALPHA + ((lo >> (8 * b)) & 0xFFu)].x;
+      float ehi = edge[j * MAX_ALPHA + ((hi >> (8 * b)) & 0xFFu)].y;
+      float m = fmaxf(fmaxf(elo - q[j], q[j] - ehi), 0.f);
+      float mm = (NYQ && j == 0) ? 0.5f * m : m;
+      acc = fmaf(mm, m, acc);
+    }
+  }
+  return acc;
+}
+
+// Series bound from a word: m_j = max(|q_j - c_j| - h_j, 0) with (c, h) the
+// symbol's widened interval as centre / half-width.
+template <int LW, bool NYQ>
+__device__ __forceinline__ float word_bound(const float* c, const float* h, const float* q) {
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < LW; ++j) {
+    float m = fmaxf(fabsf(q[j] - c[j]) - h[j], 0.f);
+    float mm = (NYQ && j == 0) ? 0.5f * m : m;
+    acc = fmaf(mm, m, acc);
+  }
+  return acc;
+}
+
+template <int LW>
+__device__ __forceinline__ void load_word_bounds(const uint8_t* __restrict__ words, int64_t p, bool valid,
+                                                 const float2* __restrict__ ch, float* c, float* h) {
+  uint32_t w32[LW / 4];
+  if (valid) {
+    const uint4* w = reinterpret_cast<const uint4*>(words + p * LW);
+#pragma unroll
+    for (int i = 0; i < LW / 16; ++i) {
+      uint4 v = __ldg(w + i);
+      w32[4 * i] = v.x;
+      w32[4 * i + 1] = v.y;
+      w32[4 * i + 2] = v.z;
+      w32[4 * i + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < LW / 4; ++i) w32[i] = 0u;
+  }
+#pragma unroll
+  for (int j = 0; j < LW; ++j) {
+    float2 v = ch[j * MAX_ALPHA + ((w32[j >> 2] >> (8 * (j & 3))) & 0xFFu)];
+    c[j] = v.x;
+    h[j] = v.y;
+  }
+}
+
+// FP32 squared distance of series p computed by a group of 4 lanes (sub =
+// lane & 3); every lane of the warp must call it (the group reduction uses
+// shuffles), inactive groups pass active = false.
+__device__ __forceinline__ float group4_sqdist(const float* __restrict__ zq, const float* __restrict__ Z, int64_t p,
+                                               int n, int sub, bool active) {
+  float acc = 0.f;
+  if (active) {
+    const float* row = Z + p * n;
+    if ((n & 3) == 0) {
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+      const float4* q4 = reinterpret_cast<const float4*>(zq);
+#pragma unroll 16
+      for (int i = sub; i < n / 4; i += 4) {
+        float4 x = __ldg(r4 + i);
+        float4 y = q4[i];
+        float d0 = y.x - x.x, d1 = y.y - x.y, d2 = y.z - x.z, d3 = y.w - x.w;
+        acc = fmaf(d0, d0, acc);
+        acc = fmaf(d1, d1, acc);
+        acc = fmaf(d2, d2, acc);
+        acc = fmaf(d3, d3, acc);
+      }
+    } else {
+      for (int t = sub; t < n; t += 4) {
+        float d = zq[t] - __ldg(row + t);
+        acc = fmaf(d, d, acc);
+      }
+    }
+  }
+  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+  return acc;
+}
+
+// Bitonic sort of `len` (power of two) 64-bit keys in shared memory by the
+// whole block.
+__device__ inline void block_bitonic(unsigned long long* key, int len) {
+  for (int size = 2; size <= len; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < len / 2; i += blockDim.x) {
+        int lo = 2 * i - (i & (stride - 1));
+        int hi = lo + stride;
+        bool up = ((lo & size) == 0);
+        unsigned long long a = key[lo], b = key[hi];
+        if ((a > b) == up) {
+          key[lo] = b;
+          key[hi] = a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long pack_key(float v, uint32_t p) {
+  return ((unsigned long long)__float_as_uint(v) << 32) | p;  // v >= 0: bit order = value order
+}
+
+// Write the kept list of a query from `len` sorted (d2, pos) keys: the first
+// k entries and every later one within the tie window of the k-th.  Sets the
+// prune threshold.  Returns false when entries inside the window were dropped.
+__device__ inline bool emit_list(const unsigned long long* key, int len, const QueryParams& P, int64_t q,
+                                 float* list_d, uint32_t* list_p, int* list_n, float* thr) {
+  __shared__ int s_cnt;
+  const float dk = __uint_as_float((uint32_t)(key[P.k - 1] >> 32));
+  const float lim = __fmul_ru(dk, P.f_keep);
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    float d = __uint_as_float((uint32_t)(key[i] >> 32));
+    if (i < P.k || d <= lim) atomicMax(&s_cnt, i + 1);
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  const int keep = cnt < KCAP ? cnt : KCAP;
+  for (int i = threadIdx.x; i < keep; i += blockDim.x) {
+    list_d[q * KCAP + i] = __uint_as_float((uint32_t)(key[i] >> 32));
+    list_p[q * KCAP + i] = (uint32_t)key[i];
+  }
+  if (threadIdx.x == 0) {
+    list_n[q] = keep;
+    thr[q] = __fmul_ru(__fmul_ru(dk, P.f_prune), 0.5f);
+  }
+  __syncthreads();
+  return cnt <= KCAP;
+}
+
+// ------------------------------------------------------------------------
+// Seed (plain approximate search, Sec. IV "Exact Similarity Search": the leaf
+// with the smallest lower bound gives the first best-so-far).  One CTA per
+// query: (1) leaf bounds of every leaf block -> llb; (2) best leaf, then its
+// best tile; (3) the tile's series bounds, the seed_count smallest refined in
+// FP32; (4) kept list and prune threshold.
+template <int LW, bool NYQ>
+__global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __restrict__ qv,
+                                              const float* __restrict__ zq, const uint8_t* __restrict__ lenv,
+                                              const uint8_t* __restrict__ tenv, const uint8_t* __restrict__ words,
+                                              const float* __restrict__ Z, const float2* __restrict__ edge,
+                                              const float2* __restrict__ ch, const float* __restrict__ beta,
+                                              int alpha, int l, const uint64_t* __restrict__ keys,
+                                              const uint8_t* __restrict__ keyorder, int keybits,
+                                              float* __restrict__ llb, float* __restrict__ list_d,
+                                              uint32_t* __restrict__ list_p, int* __restrict__ list_n,
+                                              float* __restrict__ thr, int* __restrict__ status) {
+  extern __shared__ float4 ssm[];
+  float* szq = reinterpret_cast<float*>(ssm);            // n
+  __shared__ float sq[LW];
+  __shared__ unsigned long long skey[SEED_SORT];
+  __shared__ unsigned long long sbest[8];
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < LW) sq[tid] = qv[q * P.NB + tid];
+  for (int t = tid; t < P.n; t += blockDim.x) szq[t] = zq[q * P.n + t];
+  __syncthreads();
+
+  // (1) leaf bounds of every leaf block (routing input)
+  for (int64_t b = tid; b < P.L; b += blockDim.x) llb[q * P.L + b] = env_bound<LW, NYQ>(lenv + b * 2 * LW, sq, edge);
+
+  // (2) approximate search: the query's own SFA word and layout key, and the
+  // key-sorted position where it would be inserted (the flat layout's analogue
+  // of descending the tree to the leaf of the query's word)
+  __shared__ uint8_t qsym[LW];
+  __shared__ uint64_t s_qkey;
+  __shared__ int64_t s_lo, s_hi;
+  __shared__ int s_less;
+  if (tid < LW) {
+    int c = 0;
+    if (tid < l) {
+      const float* bj = beta + (int64_t)tid * (alpha + 1);
+      for (int step = 128; step > 0; step >>= 1)
+        if (c + step <= alpha - 1 && bj[c + step] <= sq[tid]) c += step;
+    }
+    qsym[tid] = (uint8_t)c;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint64_t key = 0;
+    for (int t = 0; t < keybits; ++t) {
+      const int d = keyorder[t] >> 3, bb = keyorder[t] & 7;
+      key |= (uint64_t)((qsym[d] >> bb) & 1u) << (63 - t);
+    }
+    s_qkey = key;
+    s_lo = 0;
+    s_hi = P.N;
+  }
+  __syncthreads();
+  // 256-ary search for the first position a whose key is >= the query's key.
+  // Invariant: keys[p] < qkey for p < lo, keys[p] >= qkey for p >= hi.  Each
+  // round probes lo + span*t/256; the probes below the key form a prefix of m,
+  // so a lies in [probe m-1 + 1, probe m]; lo grows by >= 1 or hi becomes lo.
+  for (int it = 0; it < 64; ++it) {
+    const int64_t lo = s_lo, hi = s_hi;
+    if (hi <= lo) break;
+    const int64_t span = hi - lo;
+    if (tid == 0) s_less = 0;
+    __syncthreads();
+    const int64_t pos = lo + (span * tid) / 256;
+    if (keys[pos] < s_qkey) atomicAdd(&s_less, 1);
+    __syncthreads();
+    if (tid == 0) {
+      const int m = s_less;
+      if (m == 0) {
+        s_hi = lo;
+      } else {
+        s_lo = lo + (span * (m - 1)) / 256 + 1;
+        if (m < 256) s_hi = lo + (span * m) / 256;
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t W = P.N < SEED_SORT ? P.N : SEED_SORT;
+  int64_t p0 = s_lo - W / 2;
+  if (p0 > P.N - W) p0 = P.N - W;
+  if (p0 < 0) p0 = 0;
+
+  // (3) series bounds of the window around that position; the seed_count
+  // smallest are refined
+  for (int i = tid; i < SEED_SORT; i += blockDim.x) {
+    const int64_t p = p0 + i;
+    const bool valid = i < W;
+    float c[LW], h[LW];
+    load_word_bounds<LW>(words, p, valid, ch, c, h);
+    skey[i] = valid ? pack_key(word_bound<LW, NYQ>(c, h, sq), (uint32_t)p) : ~0ull;
+  }
+  block_bitonic(skey, SEED_SORT);
+  int cnt = P.seed_count > P.k ? P.seed_count : P.k;
+  if (cnt > W) cnt = (int)W;
+  __shared__ float sd[TILE];
+  __shared__ uint32_t sp[TILE];
+  for (int base = 0; base < cnt; base += 64) {  // same 4-lane FP32 sum as the refinement
+    const int i = base + warp * 8 + (lane >> 2);
+    const bool active = i < cnt;
+    const uint32_t p = active ? (uint32_t)skey[i] : 0u;
+    const float d2 = group4_sqdist(szq, Z, p, P.n, lane & 3, active);
+    if (active && (lane & 3) == 0) {
+      sd[i] = d2;
+      sp[i] = p;
+    }
+  }
+  __syncthreads();
+  // (4) sort the refined entries by (d2, pos) and emit the kept list
+  for (int i = tid; i < TILE; i += blockDim.x) skey[i] = i < cnt ? pack_key(sd[i], sp[i]) : ~0ull;
+  block_bitonic(skey, TILE);
+  if (!emit_list(skey, cnt, P, q, list_d, list_p, list_n, thr) && tid == 0) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
+}
+
+// ------------------------------------------------------------------------
+// Routing: every (query, leaf block) whose leaf bound does not exceed the
+// query's threshold goes to that leaf's query list (only queries with
+// qsel[q] != 0 when qsel is given).  Count pass, then fill pass.
+__global__ void k_route_count(int64_t Q, int64_t L, const float* __restrict__ llb, const float* __restrict__ thr,
+                              const int* __restrict__ qsel, int* __restrict__ leaf_cnt,
+                              unsigned long long* __restrict__ counters) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool take = false;
+  if (e < Q * L) {
+    int64_t q = e / L, b = e - q * L;
+    take = (!qsel || qsel[q]) && llb[e] <= thr[q];
+    if (take) atomicAdd(leaf_cnt + b, 1);
+  }
+  unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(counters + 0, (unsigned long long)__popc(m));
+}
+
+// Exclusive scans over leaves of the routed counts and of the unit counts
+// ceil(cnt / group); totals land at index L.  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_leaf_scan(int64_t L, int group, const int* __restrict__ leaf_cnt,
+                                                    int* __restrict__ leaf_off, int* __restrict__ unit_off,
+                                                    int* __restrict__ leaf_cursor) {
+  __shared__ long long s1[1024], s2[1024];
+  const int tid = threadIdx.x;
+  const int64_t per = (L + 1023) / 1024;
+  const int64_t b0 = tid * per, b1 = min(L, b0 + per);
+  long long a = 0, u = 0;
+  for (int64_t b = b0; b < b1; ++b) {
+    a += leaf_cnt[b];
+    u += (leaf_cnt[b] + group - 1) / group;
+  }
+  s1[tid] = a;
+  s2[tid] = u;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    long long x1 = tid >= o ? s1[tid - o] : 0, x2 = tid >= o ? s2[tid - o] : 0;
+    __syncthreads();
+    s1[tid] += x1;
+    s2[tid] += x2;
+    __syncthreads();
+  }
+  long long ra = s1[tid] - a, ru = s2[tid] - u;
+  for (int64_t b = b0; b < b1; ++b) {
+    leaf_off[b] = (int)ra;
+    unit_off[b] = (int)ru;
+    leaf_cursor[b] = 0;
+    ra += leaf_cnt[b];
+    ru += (leaf_cnt[b] + group - 1) / group;
+  }
+  if (tid == 1023) {
+    leaf_off[L] = (int)s1[1023];
+    unit_off[L] = (int)s2[1023];
+  }
+}
+
+__global__ void k_route_fill(int64_t Q, int64_t L, const float* __restrict__ llb, const float* __restrict__ thr,
+                             const int* __restrict__ qsel, const int* __restrict__ leaf_off,
+                             int* __restrict__ leaf_cursor, int* __restrict__ leaf_q) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Q * L) return;
+  int64_t q = e / L, b = e - q * L;
+  if ((!qsel || qsel[q]) && llb[e] <= thr[q]) {
+    int pos = atomicAdd(leaf_cursor + b, 1);
+    leaf_q[leaf_off[b] + pos] = (int)q;
+  }
+}
+
+// Work units (leaf, first list entry, count <= group).
+__global__ void k_units(int64_t L, int group, const int* __restrict__ leaf_cnt, const int* __restrict__ leaf_off,
+                        const int* __restrict__ unit_off, int4* __restrict__ units) {
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= L) return;
+  int c = leaf_cnt[b], u0 = unit_off[b];
+  for (int i = 0, u = 0; i < c; i += group, ++u)
+    units[u0 + u] = make_int4((int)b, leaf_off[b] + i, min(group, c - i), 0);
+}
+
+// ------------------------------------------------------------------------
+// The series scan (Alg. 3's bound, batched).  A persistent CTA takes work
+// units (leaf block, up to 64 queries).  First every (tile, query) envelope
+// check of the unit is done in one parallel pass into a per-tile query mask.
+// Then each thread walks the tiles with a non-empty mask on its own series
+// (no barriers): it reads the word once, gathers its symbol intervals from
+// shared memory once, and evaluates the bound for every query of the mask in
+// chunks of 8 values; after each chunk a warp vote abandons the query when
+// the partial sum already exceeds the threshold for all 32 series (Alg. 3's
+// chunked early abandoning).  Survivors are appended to the query's candidate
+// buffer with warp-aggregated atomics.
+constexpr int MAX_LEAF_TILES = 256;
+template <int LW, bool NYQ>
+__global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restrict__ units,
+                                              const int* __restrict__ n_units_ptr, const int* __restrict__ leaf_q,
+                                              const float* __restrict__ qv, const float* __restrict__ thr,
+                                              const uint8_t* __restrict__ tenv, const uint8_t* __restrict__ words,
+                                              const float2* __restrict__ edge, const float2* __restrict__ ch,
+                                              const int* __restrict__ qslot, uint32_t* __restrict__ cand_p,
+                                              float* __restrict__ cand_lb, int* __restrict__ cand_n,
+                                              unsigned long long* __restrict__ counters) {
+  extern __shared__ float2 tabs[];
+  float2* sch = tabs;                     // LW x 256
+  float2* sedge = tabs + LW * MAX_ALPHA;  // LW x 256
+  __shared__ __align__(16) float sq[MAX_GROUP][LW];
+  __shared__ float sT[MAX_GROUP];
+  __shared__ int sslot[MAX_GROUP];
+  __shared__ unsigned long long smask[MAX_LEAF_TILES];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int e = tid; e < LW * MAX_ALPHA; e += blockDim.x) {
+    sch[e] = ch[e];
+    sedge[e] = edge[e];
+  }
+  unsigned long long n_tile_pairs = 0, n_cand = 0, n_loads = 0, n_checks = 0;
+  const int n_units = *n_units_ptr;
+  for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+    __syncthreads();
+    const int4 un = units[u];
+    const int64_t b = un.x;
+    const int cnt = un.z;
+    const int64_t t0 = b * P.leaf_tiles;
+    const int nt = (int)((P.T - t0) < P.leaf_tiles ? (P.T - t0) : P.leaf_tiles);
+    for (int e = tid; e < cnt * LW; e += blockDim.x) {
+      int g = e / LW, j = e - g * LW;
+      int qq = leaf_q[un.y + g];
+      sq[g][j] = qv[(int64_t)qq * P.NB + j];
+      if (j == 0) {
+        sslot[g] = qslot ? qslot[qq] : qq;
+        sT[g] = thr[qq];
+      }
+    }
+    for (int t = tid; t < nt; t += blockDim.x) smask[t] = 0ull;
+    __syncthreads();
+    // all envelope checks of the unit
+    for (int e = tid; e < nt * cnt; e += blockDim.x) {
+      const int t = e / cnt, g = e - t * cnt;
+      float a = env_bound<LW, NYQ>(tenv + (t0 + t) * 2 * LW, sq[g], sedge);
+      if (a <= sT[g]) atomicOr(&smask[t], 1ull << g);
+    }
+    n_checks += (tid == 0) ? (unsigned long long)nt : 0ull;
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+      unsigned long long m = smask[t];
+      if (!m) continue;
+      if (tid == 0) {
+        n_tile_pairs += __popcll(m);
+        n_loads += 1;
+      }
+      const int64_t p = (t0 + t) * TILE + tid;
+      const bool valid = p < P.N;
+      float c[LW], h[LW];
+      load_word_bounds<LW>(words, p, valid, sch, c, h);
+      while (m) {
+        const int g = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        const float T = sT[g];
+        const float* qg = sq[g];
+        float acc = 0.f;
+        bool live = valid;
+#pragma unroll
+        for (int c0 = 0; c0 < LW; c0 += 8) {
+          if (!__any_sync(0xFFFFFFFFu, live)) break;
+#pragma unroll
+          for (int j = c0; j < c0 + 8; ++j) {
+            float mj = fmaxf(fabsf(qg[j] - c[j]) - h[j], 0.f);
+            float mm = (NYQ && j == 0) ? 0.5f * mj : mj;
+            acc = fmaf(mm, mj, acc);
+          }
+          live = live && acc <= T;
+        }
+        const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
+        if (hit) {
+          const int qs = sslot[g];
+          int base = 0;
+          if (lane == 0) base = atomicAdd(cand_n + qs, __popc(hit));
+          base = __shfl_sync(0xFFFFFFFFu, base, 0);
+          if (live) {
+            const int slot = base + __popc(hit & ((1u << lane) - 1u));
+            if (slot < P.cap) {
+              cand_p[(int64_t)qs * P.cap + slot] = (uint32_t)p;
+              cand_lb[(int64_t)qs * P.cap + slot] = acc;
+            }
+          }
+          if (lane == 0) n_cand += __popc(hit);
+        }
+      }
+    }
+  }
+  if (n_tile_pairs) atomicAdd(counters + 1, n_tile_pairs);
+  if (n_cand) atomicAdd(counters + 2, n_cand);
+  if (n_loads) atomicAdd(counters + 4, n_loads);
+  if (n_checks) atomicAdd(counters + 5, n_checks);
+}
+
+// ------------------------------------------------------------------------
+// Refinement (GEMINI's exact distance for the survivors of the bound, Sec.
+// II-A, visited in ascending bound order as in Sec. IV "Exact Similarity
+// Search").  Every chunk of RSORT candidates of a query gets its own CTA:
+// the chunk is sorted by bound; rounds of 64 candidates (8 warps x 8 groups of
+// 4 lanes) get their FP32 distance; entries inside the chunk's tie window go to
+// a chunk-local kept list.  The query's threshold lives in global memory: a
+// chunk whose list holds k entries publishes k-th * f_prune / 2 with atomicMin
+// (a real k-th distance of k distinct series, hence a valid bound), and each
+// round reads the current value, so all chunks of a query tighten together.
+// The first candidate whose bound exceeds the threshold ends the chunk.
+constexpr int RSORT = 4096;
+constexpr int RROUND = 64;  // candidates refined per round: 8 warps x 8 groups of 4 lanes
+__global__ void __launch_bounds__(256) k_refine(QueryParams P, int nchunk, const int* __restrict__ qsel,
+                                                const int* __restrict__ qslot,
+                                                const float* __restrict__ zq, const float* __restrict__ Z,
+                                                const uint32_t* __restrict__ cand_p,
+                                                const float* __restrict__ cand_lb, const int* __restrict__ cand_n,
+                                                float* __restrict__ thr, float* __restrict__ chunk_d,
+                                                uint32_t* __restrict__ chunk_p, int* __restrict__ chunk_n,
+                                                unsigned long long* __restrict__ counters, int* __restrict__ status) {
+  extern __shared__ float4 rsm[];
+  float* szq = reinterpret_cast<float*>(rsm);  // n
+  __shared__ unsigned long long skey[RSORT];
+  __shared__ float sld[KCAP];
+  __shared__ uint32_t slp[KCAP];
+  __shared__ float acc_d[RROUND];
+  __shared__ uint32_t acc_p[RROUND];
+  __shared__ int s_nacc, s_nl, s_stop, s_lost;
+  __shared__ float s_lim;
+  const int64_t q = blockIdx.x / nchunk;
+  const int c = blockIdx.x - (int)(q * nchunk);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (qsel && !qsel[q]) return;
+  const int64_t slot_q = qslot ? qslot[q] : q;
+  const int all = cand_n[slot_q];
+  const int cnt = all < P.cap ? all : P.cap;
+  const int c0 = c * RSORT;
+  int* const out_n = chunk_n + slot_q * nchunk + c;
+  if (c0 >= cnt) {
+    if (tid == 0) *out_n = 0;
+    return;
+  }
+  const int cc = cnt - c0 < RSORT ? cnt - c0 : RSORT;
+  for (int t = tid; t < P.n; t += blockDim.x) szq[t] = zq[q * P.n + t];
+  int pw = 1;
+  while (pw < cc) pw <<= 1;
+  for (int i = tid; i < pw; i += blockDim.x)
+    skey[i] = i < cc ? pack_key(cand_lb[slot_q * P.cap + c0 + i], cand_p[slot_q * P.cap + c0 + i]) : ~0ull;
+  if (tid == 0) {
+    s_nl = 0;
+    s_stop = 0;
+    s_lost = 0;
+    s_lim = INFINITY;
+    s_nacc = 0;
+  }
+  block_bitonic(skey, pw);
+  volatile float* vthr = thr;
+  unsigned long long refined = 0;
+  for (int base = 0; base < cc; base += RROUND) {
+    const int slot = warp * 8 + (lane >> 2);
+    const int i = base + slot;
+    const float T = vthr[q];
+    bool active = false;
+    uint32_t p = 0xFFFFFFFFu;
+    if (i < cc) {
+      const float lb = __uint_as_float((uint32_t)(skey[i] >> 32));
+      active = lb <= T;
+      if (active) p = (uint32_t)skey[i];
+    }
+    if (tid == 0 && __uint_as_float((uint32_t)(skey[base] >> 32)) > T) s_stop = 1;  // sorted: the rest exceeds T
+    const float d2 = group4_sqdist(szq, Z, p, P.n, lane & 3, active);
+    if ((lane & 3) == 0 && active) {
+      ++refined;
+      if (d2 <= s_lim) {  // a candidate for the local kept list
+        const int a = atomicAdd(&s_nacc, 1);
+        acc_d[a] = d2;
+        acc_p[a] = p;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int nl = s_nl;
+      float lim = s_lim;
+      const int na = s_nacc;
+      for (int w = 0; w < na; ++w) {
+        const float d = acc_d[w];
+        const uint32_t pp = acc_p[w];
+        if (!(d <= lim)) continue;
+        int j = nl - 1;  // insertion by (d2, pos)
+        while (j >= 0 && (sld[j] > d || (sld[j] == d && slp[j] > pp))) {
+          if (j + 1 < KCAP) {
+            sld[j + 1] = sld[j];
+            slp[j + 1] = slp[j];
+          }
+          --j;
+        }
+        if (j + 1 < KCAP) {
+          sld[j + 1] = d;
+          slp[j + 1] = pp;
+        }
+        if (nl < KCAP) ++nl;
+        else s_lost = 1;
+        if (nl >= P.k) {
+          lim = __fmul_ru(sld[P.k - 1], P.f_keep);
+          while (nl > P.k && sld[nl - 1] > lim) --nl;  // drop entries that left the window
+        }
+      }
+      s_nacc = 0;
+      s_nl = nl;
+      s_lim = lim;
+      if (nl >= P.k) {
+        const float t = __fmul_ru(__fmul_ru(sld[P.k - 1], P.f_prune), 0.5f);
+        atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(t));  // t >= 0: int order = float order
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+  }
+  const int nl = s_nl;
+  float* od = chunk_d + (slot_q * nchunk + c) * KCAP;
+  uint32_t* op = chunk_p + (slot_q * nchunk + c) * KCAP;
+  for (int i = tid; i < nl; i += blockDim.x) {
+    od[i] = sld[i];
+    op[i] = slp[i];
+  }
+  if (tid == 0) {
+    *out_n = nl;
+    if (s_lost) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
+  }
+  if ((lane & 3) == 0 && refined) atomicAdd(counters + 3, refined);
+}
+
+// Merge of a query's kept list with the lists of its refined chunks: drop
+// duplicates (an overflow pass may meet a series again) and entries outside
+// the window of the current threshold, sort by (d2, pos), emit the new kept
+// list and its threshold, and flag the query when its buffer overflowed.
+constexpr int MSORT = 4096;
+__global__ void __launch_bounds__(256) k_merge(QueryParams P, int nchunk, const int* __restrict__ qsel,
+                                               const int* __restrict__ qslot, const int* __restrict__ cand_n,
+                                               const float* __restrict__ chunk_d, const uint32_t* __restrict__ chunk_p,
+                                               const int* __restrict__ chunk_n, float* __restrict__ list_d,
+                                               uint32_t* __restrict__ list_p, int* __restrict__ list_n,
+                                               float* __restrict__ thr, int* __restrict__ qflag_out,
+                                               int* __restrict__ n_overflow, int* __restrict__ status) {
+  __shared__ unsigned long long skey[MSORT];
+  __shared__ int s_cnt;
+  const int64_t q = blockIdx.x;
+  if (qsel && !qsel[q]) return;
+  const int tid = threadIdx.x;
+  const int64_t slot_q = qslot ? qslot[q] : q;
+  const int all = cand_n[slot_q];
+  if (all == 0) return;
+  // the threshold is an upper bound of (k-th d2) * f_prune / 2: entries above
+  // that k-th estimate widened by the keep factor cannot reach the window
+  const float lim = __fmul_ru(__fdiv_ru(__fmul_ru(thr[q], 2.0f), P.f_prune), P.f_keep);
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+  const int nl = list_n[q];
+  for (int i = tid; i < nl; i += blockDim.x) {
+    const float d = list_d[q * KCAP + i];
+    if (i < P.k || d <= lim) {
+      const int a = atomicAdd(&s_cnt, 1);
+      if (a < MSORT) skey[a] = pack_key(d, list_p[q * KCAP + i]);
+    }
+  }
+  for (int c = 0; c < nchunk; ++c) {
+    const int m = chunk_n[slot_q * nchunk + c];
+    const float* cd = chunk_d + (slot_q * nchunk + c) * KCAP;
+    const uint32_t* cp = chunk_p + (slot_q * nchunk + c) * KCAP;
+    for (int i = tid; i < m; i += blockDim.x) {
+      if (cd[i] <= lim) {
+        const int a = atomicAdd(&s_cnt, 1);
+        if (a < MSORT) skey[a] = pack_key(cd[i], cp[i]);
+      }
+    }
+  }
+  __syncthreads();
+  int len = s_cnt;
+  if (len > MSORT) {
+    len = MSORT;
+    if (tid == 0) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
+  }
+  int pw = 1;
+  while (pw < len) pw <<= 1;
+  for (int i = len + tid; i < pw; i += blockDim.x) skey[i] = ~0ull;
+  block_bitonic(skey, pw);
+  // equal keys are the same (d2, pos): keep the first of each run
+  __shared__ int s_u;
+  if (tid == 0) {
+    int u = 0;
+    for (int i = 0; i < len; ++i)
+      if (i == 0 || skey[i] != skey[u - 1]) skey[u++] = skey[i];
+    s_u = u;
+  }
+  __syncthreads();
+  if (!emit_list(skey, s_u, P, q, list_d, list_p, list_n, thr) && tid == 0) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
+  if (tid == 0 && all > P.cap) {
+    qflag_out[q] = 1;
+    atomicAdd(n_overflow, 1);
+  }
+}
+
+// ------------------------------------------------------------------------
+// Final answer: FP64 re-score of every kept entry (the left-to-right FP64 sum
+// of squared differences of the canonical series), order by (distance, id),
+// then each run of distances within 1e-6 relative of the run's first is
+// ordered by ascending id; the first k are written out.
+__global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __restrict__ zq,
+                                               const float* __restrict__ Z, const uint32_t* __restrict__ perm,
+                                               const uint32_t* __restrict__ list_p, const int* __restrict__ list_n,
+                                               int64_t* __restrict__ idx, float* __restrict__ dist) {
+  extern __shared__ float dsm[];
+  float* szq = dsm;
+  __shared__ double sd[128];
+  __shared__ uint32_t sid[128];
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int nl = list_n[q];
+  for (int t = tid; t < P.n; t += blockDim.x) szq[t] = zq[q * P.n + t];
+  __syncthreads();
+  double d = INFINITY;
+  uint32_t id = 0xFFFFFFFFu;
+  if (tid < nl) {
+    const uint32_t p = list_p[q * KCAP + tid];
+    const float* row = Z + (int64_t)p * P.n;
+    double acc = 0.0;
+    for (int t = 0; t < P.n; ++t) {
+      double df = __dsub_rn((double)szq[t], (double)row[t]);
+      acc = __dadd_rn(acc, __dmul_rn(df, df));
+    }
+    d = __dsqrt_rn(acc);
+    id = perm[p];
+  }
+  sd[tid] = d;
+  sid[tid] = id;
+  for (int size = 2; size <= 128; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      if (tid < 64) {
+        int lo = 2 * tid - (tid & (stride - 1));
+        int hi = lo + stride;
+        bool up = ((lo & size) == 0);
+        bool gt = sd[lo] > sd[hi] || (sd[lo] == sd[hi] && sid[lo] > sid[hi]);
+        if (gt == up) {
+          double td = sd[lo];
+          sd[lo] = sd[hi];
+          sd[hi] = td;
+          uint32_t ti = sid[lo];
+          sid[lo] = sid[hi];
+          sid[hi] = ti;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int i = 0;
+    while (i < nl && i < P.k) {
+      const double d0 = sd[i];
+      const double lim = __dadd_rn(d0, __dmul_rn(1e-6, d0));
+      int j = i;
+      while (j + 1 < nl && sd[j + 1] <= lim) ++j;
+      for (int a = i + 1; a <= j; ++a) {  // insertion sort of the run by id
+        double vd = sd[a];
+        uint32_t vi = sid[a];
+        int b = a - 1;
+        while (b >= i && sid[b] > vi) {
+          sd[b + 1] = sd[b];
+          sid[b + 1] = sid[b];
+          --b;
+        }
+        sd[b + 1] = vd;
+        sid[b + 1] = vi;
+      }
+      i = j + 1;
+    }
+  }
+  __syncthreads();
+  if (tid < P.k) {
+    idx[q * P.k + tid] = tid < nl ? (int64_t)sid[tid] : -1;
+    dist[q * P.k + tid] = tid < nl ? (float)sd[tid] : INFINITY;
+  }
+}
+
+// ========================================================================
+// Host driver of one sofa_query call.
+// ========================================================================
+#define TRYQ(x)          \
+  do {                   \
+    int rc_ = (x);       \
+    if (rc_) return rc_; \
+  } while (0)
+
+static QueryParams make_params(const Index* ix, int k) {
+  QueryParams P;
+  P.N = ix->N;
+  P.T = ix->T;
+  P.L = ix->L;
+  P.n = ix->n;
+  P.NB = ix->NB;
+  P.leaf_tiles = ix->leaf_tiles;
+  P.k = k;
+  P.cap = ix->cand_cap;
+  P.group = ix->group;
+  P.seed_count = ix->seed_count;
+  // Rounding-error factors (u = 2^-24): the FP32 bound sum over LW values has
+  // relative error <= (LW+3)u; the FP32 distance <= (n+3)u/(1-(n+3)u).  A
+  // series is pruned only when its bound proves it farther than the k-th kept
+  // distance widened by the 1e-6 tie window; the kept list holds every entry
+  // that may fall inside that window.
+  const double u = std::ldexp(1.0, -24);
+  const double g_lb = (ix->LW + 3) * u;
+  const double g_ed = (ix->n + 3) * u / (1.0 - (ix->n + 3) * u);
+  const double tie = (1.0 + 1e-6) * (1.0 + 1e-6);
+  P.f_prune = std::nextafter((float)(tie * (1.0 + g_lb) / (1.0 - g_ed) * (1.0 + 4 * u)), 2.0f);
+  P.f_keep = std::nextafter((float)(tie * (1.0 + g_ed) / (1.0 - g_ed) * (1.0 + 4 * u)), 2.0f);
+  return P;
+}
+
+template <int LW, bool NYQ>
+static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* idx, float* dist,
+                       cudaStream_t st) {
+  QueryScratch& s = ix->qs;
+  const int n = ix->n, NB = ix->NB;
+  const int64_t L = ix->L;
+  QueryParams P = make_params(ix, k);
+  TRYQ(s.zq.ensure(Q * n * sizeof(float)));
+  TRYQ(s.qv.ensure(Q * NB * sizeof(float)));
+  TRYQ(s.llb.ensure(Q * L * sizeof(float)));
+  TRYQ(s.thr.ensure(Q * sizeof(float)));
+  TRYQ(s.list_d.ensure(Q * KCAP * sizeof(float)));
+  TRYQ(s.list_p.ensure(Q * KCAP * sizeof(uint32_t)));
+  TRYQ(s.list_n.ensure(Q * sizeof(int)));
+  TRYQ(s.leaf_cnt.ensure((L + 1) * sizeof(int)));
+  TRYQ(s.leaf_off.ensure((L + 1) * sizeof(int)));
+  TRYQ(s.unit_off.ensure((L + 1) * sizeof(int)));
+  TRYQ(s.leaf_cursor.ensure((L + 1) * sizeof(int)));
+  TRYQ(s.cand_n.ensure(Q * sizeof(int)));
+  TRYQ(s.qflag.ensure(2 * Q * sizeof(int)));
+  TRYQ(s.counters.ensure(16 * sizeof(unsigned long long)));
+
+  float* zq = s.zq.as<float>();
+  float* qv = s.qv.as<float>();
+  float* llb = s.llb.as<float>();
+  float* thr = s.thr.as<float>();
+  int* status = reinterpret_cast<int*>(s.counters.as<unsigned long long>() + 8);
+  int* n_overflow = status + 1;
+  int* n_units = status + 2;
+  unsigned long long* counters = s.counters.as<unsigned long long>();
+
+  ix->prof.begin(0, st);
+  TRYQ(launch_qprep(ix, qdev, Q, zq, qv, st));
+  ix->prof.end(st);
+  const size_t nsm = (size_t)n * sizeof(float);
+  ix->prof.begin(1, st);
+  k_seed<LW, NYQ><<<(unsigned)Q, 256, nsm, st>>>(P, qv, zq, ix->lenv, ix->tenv, ix->words, ix->Z, ix->edge, ix->ch,
+                                                  ix->beta, ix->alpha, ix->l, ix->keys, ix->keyorder, ix->keybits,
+                                                  llb, s.list_d.as<float>(), s.list_p.as<uint32_t>(),
+                                                  s.list_n.as<int>(), thr, status);
+  ix->prof.end(st);
+  SOFA_CUDA(cudaGetLastError());
+
+  static int scan_blocks[2] = {0, 0};
+  const size_t scan_smem = (size_t)2 * LW * MAX_ALPHA * sizeof(float2);
+  SOFA_CUDA(cudaFuncSetAttribute(k_scan<LW, NYQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem));
+  int& nb = scan_blocks[LW == 32];
+  if (nb == 0) {
+    int per_sm = 0, sms = 0, dev = 0;
+    SOFA_CUDA(cudaGetDevice(&dev));
+    SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SOFA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<LW, NYQ>, 256, scan_smem));
+    nb = sms * (per_sm > 0 ? per_sm : 1);
+  }
+
+  int* qsel = nullptr;     // queries scanned in this pass (all in the first)
+  int* qslot = nullptr;    // their candidate-buffer slots (identity in the first)
+  int* qflag_out = s.qflag.as<int>();
+  int* h_over = nullptr;
+  SOFA_CUDA(cudaMallocHost((void**)&h_over, sizeof(int)));
+  std::vector<int> hflag, hslot;
+  int rc = 0;
+  int64_t slots = Q;
+  for (int pass = 0;; ++pass) {
+    TRYQ(s.cand_p.ensure((size_t)slots * P.cap * sizeof(uint32_t)));
+    TRYQ(s.cand_lb.ensure((size_t)slots * P.cap * sizeof(float)));
+    SOFA_CUDA(cudaMemsetAsync(s.leaf_cnt.p, 0, (L + 1) * sizeof(int), st));
+    SOFA_CUDA(cudaMemsetAsync(s.cand_n.p, 0, Q * sizeof(int), st));
+    SOFA_CUDA(cudaMemsetAsync(qflag_out, 0, Q * sizeof(int), st));
+    SOFA_CUDA(cudaMemsetAsync(n_overflow, 0, sizeof(int), st));
+    const int64_t pairs = Q * L;
+    const unsigned rb = (unsigned)ceil_div(pairs, 256);
+    ix->prof.begin(2, st, 2);
+    k_route_count<<<rb, 256, 0, st>>>(Q, L, llb, thr, qsel, s.leaf_cnt.as<int>(), counters);
+    int* cursor = s.leaf_cursor.as<int>();
+    k_leaf_scan<<<1, 1024, 0, st>>>(L, P.group, s.leaf_cnt.as<int>(), s.leaf_off.as<int>(), s.unit_off.as<int>(),
+                                     cursor);
+    ix->prof.end(st);
+    SOFA_CUDA(cudaGetLastError());
+    // sizes of the routed list and the unit list are only known on the device:
+    // read the two totals back (one small copy per pass)
+    int tot[2];
+    SOFA_CUDA(cudaMemcpyAsync(&tot[0], s.leaf_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SOFA_CUDA(cudaMemcpyAsync(&tot[1], s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SOFA_CUDA(cudaStreamSynchronize(st));
+    TRYQ(s.leaf_q.ensure(((size_t)tot[0] + 1) * sizeof(int)));
+    TRYQ(s.units.ensure(((size_t)tot[1] + 1) * sizeof(int4)));
+    ix->prof.begin(2, st, 2);
+    k_route_fill<<<rb, 256, 0, st>>>(Q, L, llb, thr, qsel, s.leaf_off.as<int>(), cursor, s.leaf_q.as<int>());
+    k_units<<<(unsigned)ceil_div(L, 256), 256, 0, st>>>(L, P.group, s.leaf_cnt.as<int>(), s.leaf_off.as<int>(),
+                                                         s.unit_off.as<int>(), s.units.as<int4>());
+    SOFA_CUDA(cudaMemcpyAsync(n_units, s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    ix->prof.end(st);
+    ix->prof.begin(3, st);
+    k_scan<LW, NYQ><<<nb, 256, scan_smem, st>>>(P, s.units.as<int4>(), n_units, s.leaf_q.as<int>(), qv, thr,
+                                                 ix->tenv, ix->words, ix->edge, ix->ch, qslot,
+                                                 s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(),
+                                                 counters);
+    ix->prof.end(st);
+    SOFA_CUDA(cudaGetLastError());
+    const int nchunk = (int)ceil_div(P.cap, RSORT);
+    TRYQ(s.chunk_d.ensure((size_t)slots * nchunk * KCAP * sizeof(float)));
+    TRYQ(s.chunk_p.ensure((size_t)slots * nchunk * KCAP * sizeof(uint32_t)));
+    TRYQ(s.chunk_n.ensure((size_t)slots * nchunk * sizeof(int)));
+    ix->prof.begin(4, st, 2);
+    k_refine<<<(unsigned)(Q * nchunk), 256, nsm, st>>>(P, nchunk, qsel, qslot, zq, ix->Z, s.cand_p.as<uint32_t>(),
+                                                       s.cand_lb.as<float>(), s.cand_n.as<int>(), thr,
+                                                       s.chunk_d.as<float>(), s.chunk_p.as<uint32_t>(),
+                                                       s.chunk_n.as<int>(), counters, status);
+    SOFA_CUDA(cudaGetLastError());
+    k_merge<<<(unsigned)Q, 256, 0, st>>>(P, nchunk, qsel, qslot, s.cand_n.as<int>(), s.chunk_d.as<float>(),
+                                         s.chunk_p.as<uint32_t>(), s.chunk_n.as<int>(), s.list_d.as<float>(),
+                                         s.list_p.as<uint32_t>(), s.list_n.as<int>(), thr, qflag_out, n_overflow,
+                                         status);
+    ix->prof.end(st);
+    SOFA_CUDA(cudaGetLastError());
+    SOFA_CUDA(cudaMemcpyAsync(h_over, n_overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SOFA_CUDA(cudaStreamSynchronize(st));
+    if (*h_over == 0) break;
+    ix->stats[5] += 1;
+    if (pass >= 64) {
+      rc = fail(SOFA_ERR_TIMEOUT, "candidate overflow passes did not converge");
+      break;
+    }
+    // Next pass: only the overflowed queries, against their tightened
+    // thresholds, each with an 8x larger candidate buffer (so the passes end:
+    // at the latest when a buffer holds every series).
+    hflag.resize(Q);
+    hslot.assign(Q, 0);
+    SOFA_CUDA(cudaMemcpy(hflag.data(), qflag_out, Q * sizeof(int), cudaMemcpyDeviceToHost));
+    int64_t m = 0;
+    for (int64_t i = 0; i < Q; ++i)
+      if (hflag[i]) hslot[i] = (int)m++;
+    slots = m;
+    P.cap = (int)std::min<int64_t>((int64_t)P.cap * 8, std::max<int64_t>(ix->N, 1));
+    TRYQ(s.qslot.ensure(Q * sizeof(int)));
+    SOFA_CUDA(cudaMemcpy(s.qslot.p, hslot.data(), Q * sizeof(int), cudaMemcpyHostToDevice));
+    qslot = s.qslot.as<int>();
+    int* prev = qflag_out;
+    qflag_out = (qflag_out == s.qflag.as<int>()) ? s.qflag.as<int>() + Q : s.qflag.as<int>();
+    qsel = prev;
+  }
+  cudaFreeHost(h_over);
+  if (rc) return rc;
+  ix->prof.begin(5, st);
+  k_final<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(), idx,
+                                         dist);
+  ix->prof.end(st);
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int run_query(Index* ix, const float* q, int64_t Q, int k, int64_t* idx, float* dist, cudaStream_t st) {
+  QueryScratch& s = ix->qs;
+  const bool fresh = s.counters.p == nullptr;
+  TRYQ(s.counters.ensure(16 * sizeof(unsigned long long)));
+  if (fresh) SOFA_CUDA(cudaMemsetAsync(s.counters.p, 0, 16 * sizeof(unsigned long long), st));
+  int* status = reinterpret_cast<int*>(s.counters.as<unsigned long long>() + 8);
+  SOFA_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  const int64_t QB = 8192;
+  for (int64_t q0 = 0; q0 < Q; q0 += QB) {
+    const int64_t qb = std::min(QB, Q - q0);
+    const float* qp = q + q0 * ix->n;
+    int64_t* ip = idx + q0 * k;
+    float* dp = dist + q0 * k;
+    int rc;
+    if (ix->LW == 16)
+      rc = ix->nyq_first ? query_batch<16, true>(ix, qp, qb, k, ip, dp, st) : query_batch<16, false>(ix, qp, qb, k, ip, dp, st);
+    else
+      rc = ix->nyq_first ? query_batch<32, true>(ix, qp, qb, k, ip, dp, st) : query_batch<32, false>(ix, qp, qb, k, ip, dp, st);
+    if (rc) return rc;
+  }
+  ix->stats[0] += Q;
+  return 0;
+}
+
+// Scan bounds of Q queries against every series (testing aid): out[q][perm[p]].
+template <int LW, bool NYQ>
+__global__ void k_all_bounds(int64_t Q, int64_t N, int NB, const float* __restrict__ qv,
+                             const uint8_t* __restrict__ words, const uint32_t* __restrict__ perm,
+                             const float2* __restrict__ ch, float* __restrict__ out) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t q = blockIdx.y;
+  if (p >= N) return;
+  float qq[LW];
+#pragma unroll
+  for (int j = 0; j < LW; ++j) qq[j] = qv[q * NB + j];
+  float c[LW], h[LW];
+  load_word_bounds<LW>(words, p, true, ch, c, h);
+  out[q * N + perm[p]] = 2.0f * word_bound<LW, NYQ>(c, h, qq);
+}
+
+int launch_lower_bounds(Index* ix, const float* qv, int64_t Q, float* out, cudaStream_t st) {
+  dim3 g((unsigned)ceil_div(ix->N, 256), (unsigned)Q);
+  if (ix->LW == 16) {
+    if (ix->nyq_first) k_all_bounds<16, true><<<g, 256, 0, st>>>(Q, ix->N, ix->NB, qv, ix->words, ix->perm, ix->ch, out);
+    else k_all_bounds<16, false><<<g, 256, 0, st>>>(Q, ix->N, ix->NB, qv, ix->words, ix->perm, ix->ch, out);
+  } else {
+    if (ix->nyq_first) k_all_bounds<32, true><<<g, 256, 0, st>>>(Q, ix->N, ix->NB, qv, ix->words, ix->perm, ix->ch, out);
+    else k_all_bounds<32, false><<<g, 256, 0, st>>>(Q, ix->N, ix->NB, qv, ix->words, ix->perm, ix->ch, out);
+  }
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace sofa

@@ -1,0 +1,160 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/sofa.h"
+
+namespace sofa {
+
+constexpr int TILE = 256;          // series per tile (one scan CTA pass)
+constexpr int MAX_ALPHA = 256;
+constexpr int KCAP = 96;           // kept-list capacity per query (>= SOFA_MAX_K + near ties)
+constexpr int MAX_GROUP = 64;      // queries per scan work unit
+constexpr int NB_MAX = 64;         // projection columns (2l <= 64)
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define SOFA_CUDA(call)                                                               \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return ::sofa::fail(e_ == cudaErrorMemoryAllocation ? SOFA_ERR_OOM : SOFA_ERR_CUDA, \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+// Device buffers that grow on demand and are reused across calls.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t want);
+  void release();
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct QueryScratch {
+  DevBuf zq;        // Q x n canonical query series
+  DevBuf qv;        // Q x NB projected values
+  DevBuf llb;       // Q x L leaf lower bounds (half units)
+  DevBuf thr;       // Q prune thresholds (half units, fp32)
+  DevBuf list_d;    // Q x KCAP kept squared distances (fp32)
+  DevBuf list_p;    // Q x KCAP kept sorted positions
+  DevBuf list_n;    // Q kept counts
+  DevBuf leaf_cnt;  // L + 1
+  DevBuf leaf_off;  // L + 1
+  DevBuf leaf_q;    // routed (query, leaf) pairs grouped by leaf
+  DevBuf leaf_cursor;  // L fill cursors
+  DevBuf unit_off;  // L + 1
+  DevBuf units;     // int4 work units
+  DevBuf cand_p;    // Q x cap candidate positions
+  DevBuf cand_lb;   // Q x cap candidate bounds
+  DevBuf cand_n;    // Q candidate counts
+  DevBuf qflag;     // 2 x Q per-query flags (overflow), double-buffered
+  DevBuf qslot;     // Q candidate-buffer slots of overflowed queries
+  DevBuf chunk_d;   // refined chunk kept lists
+  DevBuf chunk_p;
+  DevBuf chunk_n;
+  DevBuf counters;  // misc device counters (int64)
+  DevBuf stage_in;  // staging for host queries
+  DevBuf stage_out;
+  DevBuf pinned_dummy;
+};
+
+struct Mlp;  // proposal network (mlp.cu)
+
+// Phase timing with CUDA events on the launching stream.
+constexpr int NPHASE = 8;
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> open;
+  double ms[NPHASE] = {0};
+  long long launches[NPHASE] = {0};
+  cudaEvent_t get();
+  void begin(int phase, cudaStream_t st, int kernels = 1);
+  void end(cudaStream_t st);
+  void collect();  // after the stream has been synchronised
+  void release();
+};
+
+struct Index {
+  int64_t N = 0;
+  int n = 0, l = 0, alpha = 0, LW = 16, nsel = 0, NB = 16, bps = 8;
+  int nyq_first = 0;
+  int leaf_tiles = 64;
+  int64_t T = 0, L = 0;
+  int precision = 0;
+  double delta_d = 0, delta_q = 0, vmax = 0;
+  int device = 0;
+  // summary
+  int32_t* sel = nullptr;      // [nsel] value ids (device)
+  int32_t* sel_k = nullptr;    // [nsel]
+  int32_t* sel_part = nullptr; // [nsel]
+  double* var = nullptr;       // [nsel] selected variances
+  float* basis = nullptr;      // [n][NB] projection basis
+  float* beta = nullptr;       // [LW][alpha+1]
+  float2* edge = nullptr;      // [LW][256] widened (lo, hi) per symbol
+  float2* ch = nullptr;        // [LW][256] (centre, half-width) per symbol
+  // layout
+  uint8_t* words = nullptr;    // [N][LW] key-sorted
+  float* Z = nullptr;          // [N][n] key-sorted canonical series
+  uint32_t* perm = nullptr;    // [N] sorted position -> original row
+  uint64_t* keys = nullptr;    // [N] sorted layout keys
+  uint8_t* keyorder = nullptr; // [64] key bit order (dim << 3 | bit)
+  int keybits = 0;
+  uint8_t* tenv = nullptr;     // [T][2][LW] tile envelopes (lo row, hi row)
+  uint8_t* lenv = nullptr;     // [L][2][LW] leaf envelopes
+  int64_t device_bytes = 0;
+  // query state
+  QueryScratch qs;
+  int group = 32, cand_cap = 32768, seed_count = 32;
+  int seed_mode = 0;
+  int status = 0;
+  int64_t stats[8] = {0};
+  Mlp* mlp = nullptr;
+  Prof prof;
+};
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Canonical z-normalisation statistics of one row, the left-to-right FP64
+// sums of Sec. II Def. z-ED (explicit IEEE intrinsics: nothing is fused).
+__device__ inline void znorm_stats_seq(const float* row, int n, int stride, double& mu, double& inv) {
+  double s = 0.0;
+  for (int t = 0; t < n; ++t) s = __dadd_rn(s, (double)row[t * stride]);
+  mu = __ddiv_rn(s, (double)n);
+  double ss = 0.0;
+  for (int t = 0; t < n; ++t) {
+    double d = __dsub_rn((double)row[t * stride], mu);
+    ss = __dadd_rn(ss, __dmul_rn(d, d));
+  }
+  double sigma = __dsqrt_rn(__ddiv_rn(ss, (double)n));
+  inv = (sigma == 0.0) ? 0.0 : __ddiv_rn(1.0, sigma);
+}
+
+__device__ inline float znorm_value(float x, double mu, double inv) {
+  return __double2float_rn(__dmul_rn(__dsub_rn((double)x, mu), inv));
+}
+
+// Launch helpers implemented in the .cu files.
+int build_index(Index* ix, const float* data_dev, const sofa_build_opts& o, cudaStream_t st);
+int run_query(Index* ix, const float* q_dev, int64_t Q, int k, int64_t* idx_dev, float* dist_dev,
+              cudaStream_t st);
+int launch_qprep(Index* ix, const float* q_dev, int64_t Q, float* zq, float* qv, cudaStream_t st);
+int launch_lower_bounds(Index* ix, const float* qv, int64_t Q, float* out, cudaStream_t st);
+int launch_znorm(const float* x, int64_t R, int n, float* z, cudaStream_t st);
+int mlp_train(Index* ix, const sofa_train_opts& o, cudaStream_t st);
+int mlp_seed(Index* ix, const float* qv, int64_t Q, int k, cudaStream_t st);
+void mlp_free(Mlp* m);
+
+}  // namespace sofa
+
+// The opaque handle type of the C ABI is the index itself.
+struct sofa_index : public sofa::Index {};

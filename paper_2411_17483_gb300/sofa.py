@@ -1,0 +1,272 @@
+"""Thin ctypes binding of the C ABI in include/sofa.h (argument marshalling only).
+
+Every step of the search runs in libsofa.so's CUDA kernels; this module only
+passes pointers, sizes and streams.  Tensors may live on the GPU or (for the
+build and for host-buffer queries) on the host.  There is no CPU fallback:
+if the library is missing, load() raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsofa.so")
+
+SOFA_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "NOT_TRAINED", -6: "TIE_OVERFLOW"}
+MAX_K = 64
+MAX_WORD = 32
+
+_lib = None
+
+
+class SofaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sofa error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("sample_ratio", ctypes.c_float), ("binning", ctypes.c_int32), ("select", ctypes.c_int32),
+                ("pool_coeffs", ctypes.c_int32), ("leaf_tiles", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("user_sel", ctypes.POINTER(ctypes.c_int32)), ("user_nsel", ctypes.c_int32),
+                ("user_beta", ctypes.POINTER(ctypes.c_float))]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("n_train", ctypes.c_int64), ("n_classes", ctypes.c_int32), ("epochs", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("train_queries", ctypes.c_void_p), ("top_m", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int32), ("cand_cap", ctypes.c_int32), ("seed_count", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in
+                ("queries", "leaf_pairs", "tile_pairs", "candidates", "refined", "overflow_passes",
+                 "n_leaves", "n_tiles")]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8),
+                ("scan_tile_loads", ctypes.c_int64), ("scan_tile_checks", ctypes.c_int64)]
+
+
+PHASES = ("qprep", "seed", "route", "scan", "refine", "final", "p6", "p7")
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("n", ctypes.c_int32), ("l", ctypes.c_int32),
+                ("alphabet", ctypes.c_int32), ("nsel", ctypes.c_int32), ("word_bytes", ctypes.c_int32),
+                ("nyquist_first", ctypes.c_int32), ("leaf_tiles", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("delta_data", ctypes.c_double), ("delta_query", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
+
+
+def load():
+    """Load libsofa.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library must be built first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "sofa_build": (P, [P, i64, i32, i32, i32]),
+        "sofa_build_ex": (P, [P, i64, i32, i32, i32, ctypes.POINTER(BuildOpts), P]),
+        "sofa_query": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
+        "sofa_query_multi": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P]),
+        "sofa_train_proposal": (ctypes.c_int, [P, ctypes.POINTER(TrainOpts), P]),
+        "sofa_set_seed_mode": (ctypes.c_int, [P, i32]),
+        "sofa_set_tuning": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
+        "sofa_query_status": (ctypes.c_int, [P]),
+        "sofa_stats": (ctypes.c_int, [P, ctypes.POINTER(Stats), i32]),
+        "sofa_info": (ctypes.c_int, [P, ctypes.POINTER(Info)]),
+        "sofa_set_profiling": (ctypes.c_int, [P, i32]),
+        "sofa_profile": (ctypes.c_int, [P, ctypes.POINTER(Profile), i32]),
+        "sofa_export_summary": (ctypes.c_int, [P, P, P, P]),
+        "sofa_export_words": (ctypes.c_int, [P, P]),
+        "sofa_export_perm": (ctypes.c_int, [P, P]),
+        "sofa_lower_bounds": (ctypes.c_int, [P, P, i64, P, P]),
+        "sofa_znorm": (ctypes.c_int, [P, i64, i32, P, P]),
+        "sofa_free": (None, [P]),
+        "sofa_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != SOFA_OK:
+        raise SofaError(rc, load().sofa_last_error().decode())
+
+
+def _stream(stream=None):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Index:
+    """An SFA index over N series of length n (sofa_build_ex)."""
+
+    def __init__(self, data: torch.Tensor, l: int = 16, alphabet: int = 256, *, sample_ratio: float = 0.1,
+                 binning: str = "equi-depth", select: str = "variance", pool_coeffs: int = 0,
+                 leaf_tiles: int = 0, precision: int = 0, user_sel=None, user_beta=None, stream=None):
+        lib = load()
+        if data.dtype != torch.float32 or data.dim() != 2:
+            raise ValueError("data must be a 2-d float32 tensor")
+        data = data.contiguous()
+        o = BuildOpts()
+        o.sample_ratio = sample_ratio
+        o.binning = {"equi-depth": 0, "equi-width": 1}[binning]
+        o.select = {"variance": 0, "first": 1}[select]
+        o.pool_coeffs = pool_coeffs
+        o.leaf_tiles = leaf_tiles
+        o.precision = precision
+        keep = []
+        if user_sel is not None:
+            us = torch.as_tensor(user_sel, dtype=torch.int32).contiguous()
+            ub = torch.as_tensor(user_beta, dtype=torch.float32).contiguous()
+            keep += [us, ub]
+            o.user_sel = ctypes.cast(us.data_ptr(), ctypes.POINTER(ctypes.c_int32))
+            o.user_nsel = us.numel()
+            o.user_beta = ctypes.cast(ub.data_ptr(), ctypes.POINTER(ctypes.c_float))
+        st = _stream(stream) if data.is_cuda else ctypes.c_void_p(0)
+        h = lib.sofa_build_ex(_ptr(data), data.shape[0], data.shape[1], l, alphabet, ctypes.byref(o), st)
+        if not h:
+            raise SofaError(-1, lib.sofa_last_error().decode())
+        self.h = ctypes.c_void_p(h)
+        self.N, self.n, self.l, self.alphabet = data.shape[0], data.shape[1], l, alphabet
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sofa_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, q: torch.Tensor, k: int = 1, idx: torch.Tensor | None = None,
+              dist: torch.Tensor | None = None, stream=None):
+        """Exact k-NN of the rows of q; returns (idx int64 [Q,k], dist fp32 [Q,k])."""
+        q = q.contiguous()
+        Q = q.shape[0]
+        dev = q.device
+        if idx is None:
+            idx = torch.empty((Q, k), dtype=torch.int64, device=dev)
+        if dist is None:
+            dist = torch.empty((Q, k), dtype=torch.float32, device=dev)
+        _check(load().sofa_query(self.h, _ptr(q), Q, k, _ptr(idx), _ptr(dist), _stream(stream)))
+        return idx, dist
+
+    def set_tuning(self, group=0, cand_cap=0, seed_count=0):
+        t = Tuning(group, cand_cap, seed_count)
+        _check(load().sofa_set_tuning(self.h, ctypes.byref(t)))
+
+    def set_seed_mode(self, mode: int):
+        _check(load().sofa_set_seed_mode(self.h, mode))
+
+    def train_proposal(self, n_train=0, n_classes=0, epochs=0, batch=0, lr=0.0, seed=2, train_queries=None,
+                       top_m=0, stream=None):
+        o = TrainOpts(n_train, n_classes, epochs, batch, lr, seed,
+                      train_queries.data_ptr() if train_queries is not None else None, top_m)
+        _check(load().sofa_train_proposal(self.h, ctypes.byref(o), _stream(stream)))
+
+    def status(self) -> int:
+        return load().sofa_query_status(self.h)
+
+    def stats(self, reset=False) -> dict:
+        s = Stats()
+        _check(load().sofa_stats(self.h, ctypes.byref(s), 1 if reset else 0))
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def set_profiling(self, on: bool = True):
+        _check(load().sofa_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self, reset=False) -> dict:
+        s = Profile()
+        _check(load().sofa_profile(self.h, ctypes.byref(s), 1 if reset else 0))
+        return {"ms": {PHASES[i]: s.ms[i] for i in range(6)},
+                "launches": {PHASES[i]: s.launches[i] for i in range(6)},
+                "scan_tile_loads": s.scan_tile_loads, "scan_tile_checks": s.scan_tile_checks}
+
+    def info(self) -> dict:
+        s = Info()
+        _check(load().sofa_info(self.h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in Info._fields_}
+
+    def summary(self):
+        inf = self.info()
+        sel = torch.empty(inf["nsel"], dtype=torch.int32)
+        var = torch.empty(inf["nsel"], dtype=torch.float64)
+        beta = torch.empty((self.l, self.alphabet + 1), dtype=torch.float32)
+        _check(load().sofa_export_summary(self.h, _ptr(sel), _ptr(var), _ptr(beta)))
+        return sel, var, beta
+
+    def words(self) -> torch.Tensor:
+        w = torch.empty((self.N, self.l), dtype=torch.uint8)
+        _check(load().sofa_export_words(self.h, _ptr(w)))
+        return w
+
+    def perm(self) -> torch.Tensor:
+        p = torch.empty(self.N, dtype=torch.int32)
+        _check(load().sofa_export_perm(self.h, _ptr(p)))
+        return p
+
+    def lower_bounds(self, q: torch.Tensor, stream=None) -> torch.Tensor:
+        q = q.contiguous()
+        out = torch.empty((q.shape[0], self.N), dtype=torch.float32, device=q.device)
+        _check(load().sofa_lower_bounds(self.h, _ptr(q), q.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+
+def znorm(x: torch.Tensor, stream=None) -> torch.Tensor:
+    x = x.contiguous()
+    z = torch.empty_like(x)
+    _check(load().sofa_znorm(_ptr(x), x.shape[0], x.shape[1], _ptr(z), _stream(stream)))
+    return z
+
+
+def query_multi(indexes, queries: torch.Tensor, q_offsets, q_len, q_k, out_offsets, total_out, stream=None):
+    """Mixed-length / mixed-k queries over several indexes (sofa_query_multi)."""
+    dev = queries.device
+    arr = (ctypes.c_void_p * len(indexes))(*[ix.h.value for ix in indexes])
+    qo = torch.as_tensor(q_offsets, dtype=torch.int64, device=dev).contiguous()
+    ql = torch.as_tensor(q_len, dtype=torch.int32, device=dev).contiguous()
+    qk = torch.as_tensor(q_k, dtype=torch.int32, device=dev).contiguous()
+    oo = torch.as_tensor(out_offsets, dtype=torch.int64, device=dev).contiguous()
+    idx = torch.full((total_out,), -1, dtype=torch.int64, device=dev)
+    dist = torch.full((total_out,), float("inf"), dtype=torch.float32, device=dev)
+    _check(load().sofa_query_multi(arr, len(indexes), _ptr(queries), _ptr(qo), _ptr(ql), _ptr(qk), qo.numel(),
+                                   _ptr(idx), _ptr(dist), _ptr(oo), _stream(stream)))
+    return idx, dist
+
+
+def search(data: torch.Tensor, queries: torch.Tensor, k: int = 1, l: int = 16, alphabet: int = 256, **kw):
+    """Build an index, answer the queries, free the index."""
+    ix = Index(data, l, alphabet, **kw)
+    try:
+        return ix.query(queries, k)
+    finally:
+        ix.close()
