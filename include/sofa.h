@@ -125,9 +125,11 @@ int sofa_set_seed_mode(sofa_handle h, int32_t mode);
 
 /* Run-time tuning knobs (any value keeps answers exact). */
 typedef struct {
-  int32_t group;        /* queries per scan work unit (1..64); 0 -> 32         */
-  int32_t cand_cap;     /* candidate slots per query per pass; 0 -> 32768      */
-  int32_t seed_count;   /* series refined by the seed; 0 -> 32 (>= k used)     */
+  int32_t group;        /* queries per scan work unit (1..64); 0 -> 64         */
+  int32_t cand_cap;     /* candidate slots per query per pass; 0 -> 131072     */
+  int32_t seed_count;   /* series refined by the seed; 0 -> 128 (>= k used)    */
+  int32_t seed_window;  /* key-sorted series bounded by the seed (power of two
+                           <= 4096); 0 -> 4096                                  */
 } sofa_tuning;
 int sofa_set_tuning(sofa_handle h, const sofa_tuning* t);
 
@@ -145,6 +147,8 @@ typedef struct {
   int64_t overflow_passes;  /* extra scan passes after a full candidate buffer   */
   int64_t n_leaves;         /* leaf blocks in the index                          */
   int64_t n_tiles;          /* tiles in the index                                */
+  double seed_dist_sum;     /* sum over queries of the seed's k-th distance      */
+  double final_dist_sum;    /* sum over queries of the answer's k-th distance    */
 } sofa_stats_t;
 int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset);
 

@@ -247,10 +247,15 @@ int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset) {
   out->candidates = (int64_t)c[2];
   out->refined = (int64_t)c[3];
   out->overflow_passes = h->stats[5];
+  out->seed_dist_sum = (double)c[6] * 1e-6;
+  out->final_dist_sum = (double)c[7] * 1e-6;
   out->n_leaves = h->L;
   out->n_tiles = h->T;
   if (reset) {
-    if (h->qs.counters.p) SOFA_CUDA(cudaMemset(h->qs.counters.p, 0, 4 * sizeof(unsigned long long)));
+    if (h->qs.counters.p) {
+      SOFA_CUDA(cudaMemset(h->qs.counters.p, 0, 4 * sizeof(unsigned long long)));
+      SOFA_CUDA(cudaMemset(h->qs.counters.as<unsigned long long>() + 6, 0, 2 * sizeof(unsigned long long)));
+    }
     h->stats[0] = 0;
     h->stats[5] = 0;
   }
@@ -262,9 +267,12 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   if (t->group < 0 || t->group > MAX_GROUP) return fail(SOFA_ERR_INVALID_ARG, "group must lie in [0, 64]");
   if (t->cand_cap < 0) return fail(SOFA_ERR_INVALID_ARG, "cand_cap must be >= 0");
   if (t->seed_count < 0 || t->seed_count > TILE) return fail(SOFA_ERR_INVALID_ARG, "seed_count must lie in [0, 256]");
-  h->group = t->group ? t->group : 32;
-  h->cand_cap = t->cand_cap ? t->cand_cap : 32768;
-  h->seed_count = t->seed_count ? t->seed_count : 32;
+  if (t->seed_window < 0 || t->seed_window > SEED_MAX || (t->seed_window & (t->seed_window - 1)))
+    return fail(SOFA_ERR_INVALID_ARG, "seed_window must be 0 or a power of two <= 4096");
+  h->group = t->group ? t->group : 64;
+  h->cand_cap = t->cand_cap ? t->cand_cap : 131072;
+  h->seed_count = t->seed_count ? t->seed_count : 128;
+  h->seed_window = t->seed_window ? t->seed_window : 4096;
   return 0;
 }
 

@@ -16,12 +16,10 @@
 namespace sofa {
 
 
-constexpr int SEED_TILES = 4;                 // tiles of the best leaf whose series seed the bound
-constexpr int SEED_SORT = SEED_TILES * TILE;  // 1024 series bounded by the seed
 
 struct QueryParams {
   int64_t N, T, L;
-  int n, NB, leaf_tiles, k, cap, group, seed_count;
+  int n, NB, leaf_tiles, k, cap, group, seed_count, seed_window;
   float f_prune;  // threshold = d2_kth * f_prune / 2 (half units)
   float f_keep;   // kept list: d2 <= d2_kth * f_keep
 };
@@ -192,11 +190,12 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
                                               const uint8_t* __restrict__ keyorder, int keybits,
                                               float* __restrict__ llb, float* __restrict__ list_d,
                                               uint32_t* __restrict__ list_p, int* __restrict__ list_n,
-                                              float* __restrict__ thr, int* __restrict__ status) {
+                                              float* __restrict__ thr, int* __restrict__ status,
+                                              unsigned long long* __restrict__ counters) {
   extern __shared__ float4 ssm[];
   float* szq = reinterpret_cast<float*>(ssm);            // n
   __shared__ float sq[LW];
-  __shared__ unsigned long long skey[SEED_SORT];
+  __shared__ unsigned long long skey[SEED_MAX];
   __shared__ unsigned long long sbest[8];
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -259,21 +258,21 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
     }
     __syncthreads();
   }
-  const int64_t W = P.N < SEED_SORT ? P.N : SEED_SORT;
+  const int64_t W = P.N < P.seed_window ? P.N : P.seed_window;
   int64_t p0 = s_lo - W / 2;
   if (p0 > P.N - W) p0 = P.N - W;
   if (p0 < 0) p0 = 0;
 
   // (3) series bounds of the window around that position; the seed_count
   // smallest are refined
-  for (int i = tid; i < SEED_SORT; i += blockDim.x) {
+  for (int i = tid; i < P.seed_window; i += blockDim.x) {
     const int64_t p = p0 + i;
     const bool valid = i < W;
     float c[LW], h[LW];
     load_word_bounds<LW>(words, p, valid, ch, c, h);
     skey[i] = valid ? pack_key(word_bound<LW, NYQ>(c, h, sq), (uint32_t)p) : ~0ull;
   }
-  block_bitonic(skey, SEED_SORT);
+  block_bitonic(skey, P.seed_window);
   int cnt = P.seed_count > P.k ? P.seed_count : P.k;
   if (cnt > W) cnt = (int)W;
   __shared__ float sd[TILE];
@@ -293,6 +292,8 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
   for (int i = tid; i < TILE; i += blockDim.x) skey[i] = i < cnt ? pack_key(sd[i], sp[i]) : ~0ull;
   block_bitonic(skey, TILE);
   if (!emit_list(skey, cnt, P, q, list_d, list_p, list_n, thr) && tid == 0) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
+  if (tid == 0)
+    atomicAdd(counters + 6, (unsigned long long)(1e6 * sqrt((double)__uint_as_float((uint32_t)(skey[P.k - 1] >> 32)))));
 }
 
 // ------------------------------------------------------------------------
@@ -450,19 +451,26 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
         m &= m - 1;
         const float T = sT[g];
         const float* qg = sq[g];
-        float acc = 0.f;
+        // two partial sums (even / odd values) halve the dependent FMA chain;
+        // the warp votes after 4, 8, 16 (and 32) values
+        float a0 = 0.f, a1 = 0.f;
         bool live = valid;
 #pragma unroll
-        for (int c0 = 0; c0 < LW; c0 += 8) {
+        for (int stage = 0; stage < 8; ++stage) {
+          const int j0 = stage == 0 ? 0 : (4 << (stage - 1));
+          const int j1 = 4 << stage;
+          if (j0 >= LW) break;
           if (!__any_sync(0xFFFFFFFFu, live)) break;
 #pragma unroll
-          for (int j = c0; j < c0 + 8; ++j) {
-            float mj = fmaxf(fabsf(qg[j] - c[j]) - h[j], 0.f);
-            float mm = (NYQ && j == 0) ? 0.5f * mj : mj;
-            acc = fmaf(mm, mj, acc);
+          for (int j = j0; j < j1 && j < LW; j += 2) {
+            const float m0 = fmaxf(fabsf(qg[j] - c[j]) - h[j], 0.f);
+            const float m1 = fmaxf(fabsf(qg[j + 1] - c[j + 1]) - h[j + 1], 0.f);
+            a0 = fmaf((NYQ && j == 0) ? 0.5f * m0 : m0, m0, a0);
+            a1 = fmaf(m1, m1, a1);
           }
-          live = live && acc <= T;
+          live = live && (a0 + a1) <= T;
         }
+        const float acc = a0 + a1;
         const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
         if (hit) {
           const int qs = sslot[g];
@@ -698,7 +706,8 @@ __global__ void __launch_bounds__(256) k_merge(QueryParams P, int nchunk, const 
 __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __restrict__ zq,
                                                const float* __restrict__ Z, const uint32_t* __restrict__ perm,
                                                const uint32_t* __restrict__ list_p, const int* __restrict__ list_n,
-                                               int64_t* __restrict__ idx, float* __restrict__ dist) {
+                                               int64_t* __restrict__ idx, float* __restrict__ dist,
+                                               unsigned long long* __restrict__ counters) {
   extern __shared__ float dsm[];
   float* szq = dsm;
   __shared__ double sd[128];
@@ -766,6 +775,7 @@ __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __res
     }
   }
   __syncthreads();
+  if (tid == 0 && nl >= P.k) atomicAdd(counters + 7, (unsigned long long)(1e6 * sd[P.k - 1]));
   if (tid < P.k) {
     idx[q * P.k + tid] = tid < nl ? (int64_t)sid[tid] : -1;
     dist[q * P.k + tid] = tid < nl ? (float)sd[tid] : INFINITY;
@@ -793,6 +803,7 @@ static QueryParams make_params(const Index* ix, int k) {
   P.cap = ix->cand_cap;
   P.group = ix->group;
   P.seed_count = ix->seed_count;
+  P.seed_window = ix->seed_window;
   // Rounding-error factors (u = 2^-24): the FP32 bound sum over LW values has
   // relative error <= (LW+3)u; the FP32 distance <= (n+3)u/(1-(n+3)u).  A
   // series is pruned only when its bound proves it farther than the k-th kept
@@ -846,7 +857,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   k_seed<LW, NYQ><<<(unsigned)Q, 256, nsm, st>>>(P, qv, zq, ix->lenv, ix->tenv, ix->words, ix->Z, ix->edge, ix->ch,
                                                   ix->beta, ix->alpha, ix->l, ix->keys, ix->keyorder, ix->keybits,
                                                   llb, s.list_d.as<float>(), s.list_p.as<uint32_t>(),
-                                                  s.list_n.as<int>(), thr, status);
+                                                  s.list_n.as<int>(), thr, status, counters);
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
 
@@ -953,7 +964,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   if (rc) return rc;
   ix->prof.begin(5, st);
   k_final<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(), idx,
-                                         dist);
+                                         dist, counters);
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
   return 0;

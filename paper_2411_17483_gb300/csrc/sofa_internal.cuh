@@ -17,6 +17,7 @@ constexpr int MAX_ALPHA = 256;
 constexpr int KCAP = 96;           // kept-list capacity per query (>= SOFA_MAX_K + near ties)
 constexpr int MAX_GROUP = 64;      // queries per scan work unit
 constexpr int NB_MAX = 64;         // projection columns (2l <= 64)
+constexpr int SEED_MAX = 4096;     // largest seed window
 
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
@@ -113,7 +114,7 @@ struct Index {
   int64_t device_bytes = 0;
   // query state
   QueryScratch qs;
-  int group = 32, cand_cap = 32768, seed_count = 32;
+  int group = 64, cand_cap = 131072, seed_count = 128, seed_window = 4096;
   int seed_mode = 0;
   int status = 0;
   int64_t stats[8] = {0};

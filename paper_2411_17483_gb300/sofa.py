@@ -43,13 +43,14 @@ class TrainOpts(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("group", ctypes.c_int32), ("cand_cap", ctypes.c_int32), ("seed_count", ctypes.c_int32)]
+    _fields_ = [("group", ctypes.c_int32), ("cand_cap", ctypes.c_int32), ("seed_count", ctypes.c_int32),
+                ("seed_window", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in
                 ("queries", "leaf_pairs", "tile_pairs", "candidates", "refined", "overflow_passes",
-                 "n_leaves", "n_tiles")]
+                 "n_leaves", "n_tiles")] + [("seed_dist_sum", ctypes.c_double), ("final_dist_sum", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -180,8 +181,8 @@ class Index:
         _check(load().sofa_query(self.h, _ptr(q), Q, k, _ptr(idx), _ptr(dist), _stream(stream)))
         return idx, dist
 
-    def set_tuning(self, group=0, cand_cap=0, seed_count=0):
-        t = Tuning(group, cand_cap, seed_count)
+    def set_tuning(self, group=0, cand_cap=0, seed_count=0, seed_window=0):
+        t = Tuning(group, cand_cap, seed_count, seed_window)
         _check(load().sofa_set_tuning(self.h, ctypes.byref(t)))
 
     def set_seed_mode(self, mode: int):

@@ -173,7 +173,8 @@ def test_duplicates_and_member_queries(sofa):
 
 
 @pytest.mark.parametrize("tuning", [dict(group=1), dict(group=64), dict(cand_cap=1), dict(cand_cap=7, group=3),
-                                    dict(seed_count=1), dict(seed_count=256)])
+                                    dict(seed_count=1), dict(seed_count=256), dict(seed_window=4096, seed_count=128),
+                                    dict(seed_window=256)])
 def test_tuning_invariance(sofa, tuning):
     N, n = 15000, 128
     x = datagen.mixed_walks(N, n, seed=31, device=DEV)
