@@ -119,6 +119,16 @@ typedef struct {
 } sofa_train_opts;
 int sofa_train_proposal(sofa_handle h, const sofa_train_opts* opts, sofa_stream stream);
 
+/* Loss and parameter gradients of the proposal network on one batch, for
+ * checking the training kernels (not in the paper).  Network din -> hidden
+ * -> hidden -> classes with exact-erf GELU; params and grads are flat FP32 in
+ * the order W1 [din x hidden], b1, W2 [hidden x hidden], b2,
+ * W3 [hidden x classes], b3; x is B x din FP32, y B int32 labels; loss is
+ * the mean softmax cross-entropy (host).  Arithmetic: BF16 operands on
+ * tensor cores, FP32 accumulation.  params/x/y/grads: host or device. */
+int sofa_mlp_grad(int32_t din, int32_t hidden, int32_t classes, const float* params, const float* x,
+                  const int32_t* y, int32_t B, float* grads, float* loss, sofa_stream stream);
+
 /* Seed mode of later sofa_query calls: 0 plain approximate search (best leaf,
  * best tile), 1 learned proposal (needs sofa_train_proposal). */
 int sofa_set_seed_mode(sofa_handle h, int32_t mode);
@@ -155,7 +165,7 @@ int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset);
 /* Per-phase device time of sofa_query calls made while profiling is on,
  * from CUDA events recorded on the call's stream around each phase: index
  * 0 query transform, 1 seed, 2 routing, 3 series scan, 4 refinement,
- * 5 final re-score.  launches[i] counts this library's kernel launches per
+ * 5 final re-score, 6 proposal network inference.  launches[i] counts this library's kernel launches per
  * phase (counted whether or not profiling is on); scan_tile_loads counts the
  * (work unit, tile) pairs whose words the scan read. */
 typedef struct {
@@ -174,6 +184,11 @@ typedef struct {
   int64_t n_leaves, n_tiles;
   double delta_data, delta_query;  /* projection error margins in use          */
   int64_t device_bytes;            /* bytes of device memory the index holds   */
+  int64_t proposal_classes;        /* trained proposal network: classes (0: none) */
+  int64_t proposal_train;          /* training pairs                           */
+  double proposal_loss;            /* mean cross-entropy of the last epoch     */
+  double proposal_top1, proposal_topm;  /* held-out hit rate of the block of the
+                                           exact nearest neighbour (top-1, top-m) */
 } sofa_info_t;
 int sofa_info(sofa_handle h, sofa_info_t* out);
 

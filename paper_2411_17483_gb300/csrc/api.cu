@@ -291,6 +291,8 @@ int sofa_info(sofa_handle h, sofa_info_t* out) {
   out->delta_data = h->delta_d;
   out->delta_query = h->delta_q;
   out->device_bytes = h->device_bytes;
+  mlp_report(h, &out->proposal_loss, &out->proposal_top1, &out->proposal_topm, &out->proposal_classes,
+             &out->proposal_train);
   return 0;
 }
 

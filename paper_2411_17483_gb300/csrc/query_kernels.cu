@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
                                               float* __restrict__ llb, float* __restrict__ list_d,
                                               uint32_t* __restrict__ list_p, int* __restrict__ list_n,
                                               float* __restrict__ thr, int* __restrict__ status,
-                                              unsigned long long* __restrict__ counters) {
+                                              unsigned long long* __restrict__ counters,
+                                              const int32_t* __restrict__ topm, int top_m, int64_t block) {
   extern __shared__ float4 ssm[];
   float* szq = reinterpret_cast<float*>(ssm);            // n
   __shared__ float sq[LW];
@@ -258,23 +259,72 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
     }
     __syncthreads();
   }
-  const int64_t W = P.N < P.seed_window ? P.N : P.seed_window;
+  // learned seeding: the best tile (by envelope bound) of each of the
+  // proposal network's top-m blocks joins the key window
+  int m_eff = topm ? top_m : 0;
+  if (m_eff * TILE > P.seed_window / 2) m_eff = P.seed_window / (2 * TILE);
+  const int nlearn = m_eff * TILE;
+  __shared__ int64_t s_ltile[8];
+  for (int i = 0; i < m_eff; ++i) {
+    const int64_t b = topm[q * top_m + i];
+    const int64_t lo_t = (b * block) / TILE;
+    int64_t hi_p = (b + 1) * block < P.N ? (b + 1) * block : P.N;
+    const int64_t hi_t = (hi_p + TILE - 1) / TILE;
+    unsigned long long best = ~0ull;
+    for (int64_t t = lo_t + tid; t < hi_t && t < P.T; t += blockDim.x) {
+      const unsigned long long kk = pack_key(env_bound<LW, NYQ>(tenv + t * 2 * LW, sq, edge), (uint32_t)t);
+      best = kk < best ? kk : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+      best = v < best ? v : best;
+    }
+    if (lane == 0) sbest[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long v = sbest[0];
+      for (int w = 1; w < 8; ++w) v = sbest[w] < v ? sbest[w] : v;
+      s_ltile[i] = v == ~0ull ? -1 : (int64_t)(uint32_t)v;
+    }
+    __syncthreads();
+  }
+  const int wkey = P.seed_window - nlearn;
+  const int64_t W = P.N < wkey ? P.N : wkey;
   int64_t p0 = s_lo - W / 2;
   if (p0 > P.N - W) p0 = P.N - W;
   if (p0 < 0) p0 = 0;
 
-  // (3) series bounds of the window around that position; the seed_count
-  // smallest are refined
+  // (3) series bounds of the key window (and the learned tiles); the
+  // seed_count smallest distinct ones are refined
   for (int i = tid; i < P.seed_window; i += blockDim.x) {
-    const int64_t p = p0 + i;
-    const bool valid = i < W;
+    int64_t p;
+    bool valid;
+    if (i < wkey) {
+      p = p0 + i;
+      valid = i < W;
+    } else {
+      const int j = i - wkey;
+      const int64_t tt = s_ltile[j / TILE];
+      p = tt * TILE + (j % TILE);
+      valid = tt >= 0 && p < P.N;
+    }
     float c[LW], h[LW];
     load_word_bounds<LW>(words, p, valid, ch, c, h);
     skey[i] = valid ? pack_key(word_bound<LW, NYQ>(c, h, sq), (uint32_t)p) : ~0ull;
   }
   block_bitonic(skey, P.seed_window);
   int cnt = P.seed_count > P.k ? P.seed_count : P.k;
-  if (cnt > W) cnt = (int)W;
+  __shared__ int s_avail;
+  if (tid == 0) {  // a learned tile may overlap the key window: drop repeats
+    int u = 0;
+    for (int i = 0; i < P.seed_window && u < cnt; ++i) {
+      if (skey[i] == ~0ull) break;
+      if (u == 0 || skey[i] != skey[u - 1]) skey[u++] = skey[i];
+    }
+    s_avail = u;
+  }
+  __syncthreads();
+  if (cnt > s_avail) cnt = s_avail;
   __shared__ float sd[TILE];
   __shared__ uint32_t sp[TILE];
   for (int base = 0; base < cnt; base += 64) {  // same 4-lane FP32 sum as the refinement
@@ -853,11 +903,20 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   TRYQ(launch_qprep(ix, qdev, Q, zq, qv, st));
   ix->prof.end(st);
   const size_t nsm = (size_t)n * sizeof(float);
+  const int32_t* topm = nullptr;
+  int top_m = 0;
+  int64_t block = 0;
+  if (ix->seed_mode == 1) {
+    ix->prof.begin(6, st, 6);
+    TRYQ(mlp_seed(ix, qv, Q, k, st));
+    ix->prof.end(st);
+    topm = mlp_topm(ix, &top_m, &block);
+  }
   ix->prof.begin(1, st);
   k_seed<LW, NYQ><<<(unsigned)Q, 256, nsm, st>>>(P, qv, zq, ix->lenv, ix->tenv, ix->words, ix->Z, ix->edge, ix->ch,
                                                   ix->beta, ix->alpha, ix->l, ix->keys, ix->keyorder, ix->keybits,
                                                   llb, s.list_d.as<float>(), s.list_p.as<uint32_t>(),
-                                                  s.list_n.as<int>(), thr, status, counters);
+                                                  s.list_n.as<int>(), thr, status, counters, topm, top_m, block);
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
 

@@ -154,6 +154,8 @@ int launch_znorm(const float* x, int64_t R, int n, float* z, cudaStream_t st);
 int mlp_train(Index* ix, const sofa_train_opts& o, cudaStream_t st);
 int mlp_seed(Index* ix, const float* qv, int64_t Q, int k, cudaStream_t st);
 void mlp_free(Mlp* m);
+const int32_t* mlp_topm(Index* ix, int* m, int64_t* block);
+void mlp_report(Index* ix, double* loss, double* top1, double* topm, int64_t* classes, int64_t* n_train);
 
 }  // namespace sofa
 

@@ -58,7 +58,7 @@ class Profile(ctypes.Structure):
                 ("scan_tile_loads", ctypes.c_int64), ("scan_tile_checks", ctypes.c_int64)]
 
 
-PHASES = ("qprep", "seed", "route", "scan", "refine", "final", "p6", "p7")
+PHASES = ("qprep", "seed", "route", "scan", "refine", "final", "proposal", "p7")
 
 
 class Info(ctypes.Structure):
@@ -67,7 +67,9 @@ class Info(ctypes.Structure):
                 ("nyquist_first", ctypes.c_int32), ("leaf_tiles", ctypes.c_int32),
                 ("n_leaves", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
                 ("delta_data", ctypes.c_double), ("delta_query", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("proposal_classes", ctypes.c_int64),
+                ("proposal_train", ctypes.c_int64), ("proposal_loss", ctypes.c_double),
+                ("proposal_top1", ctypes.c_double), ("proposal_topm", ctypes.c_double)]
 
 
 def load():
@@ -88,6 +90,7 @@ def load():
         "sofa_query_multi": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P]),
         "sofa_train_proposal": (ctypes.c_int, [P, ctypes.POINTER(TrainOpts), P]),
         "sofa_set_seed_mode": (ctypes.c_int, [P, i32]),
+        "sofa_mlp_grad": (ctypes.c_int, [i32, i32, i32, P, P, P, i32, P, ctypes.POINTER(ctypes.c_float), P]),
         "sofa_set_tuning": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
         "sofa_query_status": (ctypes.c_int, [P]),
         "sofa_stats": (ctypes.c_int, [P, ctypes.POINTER(Stats), i32]),
@@ -208,8 +211,8 @@ class Index:
     def profile(self, reset=False) -> dict:
         s = Profile()
         _check(load().sofa_profile(self.h, ctypes.byref(s), 1 if reset else 0))
-        return {"ms": {PHASES[i]: s.ms[i] for i in range(6)},
-                "launches": {PHASES[i]: s.launches[i] for i in range(6)},
+        return {"ms": {PHASES[i]: s.ms[i] for i in range(7)},
+                "launches": {PHASES[i]: s.launches[i] for i in range(7)},
                 "scan_tile_loads": s.scan_tile_loads, "scan_tile_checks": s.scan_tile_checks}
 
     def info(self) -> dict:
@@ -240,6 +243,19 @@ class Index:
         out = torch.empty((q.shape[0], self.N), dtype=torch.float32, device=q.device)
         _check(load().sofa_lower_bounds(self.h, _ptr(q), q.shape[0], _ptr(out), _stream(stream)))
         return out
+
+
+def mlp_grad(params: torch.Tensor, x: torch.Tensor, y: torch.Tensor, din: int, hidden: int, classes: int,
+             stream=None):
+    """Loss and flat FP32 gradients of the proposal network on one batch."""
+    params = params.contiguous()
+    x = x.contiguous()
+    y = y.to(torch.int32).contiguous()
+    grads = torch.empty_like(params)
+    loss = ctypes.c_float(0.0)
+    _check(load().sofa_mlp_grad(din, hidden, classes, _ptr(params), _ptr(x), _ptr(y), x.shape[0], _ptr(grads),
+                                ctypes.byref(loss), _stream(stream)))
+    return loss.value, grads
 
 
 def znorm(x: torch.Tensor, stream=None) -> torch.Tensor:

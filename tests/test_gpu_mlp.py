@@ -1,0 +1,83 @@
+"""Proposal network: GPU gradients vs the oracle's FP64 backward pass, and
+learned seeding never changes an answer."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sofa_oracle as orc
+from paper_2411_17483_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def sofa():
+    from paper_2411_17483_gb300 import sofa as s
+    s.load()
+    return s
+
+
+def bf16_round(a):
+    return torch.as_tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("din,hidden,classes,B", [(32, 256, 4096, 512), (13, 64, 100, 257), (32, 128, 37, 1000)])
+def test_mlp_gradients_match_oracle(sofa, din, hidden, classes, B):
+    rng = np.random.default_rng(din + classes)
+    shapes = [("W1", (din, hidden)), ("b1", (hidden,)), ("W2", (hidden, hidden)), ("b2", (hidden,)),
+              ("W3", (hidden, classes)), ("b3", (classes,))]
+    params = {}
+    for name, shp in shapes:
+        scale = np.sqrt(6.0 / sum(shp)) if len(shp) == 2 else 0.05
+        params[name] = bf16_round(rng.uniform(-scale, scale, shp))
+    x = bf16_round(rng.standard_normal((B, din)))
+    y = rng.integers(0, classes, B)
+    flat = np.concatenate([params[n].reshape(-1) for n, _ in shapes]).astype(np.float32)
+    loss, grads = sofa.mlp_grad(torch.tensor(flat, device=DEV), torch.tensor(x, dtype=torch.float32, device=DEV),
+                                torch.tensor(y, device=DEV), din, hidden, classes)
+    grads = grads.cpu().numpy().astype(np.float64)
+    oloss, og = orc.mlp_loss_grad(params, x, y)
+    assert abs(loss - oloss) <= 1e-2 * oloss
+    off = 0
+    for name, shp in shapes:
+        sz = int(np.prod(shp))
+        g = grads[off:off + sz].reshape(shp)
+        off += sz
+        err = np.linalg.norm(g - og[name]) / max(np.linalg.norm(og[name]), 1e-30)
+        assert err < 3e-2, (name, err)       # BF16 operands, FP32 accumulation
+
+
+def test_seed_mode_requires_training(sofa):
+    x = datagen.random_walks(5000, 64, seed=3, device=DEV)
+    ix = sofa.Index(x, 8, 256)
+    with pytest.raises(sofa.SofaError) as e:
+        ix.set_seed_mode(1)
+    assert e.value.code == -5
+    ix.close()
+
+
+def test_learned_seed_keeps_answers_exact(sofa):
+    N, n = 200_000, 128
+    x = datagen.random_walks(N, n, seed=7, device=DEV)
+    ix = sofa.Index(x, 16, 256)
+    ix.train_proposal(n_train=40_000, n_classes=256, epochs=3, batch=2048, seed=2, top_m=4)
+    inf = ix.info()
+    assert inf["proposal_classes"] == 256 and inf["proposal_train"] == 40_000
+    assert inf["proposal_topm"] > 4 / 256 * 3           # far better than chance
+    q = datagen.half_perturbed_queries(x, 300, seed=3)
+    ix.set_seed_mode(0)
+    gi0, gd0 = ix.query(q, 5)
+    s0 = ix.stats(reset=True)
+    ix.set_seed_mode(1)
+    gi1, gd1 = ix.query(q, 5)
+    s1 = ix.stats(reset=True)
+    assert torch.equal(gi0, gi1) and torch.equal(gd0, gd1)
+    assert ix.status() == 0
+    z, _, _ = orc.znorm(x.cpu().numpy())
+    zq, _, _ = orc.znorm(q[::10].cpu().numpy())
+    oi, _ = orc.knn(z, zq, 5)
+    assert np.array_equal(gi1[::10].cpu().numpy(), oi)
+    # the learned seed is never worse than the plain seed it extends
+    assert s1["seed_dist_sum"] <= s0["seed_dist_sum"] * (1 + 1e-6)
+    ix.close()
