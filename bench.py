@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--alphabet", type=int, default=256)
     ap.add_argument("--seed-mode", default="chosen", choices=["chosen", "plain", "learned"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--n-train", type=int, default=1 << 20)
+    ap.add_argument("--classes", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -112,10 +114,10 @@ def peaks():
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(x_host_rows, zq, k, N_full, seconds):
-    """Time the oracle's brute-force k-NN over a row sample; scale to N_full."""
+def cpu_oracle_rate(z, zq, k, N_full, seconds):
+    """Time the oracle's brute-force k-NN of canonical queries zq over the
+    canonical row sample z; scale the rate to N_full series."""
     from oracle import sofa_oracle as orc
-    z, _, _ = orc.znorm(x_host_rows)
     done = 0
     t0 = time.perf_counter()
     while True:
@@ -125,7 +127,7 @@ def cpu_oracle_rate(x_host_rows, zq, k, N_full, seconds):
         if (el >= seconds and done >= 2) or done >= zq.shape[0]:
             break
     rate_sample = done / el
-    rate_full = rate_sample * x_host_rows.shape[0] / N_full
+    rate_full = rate_sample * z.shape[0] / N_full
     return rate_full, done, el, orc.num_threads()
 
 
@@ -165,6 +167,7 @@ def run_reference(a, ws, rank):
     q = datagen.random_walks(a.Q, a.n, seed=1, device=dev).cpu().numpy()
     from oracle import sofa_oracle as orc
     zq, _, _ = orc.znorm(q)
+    xs, _, _ = orc.znorm(xs)
     per_step = max(1.0, 60.0 / max(1, a.steps + a.warmup))
     for _ in range(a.warmup):
         cpu_oracle_rate(xs, zq, a.k, a.N, min(per_step, 5.0))
@@ -202,7 +205,7 @@ def run_sofa(a, ws, rank, local):
         cpu_rows = x[: min(a.N, 2_000_000)].cpu().numpy()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    ix = sofa.Index(x, a.l, a.alphabet, sample_ratio=0.1)
+    ix = sofa.Index(x, a.l, a.alphabet, sample_ratio=0.1, precision=1)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     del x
@@ -217,9 +220,24 @@ def run_sofa(a, ws, rank, local):
 
     modes = {"plain": 0}
     chosen = "plain"
+    train = None
+    if a.seed_mode in ("chosen", "learned"):
+        torch.cuda.synchronize()
+        tt0 = time.perf_counter()
+        ix.train_proposal(n_train=a.n_train, n_classes=min(a.classes, a.N), epochs=4, batch=4096, seed=2, top_m=4)
+        torch.cuda.synchronize()
+        inf2 = ix.info()
+        train = {"seconds": round(time.perf_counter() - tt0, 2), "pairs": inf2["proposal_train"],
+                 "classes": inf2["proposal_classes"], "loss": inf2["proposal_loss"],
+                 "heldout_top1": inf2["proposal_top1"], "heldout_top4": inf2["proposal_topm"]}
+        modes["learned"] = 1
+        chosen = "learned"
     results = {}
     for mode_name, mode in modes.items():
+        # plain: FP32 bounds and refinement, key-window seed; chosen: learned
+        # seed and the int8 refinement filter (both exact)
         ix.set_seed_mode(mode)
+        ix.set_tuning(refine_filter=1 if mode_name != "plain" else 0)
         for _ in range(a.warmup):
             ix.query(q, a.k, idx, dist)
         torch.cuda.synchronize()
@@ -268,11 +286,24 @@ def run_sofa(a, ws, rank, local):
         alg_bytes = (a.Q * a.steps * (info["n_leaves"] * 2 * LW + 256 * LW + 32 * a.n * 4)) / launches
     else:
         alg_bytes = None
-    roof = {"kernel": phase, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None,
-            "traffic": None, "peak_kind": peak_kind}
+    hbm = {"kernel": phase, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None,
+           "traffic": None, "peak_kind": peak_kind}
     if alg_bytes is not None and per_launch_s > 0:
         ach = alg_bytes / per_launch_s / 1e9
-        roof.update(achieved=ach, frac=ach / hbm_peak)
+        hbm.update(achieved=ach, frac=ach / hbm_peak)
+    roof = hbm
+    if phase == "scan":
+        # ALU roofline: one (query, series) bound is LW interval distances of 4
+        # FP32 instructions each; peak = SMs x 128 lanes x SM clock / (4 LW)
+        clk = (r["clocks"].get("sm_mhz") or 1920.0) * 1e6
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_b = sms * 128 * clk / (4 * LW) / 1e9
+        bounds = stats["tile_pairs"] * 256 / launches
+        ach_b = bounds / per_launch_s / 1e9
+        roof = {"kernel": "scan", "bound": "alu", "achieved": ach_b, "peak": peak_b,
+                "unit": "G (query, series) bounds/s", "frac": ach_b / peak_b, "traffic": None,
+                "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz / (4 x {LW})",
+                "hbm_view": hbm}
     # whole-step algorithmic bytes (SFA words scanned per query + refined raw series)
     step_bytes = ((stats["tile_pairs"] * 256 * LW) + stats["refined"] * a.n * 4) / a.steps
     step_roof = step_bytes / (r["ms"] / 1e3) / 1e9
@@ -299,7 +330,8 @@ def run_sofa(a, ws, rank, local):
     if cpu_rows is not None:
         from oracle import sofa_oracle as orc
         zq, _, _ = orc.znorm(q[:200].cpu().numpy())
-        rate, done, el, cores = cpu_oracle_rate(cpu_rows, zq, a.k, a.N, a.cpu_seconds)
+        zs, _, _ = orc.znorm(cpu_rows)
+        rate, done, el, cores = cpu_oracle_rate(zs, zq, a.k, a.N, a.cpu_seconds)
         cpu = {"value": rate, "unit": "queries/s", "cores": cores, "kind": "oracle",
                "sample": f"{done} queries brute-forced (FP64) over the first {cpu_rows.shape[0]} of {a.N} series "
                          f"in {el:.1f} s, scaled by {cpu_rows.shape[0]}/{a.N}"}
@@ -310,7 +342,7 @@ def run_sofa(a, ws, rank, local):
             "warmup": a.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "N": a.N, "n": a.n, "Q_per_gpu": a.Q, "k": a.k, "l": a.l,
-                       "alphabet": a.alphabet, "seed_mode": chosen, "precision": "fp32 projection + fp32 refine, fp64 final",
+                       "alphabet": a.alphabet, "seed_mode": chosen, "precision": "chosen: fp32 bounds, int8 refinement filter (derived margin), fp32 refine, fp64 final re-score",
                        "l2": "flushed between timed steps (256 MB write)", "build_s": round(t2 - t1, 3),
                        "gen_s": round(t1 - t0, 3), "parallelism": f"replicas x{ws}"},
             "roofline": roof,
@@ -320,8 +352,14 @@ def run_sofa(a, ws, rank, local):
             "e2e": e2e,
             "clocks": r["clocks"],
             "gpu_launches": int(sum(prof["launches"].values())),
-            "phases_ms_per_step": {k: v / a.steps for k, v in prof["ms"].items()},
-            "pruning": {k: v / a.steps for k, v in stats.items() if k not in ("n_leaves", "n_tiles")},
+            "modes": {m: {"queries_per_s": ws * a.Q / (results[m]["ms"] / 1e3), "ms_per_step": results[m]["ms"],
+                          "seed_over_final_dist": results[m]["stats"]["seed_dist_sum"] /
+                          max(1e-9, results[m]["stats"]["final_dist_sum"]),
+                          "pruning": {k: v / a.steps for k, v in results[m]["stats"].items()
+                                      if k not in ("n_leaves", "n_tiles", "seed_dist_sum", "final_dist_sum")},
+                          "phases_ms_per_step": {k: v / a.steps for k, v in results[m]["prof"]["ms"].items()}}
+                      for m in results},
+            "proposal_training": train,
             "index": {"n_leaves": info["n_leaves"], "n_tiles": info["n_tiles"], "device_GB": info["device_bytes"] / 1e9},
         }
         print(json.dumps(out), flush=True)

@@ -59,8 +59,9 @@ typedef struct {
                            1 first values (classical low-pass SFA)              */
   int32_t pool_coeffs;  /* candidate coefficients k <= pool; 0 = all k <= n/2  */
   int32_t leaf_tiles;   /* tiles of 256 series per leaf block (<= 256); 0 -> 64 */
-  int32_t precision;    /* data-side projection: 0 FP32, 1 FP16 tensor cores
-                           with a derived error margin                          */
+  int32_t precision;    /* 0: FP32 series only; 1: also an int8 copy of every
+                           canonical series with its scale and quantisation
+                           error norm, used by the refinement filter            */
   /* Optional user-supplied summarisation (host pointers), replacing Alg. 1:
      user_sel: value ids in the candidate order (k ascending, real before
      imaginary, Nyquist imaginary part excluded), word values first;
@@ -71,7 +72,7 @@ typedef struct {
 } sofa_build_opts;
 
 /* Index construction (Sec. IV "SOFA index": sample -> learn SFA -> transform
- * all series -> index).  data: N x n fp32 series, host or device memory,
+ * all series -> index).  1 <= N < 2^31.  data: N x n fp32 series, host or device memory,
  * read during the call only and never retained.  l: word length (1..32, at
  * most the number of candidate values); alphabet: 2..256 symbols.
  * The call synchronises `stream` before returning.  Returns NULL on error. */
@@ -136,10 +137,19 @@ int sofa_set_seed_mode(sofa_handle h, int32_t mode);
 /* Run-time tuning knobs (any value keeps answers exact). */
 typedef struct {
   int32_t group;        /* queries per scan work unit (1..64); 0 -> 64         */
-  int32_t cand_cap;     /* candidate slots per query per pass; 0 -> 131072     */
+  int32_t cand_cap;     /* candidate slots reserved per query (the excess goes
+                           to a shared pool); 0 -> 65536                       */
   int32_t seed_count;   /* series refined by the seed; 0 -> 128 (>= k used)    */
   int32_t seed_window;  /* key-sorted series bounded by the seed (power of two
                            <= 4096); 0 -> 4096                                  */
+  int32_t bound_precision; /* series-bound arithmetic: 0 FP32, 1 FP16x2 with a
+                              derived rounding margin on the threshold          */
+  int64_t pool_cap;     /* entries of the shared candidate pool; 0 -> sized for
+                           the batch (at most 2^29).  A full pool is never an
+                           error: the queries concerned are scanned again.      */
+  int32_t refine_filter; /* 1: before its FP32 distance, a candidate is bounded
+                            from its int8 copy (triangle inequality with the
+                            stored quantisation error); needs precision 1      */
 } sofa_tuning;
 int sofa_set_tuning(sofa_handle h, const sofa_tuning* t);
 
@@ -157,6 +167,7 @@ typedef struct {
   int64_t overflow_passes;  /* extra scan passes after a full candidate buffer   */
   int64_t n_leaves;         /* leaf blocks in the index                          */
   int64_t n_tiles;          /* tiles in the index                                */
+  int64_t filtered;         /* candidates read from the int8 copy only           */
   double seed_dist_sum;     /* sum over queries of the seed's k-th distance      */
   double final_dist_sum;    /* sum over queries of the answer's k-th distance    */
 } sofa_stats_t;
@@ -165,7 +176,8 @@ int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset);
 /* Per-phase device time of sofa_query calls made while profiling is on,
  * from CUDA events recorded on the call's stream around each phase: index
  * 0 query transform, 1 seed, 2 routing, 3 series scan, 4 refinement,
- * 5 final re-score, 6 proposal network inference.  launches[i] counts this library's kernel launches per
+ * 5 final re-score, 6 proposal network inference, 7 grouping of the
+ * candidate pool.  launches[i] counts this library's kernel launches per
  * phase (counted whether or not profiling is on); scan_tile_loads counts the
  * (work unit, tile) pairs whose words the scan read. */
 typedef struct {

@@ -97,14 +97,16 @@ static int num_candidates_host(int n, int pool) {
 
 static void free_index(Index* ix) {
   if (!ix) return;
-  void* ptrs[] = {ix->sel, ix->sel_k, ix->sel_part, ix->var, ix->basis, ix->beta, ix->edge, ix->ch,
-                  ix->words, ix->Z, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
+  void* ptrs[] = {ix->sel, ix->sel_k, ix->sel_part, ix->var, ix->basis, ix->beta, ix->edge, ix->ch, ix->ch16,
+                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   DevBuf* bufs[] = {&ix->qs.zq, &ix->qs.qv, &ix->qs.llb, &ix->qs.thr, &ix->qs.list_d, &ix->qs.list_p,
                     &ix->qs.list_n, &ix->qs.leaf_cnt, &ix->qs.leaf_off, &ix->qs.leaf_q, &ix->qs.leaf_cursor,
                     &ix->qs.unit_off, &ix->qs.units, &ix->qs.cand_p, &ix->qs.cand_lb, &ix->qs.cand_n,
-                    &ix->qs.qflag, &ix->qs.qslot, &ix->qs.chunk_d, &ix->qs.chunk_p, &ix->qs.chunk_n, &ix->qs.counters, &ix->qs.stage_in, &ix->qs.stage_out, &ix->qs.pinned_dummy};
+                    &ix->qs.qflag, &ix->qs.qslot, &ix->qs.chunk_d, &ix->qs.chunk_p, &ix->qs.chunk_n, &ix->qs.pool_q, &ix->qs.pool_p, &ix->qs.pool_lb,
+                    &ix->qs.pool_sp, &ix->qs.pool_slb, &ix->qs.qpool_cnt, &ix->qs.qpool_off, &ix->qs.qcursor,
+                    &ix->qs.choff, &ix->qs.chunk_q, &ix->qs.qof, &ix->qs.counters, &ix->qs.stage_in, &ix->qs.stage_out, &ix->qs.pinned_dummy};
   for (DevBuf* b : bufs) b->release();
   if (ix->mlp) mlp_free(ix->mlp);
   ix->prof.release();
@@ -130,7 +132,7 @@ sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, in
     return nullptr;
   };
   if (!data) return bad("data is NULL");
-  if (N < 1 || N >= (int64_t)0xFFFFFFFFll) return bad("N must lie in [1, 2^32-1)");
+  if (N < 1 || N >= ((int64_t)1 << 31)) return bad("N must lie in [1, 2^31)");
   if (n < 4 || n > 1024) return bad("series length n must lie in [4, 1024]");
   const int ncand = num_candidates_host(n, o.pool_coeffs);
   if (l < 1 || l > SOFA_MAX_WORD || l > ncand) return bad("word length l must lie in [1, min(32, candidate values)]");
@@ -138,7 +140,7 @@ sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, in
   if (o.sample_ratio < 0.f || o.sample_ratio > 1.f) return bad("sample_ratio must lie in [0, 1]");
   if (o.binning < 0 || o.binning > 1) return bad("binning must be 0 or 1");
   if (o.select < 0 || o.select > 1) return bad("select must be 0 or 1");
-  if (o.precision != 0) return bad("precision: only 0 (FP32 projection) is available");
+  if (o.precision < 0 || o.precision > 1) return bad("precision must be 0 or 1");
   if (o.leaf_tiles < 0 || o.leaf_tiles > 256) return bad("leaf_tiles must lie in [0, 256]");
   if (o.user_sel) {
     if (o.user_nsel < l || o.user_nsel > 2 * l) return bad("user_nsel must lie in [l, 2l]");
@@ -239,7 +241,7 @@ int sofa_query_status(sofa_handle h) {
 
 int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset) {
   if (!h || !out) return fail(SOFA_ERR_INVALID_ARG, "null argument");
-  unsigned long long c[8] = {0};
+  unsigned long long c[16] = {0};
   if (h->qs.counters.p) SOFA_CUDA(cudaMemcpy(c, h->qs.counters.p, sizeof(c), cudaMemcpyDeviceToHost));
   out->queries = h->stats[0];
   out->leaf_pairs = (int64_t)c[0];
@@ -247,6 +249,7 @@ int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset) {
   out->candidates = (int64_t)c[2];
   out->refined = (int64_t)c[3];
   out->overflow_passes = h->stats[5];
+  out->filtered = (int64_t)c[12];
   out->seed_dist_sum = (double)c[6] * 1e-6;
   out->final_dist_sum = (double)c[7] * 1e-6;
   out->n_leaves = h->L;
@@ -255,6 +258,7 @@ int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset) {
     if (h->qs.counters.p) {
       SOFA_CUDA(cudaMemset(h->qs.counters.p, 0, 4 * sizeof(unsigned long long)));
       SOFA_CUDA(cudaMemset(h->qs.counters.as<unsigned long long>() + 6, 0, 2 * sizeof(unsigned long long)));
+      SOFA_CUDA(cudaMemset(h->qs.counters.as<unsigned long long>() + 12, 0, sizeof(unsigned long long)));
     }
     h->stats[0] = 0;
     h->stats[5] = 0;
@@ -269,10 +273,17 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   if (t->seed_count < 0 || t->seed_count > TILE) return fail(SOFA_ERR_INVALID_ARG, "seed_count must lie in [0, 256]");
   if (t->seed_window < 0 || t->seed_window > SEED_MAX || (t->seed_window & (t->seed_window - 1)))
     return fail(SOFA_ERR_INVALID_ARG, "seed_window must be 0 or a power of two <= 4096");
+  if (t->bound_precision < 0 || t->bound_precision > 1) return fail(SOFA_ERR_INVALID_ARG, "bound_precision must be 0 or 1");
+  if (t->pool_cap < 0 || t->pool_cap > ((int64_t)1 << 30)) return fail(SOFA_ERR_INVALID_ARG, "pool_cap must lie in [0, 2^30]");
+  if (t->refine_filter < 0 || t->refine_filter > 1) return fail(SOFA_ERR_INVALID_ARG, "refine_filter must be 0 or 1");
+  if (t->refine_filter == 1 && !h->Z8) return fail(SOFA_ERR_INVALID_ARG, "refine_filter needs an index built with precision 1");
   h->group = t->group ? t->group : 64;
-  h->cand_cap = t->cand_cap ? t->cand_cap : 131072;
+  h->cand_cap = t->cand_cap ? t->cand_cap : 65536;
   h->seed_count = t->seed_count ? t->seed_count : 128;
   h->seed_window = t->seed_window ? t->seed_window : 4096;
+  h->bound_precision = t->bound_precision;
+  h->pool_cap = t->pool_cap;
+  h->refine_filter = t->refine_filter;
   return 0;
 }
 

@@ -383,8 +383,13 @@ __global__ void k_bins(const float* __restrict__ sorted, int64_t S, int l, int a
 // the same interval as (centre, half-width), the half-width rounded up and
 // widened by eps_abs to absorb the rounding of |q - centre|.  Unused dims and
 // symbols get an interval that never contributes.
+// ch16[j][s] holds the same interval for the FP16 bound as (centre, -half
+// width) in half precision: the centre rounded to nearest, the half-width
+// widened by 4 u16 outer (rounding of the centre, of the query value and of
+// q - c, u16 = 2^-11) and rounded up.
 __global__ void k_tables(const float* __restrict__ beta, int l, int LW, int alpha, float delta, float outer,
-                         float eps_abs, float2* __restrict__ edge, float2* __restrict__ ch) {
+                         float eps_abs, float2* __restrict__ edge, float2* __restrict__ ch,
+                         __half2* __restrict__ ch16) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= LW * MAX_ALPHA) return;
   int j = e / MAX_ALPHA, s = e % MAX_ALPHA;
@@ -392,6 +397,7 @@ __global__ void k_tables(const float* __restrict__ beta, int l, int LW, int alph
   if (j >= l || s >= alpha) {
     edge[e] = make_float2(-BIG, BIG);
     ch[e] = make_float2(0.f, BIG);
+    ch16[e] = __halves2half2(__float2half_rn(0.f), __float2half_rn(-60000.f));
     return;
   }
   const float* bj = beta + (int64_t)j * (alpha + 1);
@@ -404,6 +410,12 @@ __global__ void k_tables(const float* __restrict__ beta, int l, int LW, int alph
   float c = 0.5f * (lo + hi);
   float h = fmaxf(__fsub_ru(c, lo), __fsub_ru(hi, c));
   ch[e] = make_float2(c, __fadd_ru(h, eps_abs));
+  const __half c16 = __float2half_rn(c);
+  const float cerr = fabsf(__half2float(c16) - c);
+  const float u16 = 1.0f / 2048.0f;
+  const float h16 = __fadd_ru(__fadd_ru(h, cerr), 4.0f * u16 * outer);
+  __half hh = __float2half_ru(h16);
+  ch16[e] = __halves2half2(c16, __hneg(hh));
 }
 
 // Key-sorted layout: Z[p] = canonical z-normalisation of data row perm[p]
@@ -423,6 +435,36 @@ __global__ void k_layout(const float* __restrict__ x, int64_t N, int n, const ui
   if (lane < LW / 16)
     reinterpret_cast<uint4*>(words_out + p * LW)[lane] =
         reinterpret_cast<const uint4*>(words_in + (int64_t)o * LW)[lane];
+}
+
+// Int8 copy of every key-sorted canonical series for the refinement filter:
+// scale s = max|z| / 127 (1 for the zero series), v_t = rint(z_t / s) in
+// [-127, 127], and the residual norm e = ||z - s v|| (every term exact in
+// FP64: s v_t has at most 32 significant bits), rounded up to fp32 with a
+// 1e-6 relative cushion.  Warp per series.
+__global__ void k_quant8(const float* __restrict__ Z, int64_t N, int n, int8_t* __restrict__ Z8,
+                         float* __restrict__ scale, float* __restrict__ err) {
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= N) return;
+  const float* z = Z + p * n;
+  float mx = 0.f;
+  for (int t = lane; t < n; t += 32) mx = fmaxf(mx, fabsf(z[t]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  const float sc = mx > 0.f ? mx / 127.0f : 1.0f;
+  double e2 = 0.0;
+  for (int t = lane; t < n; t += 32) {
+    float v = rintf(z[t] / sc);
+    v = fminf(fmaxf(v, -127.f), 127.f);
+    Z8[p * n + t] = (int8_t)v;
+    const double d = (double)z[t] - (double)sc * (double)v;
+    e2 += d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, o);
+  if (lane == 0) {
+    scale[p] = sc;
+    err[p] = __double2float_ru(sqrt(e2) * (1.0 + 1e-6) + 1e-30);
+  }
 }
 
 // Symbol envelope (per word value min and max symbol) of each tile of 256
@@ -640,8 +682,10 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
   const float eps_abs = (float)(4.0 * u * (outer + 1.0));
   TRY(dalloc(&ix->edge, (int64_t)LW * MAX_ALPHA, acct));
   TRY(dalloc(&ix->ch, (int64_t)LW * MAX_ALPHA, acct));
+  TRY(dalloc(&ix->ch16, (int64_t)LW * MAX_ALPHA, acct));
   k_tables<<<(unsigned)ceil_div(LW * MAX_ALPHA, 256), 256, 0, st>>>(ix->beta, l, LW, alpha, delta, outer, eps_abs,
-                                                                     ix->edge, ix->ch);
+                                                                     ix->edge, ix->ch, ix->ch16);
+  ix->outer = outer;
   SOFA_CUDA(cudaGetLastError());
 
   // ---- key bit order
@@ -702,6 +746,15 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
       k_layout<16><<<blocks, 256, 0, st>>>(x, N, n, ix->perm, stats, words0, ix->Z, ix->words);
     else
       k_layout<32><<<blocks, 256, 0, st>>>(x, N, n, ix->perm, stats, words0, ix->Z, ix->words);
+    SOFA_CUDA(cudaGetLastError());
+  }
+
+  // ---- int8 copy for the refinement filter (optional)
+  if (o.precision == 1) {
+    TRY(dalloc(&ix->Z8, N * n, acct));
+    TRY(dalloc(&ix->s8, N, acct));
+    TRY(dalloc(&ix->e8, N, acct));
+    k_quant8<<<(unsigned)ceil_div(N * 32, 256), 256, 0, st>>>(ix->Z, N, n, ix->Z8, ix->s8, ix->e8);
     SOFA_CUDA(cudaGetLastError());
   }
 

@@ -120,6 +120,39 @@ __device__ __forceinline__ float group4_sqdist(const float* __restrict__ zq, con
   return acc;
 }
 
+// FP32 squared distance between the canonical query and the int8 copy of
+// series p, by one thread (a 256-value row is 16 consecutive 16-byte loads).
+// The copy's values s * v_t are exact reals and fmaf(-s, v, q) rounds once.
+__device__ __forceinline__ float thread_sqdist8(const float* __restrict__ zq, const int8_t* __restrict__ Z8, float sc,
+                                                int64_t p, int n) {
+  const int8_t* row = Z8 + p * n;
+  float a0 = 0.f, a1 = 0.f;
+  if ((n & 15) == 0) {
+    const uint4* r4 = reinterpret_cast<const uint4*>(row);
+    for (int i = 0; i < n / 16; ++i) {
+      const uint4 w = __ldg(r4 + i);
+      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int j = 0; j < 4; j += 2) {
+          const float v0 = (float)((int)(ws[b] << (24 - 8 * j)) >> 24);
+          const float v1 = (float)((int)(ws[b] << (16 - 8 * j)) >> 24);
+          const float d0 = fmaf(-sc, v0, zq[16 * i + 4 * b + j]);
+          const float d1 = fmaf(-sc, v1, zq[16 * i + 4 * b + j + 1]);
+          a0 = fmaf(d0, d0, a0);
+          a1 = fmaf(d1, d1, a1);
+        }
+    }
+  } else {
+    for (int t = 0; t < n; ++t) {
+      const float d = fmaf(-sc, (float)row[t], zq[t]);
+      a0 = fmaf(d, d, a0);
+    }
+  }
+  return a0 + a1;
+}
+
 // Bitonic sort of `len` (power of two) 64-bit keys in shared memory by the
 // whole block.
 __device__ inline void block_bitonic(unsigned long long* key, int len) {
@@ -436,25 +469,31 @@ __global__ void k_units(int64_t L, int group, const int* __restrict__ leaf_cnt, 
 // chunked early abandoning).  Survivors are appended to the query's candidate
 // buffer with warp-aggregated atomics.
 constexpr int MAX_LEAF_TILES = 256;
-template <int LW, bool NYQ>
+template <int LW, bool NYQ, bool H16>
 __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restrict__ units,
                                               const int* __restrict__ n_units_ptr, const int* __restrict__ leaf_q,
                                               const float* __restrict__ qv, const float* __restrict__ thr,
                                               const uint8_t* __restrict__ tenv, const uint8_t* __restrict__ words,
                                               const float2* __restrict__ edge, const float2* __restrict__ ch,
+                                              const __half2* __restrict__ ch16, float f16, float inv_f16,
                                               const int* __restrict__ qslot, uint32_t* __restrict__ cand_p,
                                               float* __restrict__ cand_lb, int* __restrict__ cand_n,
-                                              unsigned long long* __restrict__ counters) {
+                                              int64_t pool_cap, int* __restrict__ pool_n, int* __restrict__ pool_q,
+                                              uint32_t* __restrict__ pool_p, float* __restrict__ pool_lb,
+                                              int* __restrict__ qpool_cnt, unsigned long long* __restrict__ counters) {
   extern __shared__ float2 tabs[];
-  float2* sch = tabs;                     // LW x 256
-  float2* sedge = tabs + LW * MAX_ALPHA;  // LW x 256
+  float2* sedge = tabs;                                                 // LW x 256
+  float2* sch = tabs + LW * MAX_ALPHA;                                  // LW x 256 (FP32 mode)
+  __half2* sch16 = reinterpret_cast<__half2*>(tabs + LW * MAX_ALPHA);   // LW x 256 (FP16 mode)
   __shared__ __align__(16) float sq[MAX_GROUP][LW];
+  __shared__ __align__(16) __half2 sq16[MAX_GROUP][LW / 2];
   __shared__ float sT[MAX_GROUP];
   __shared__ int sslot[MAX_GROUP];
   __shared__ unsigned long long smask[MAX_LEAF_TILES];
   const int tid = threadIdx.x, lane = tid & 31;
   for (int e = tid; e < LW * MAX_ALPHA; e += blockDim.x) {
-    sch[e] = ch[e];
+    if (H16) sch16[e] = ch16[e];
+    else sch[e] = ch[e];
     sedge[e] = edge[e];
   }
   unsigned long long n_tile_pairs = 0, n_cand = 0, n_loads = 0, n_checks = 0;
@@ -470,6 +509,8 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
       int g = e / LW, j = e - g * LW;
       int qq = leaf_q[un.y + g];
       sq[g][j] = qv[(int64_t)qq * P.NB + j];
+      if (H16 && (j & 1) == 0)
+        sq16[g][j >> 1] = __floats2half2_rn(qv[(int64_t)qq * P.NB + j], qv[(int64_t)qq * P.NB + j + 1]);
       if (j == 0) {
         sslot[g] = qslot ? qslot[qq] : qq;
         sT[g] = thr[qq];
@@ -494,44 +535,117 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
       }
       const int64_t p = (t0 + t) * TILE + tid;
       const bool valid = p < P.N;
-      float c[LW], h[LW];
-      load_word_bounds<LW>(words, p, valid, sch, c, h);
+      float c[H16 ? 1 : LW], h[H16 ? 1 : LW];
+      __half2 c2[H16 ? LW / 2 : 1], nh2[H16 ? LW / 2 : 1];
+      if constexpr (H16) {
+        // gather (c, -h) of each value, then pair values 2i, 2i+1 per register
+        uint32_t w32[LW / 4];
+        if (valid) {
+          const uint4* wp = reinterpret_cast<const uint4*>(words + p * LW);
+#pragma unroll
+          for (int i = 0; i < LW / 16; ++i) {
+            uint4 v = __ldg(wp + i);
+            w32[4 * i] = v.x;
+            w32[4 * i + 1] = v.y;
+            w32[4 * i + 2] = v.z;
+            w32[4 * i + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < LW / 4; ++i) w32[i] = 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < LW / 2; ++i) {
+          const int j0 = 2 * i, j1 = 2 * i + 1;
+          const __half2 v0 = sch16[j0 * MAX_ALPHA + ((w32[j0 >> 2] >> (8 * (j0 & 3))) & 0xFFu)];
+          const __half2 v1 = sch16[j1 * MAX_ALPHA + ((w32[j1 >> 2] >> (8 * (j1 & 3))) & 0xFFu)];
+          c2[i] = __lows2half2(v0, v1);
+          nh2[i] = __highs2half2(v0, v1);
+        }
+      } else {
+        load_word_bounds<LW>(words, p, valid, sch, c, h);
+      }
       while (m) {
         const int g = __ffsll((long long)m) - 1;
         m &= m - 1;
-        const float T = sT[g];
-        const float* qg = sq[g];
-        // two partial sums (even / odd values) halve the dependent FMA chain;
-        // the warp votes after 4, 8, 16 (and 32) values
-        float a0 = 0.f, a1 = 0.f;
+        const float T = H16 ? sT[g] * f16 : sT[g];
         bool live = valid;
+        float acc;
+        if constexpr (H16) {
+          // m = relu(|q - c| - h) by one fused multiply-add with relu, then
+          // m^2 accumulated in two half lanes (even / odd values)
+          const __half2* qg = sq16[g];
+          const __half2 one2 = __floats2half2_rn(1.f, 1.f);
+          __half2 a2 = __floats2half2_rn(0.f, 0.f);
 #pragma unroll
-        for (int stage = 0; stage < 8; ++stage) {
-          const int j0 = stage == 0 ? 0 : (4 << (stage - 1));
-          const int j1 = 4 << stage;
-          if (j0 >= LW) break;
-          if (!__any_sync(0xFFFFFFFFu, live)) break;
+          for (int stage = 0; stage < 8; ++stage) {
+            const int i0 = stage == 0 ? 0 : (2 << (stage - 1));
+            const int i1 = 2 << stage;
+            if (i0 >= LW / 2) break;
+            if (!__any_sync(0xFFFFFFFFu, live)) break;
 #pragma unroll
-          for (int j = j0; j < j1 && j < LW; j += 2) {
-            const float m0 = fmaxf(fabsf(qg[j] - c[j]) - h[j], 0.f);
-            const float m1 = fmaxf(fabsf(qg[j + 1] - c[j + 1]) - h[j + 1], 0.f);
-            a0 = fmaf((NYQ && j == 0) ? 0.5f * m0 : m0, m0, a0);
-            a1 = fmaf(m1, m1, a1);
+            for (int i = i0; i < i1 && i < LW / 2; ++i) {
+              const __half2 d = __habs2(__hsub2(qg[i], c2[i]));
+              const __half2 mv = __hfma2_relu(d, one2, nh2[i]);
+              const __half2 mm = (NYQ && i == 0) ? __hmul2(mv, __floats2half2_rn(0.5f, 1.f)) : mv;
+              a2 = __hfma2(mm, mv, a2);
+            }
+            const float2 af = __half22float2(a2);
+            live = live && (af.x + af.y) <= T;
           }
-          live = live && (a0 + a1) <= T;
+          const float2 af = __half22float2(a2);
+          acc = __fmul_rd(af.x + af.y, inv_f16);  // deflated: a lower bound in exact units
+        } else {
+          const float* qg = sq[g];
+          // two partial sums (even / odd values) halve the dependent FMA chain;
+          // the warp votes after 4, 8, 16 (and 32) values
+          float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+          for (int stage = 0; stage < 8; ++stage) {
+            const int j0 = stage == 0 ? 0 : (4 << (stage - 1));
+            const int j1 = 4 << stage;
+            if (j0 >= LW) break;
+            if (!__any_sync(0xFFFFFFFFu, live)) break;
+#pragma unroll
+            for (int j = j0; j < j1 && j < LW; j += 2) {
+              const float m0 = fmaxf(fabsf(qg[j] - c[j]) - h[j], 0.f);
+              const float m1 = fmaxf(fabsf(qg[j + 1] - c[j + 1]) - h[j + 1], 0.f);
+              a0 = fmaf((NYQ && j == 0) ? 0.5f * m0 : m0, m0, a0);
+              a1 = fmaf(m1, m1, a1);
+            }
+            live = live && (a0 + a1) <= T;
+          }
+          acc = a0 + a1;
         }
-        const float acc = a0 + a1;
         const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
         if (hit) {
           const int qs = sslot[g];
-          int base = 0;
-          if (lane == 0) base = atomicAdd(cand_n + qs, __popc(hit));
+          const int npop = __popc(hit);
+          int base = 0, pbase = 0;
+          if (lane == 0) base = atomicAdd(cand_n + qs, npop);
           base = __shfl_sync(0xFFFFFFFFu, base, 0);
+          // slots beyond the query's region go to the shared pool
+          const int over0 = base > P.cap ? base : P.cap;
+          const int nover = base + npop - over0;
+          if (lane == 0 && nover > 0) {
+            pbase = atomicAdd(pool_n, nover);
+            const int64_t room = pool_cap - pbase;
+            const int written = room <= 0 ? 0 : (room < nover ? (int)room : nover);
+            if (written > 0) atomicAdd(qpool_cnt + qs, written);
+          }
+          pbase = __shfl_sync(0xFFFFFFFFu, pbase, 0);
           if (live) {
             const int slot = base + __popc(hit & ((1u << lane) - 1u));
             if (slot < P.cap) {
               cand_p[(int64_t)qs * P.cap + slot] = (uint32_t)p;
               cand_lb[(int64_t)qs * P.cap + slot] = acc;
+            } else {
+              const int64_t pi = (int64_t)pbase + (slot - over0);
+              if (pi < pool_cap) {
+                pool_q[pi] = qs;
+                pool_p[pi] = (uint32_t)p;
+                pool_lb[pi] = acc;
+              }
             }
           }
           if (lane == 0) n_cand += __popc(hit);
@@ -546,6 +660,87 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
 }
 
 // ------------------------------------------------------------------------
+// Candidate store: each query slot has a region of P.cap entries; the excess
+// of a pass goes to a shared pool of (slot, position, bound) triples.  After
+// the scan one CTA plans the refinement: per slot, r = min(count, cap) region
+// entries plus pool_cnt pool entries, cut into chunks of RSORT; exclusive
+// scans give each slot its pool segment and its first chunk, and the chunk
+// total goes to the device (the refinement is persistent and reads it).
+constexpr int RSORT = 4096;
+__global__ void __launch_bounds__(1024) k_chunk_plan(int64_t slots, int cap, const int* __restrict__ cand_n,
+                                                     const int* __restrict__ qpool_cnt, int* __restrict__ qpool_off,
+                                                     int* __restrict__ qcursor, int* __restrict__ choff,
+                                                     int* __restrict__ n_chunks) {
+  __shared__ long long s1[1024], s2[1024];
+  const int tid = threadIdx.x;
+  const int64_t per = (slots + 1023) / 1024;
+  const int64_t a0 = tid * per, a1 = a0 + per < slots ? a0 + per : slots;
+  long long pc = 0, nc = 0;
+  for (int64_t q = a0; q < a1; ++q) {
+    const int r = cand_n[q] < cap ? cand_n[q] : cap;
+    pc += qpool_cnt[q];
+    nc += (r + qpool_cnt[q] + RSORT - 1) / RSORT;
+  }
+  s1[tid] = pc;
+  s2[tid] = nc;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const long long x1 = tid >= o ? s1[tid - o] : 0, x2 = tid >= o ? s2[tid - o] : 0;
+    __syncthreads();
+    s1[tid] += x1;
+    s2[tid] += x2;
+    __syncthreads();
+  }
+  long long rp = s1[tid] - pc, rc = s2[tid] - nc;
+  for (int64_t q = a0; q < a1; ++q) {
+    const int r = cand_n[q] < cap ? cand_n[q] : cap;
+    qpool_off[q] = (int)rp;
+    choff[q] = (int)rc;
+    qcursor[q] = 0;
+    rp += qpool_cnt[q];
+    rc += (r + qpool_cnt[q] + RSORT - 1) / RSORT;
+  }
+  if (tid == 1023) *n_chunks = (int)s2[1023];
+}
+
+// Counting-sort scatter of the pool into per-slot segments (grid-stride).
+__global__ void k_pool_scatter(const int* __restrict__ pool_n, int64_t pool_cap, const int* __restrict__ pool_q,
+                               const uint32_t* __restrict__ pool_p, const float* __restrict__ pool_lb,
+                               const int* __restrict__ qpool_off, int* __restrict__ qcursor,
+                               uint32_t* __restrict__ sp, float* __restrict__ slb) {
+  const int64_t n = *pool_n < pool_cap ? *pool_n : pool_cap;
+  const int lane = threadIdx.x & 31;
+  // the scan wrote each query's entries in runs: lanes with the same query
+  // share one atomic (warp-uniform loop bounds keep every lane in the vote)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool ok = i < n;
+    const int q = ok ? pool_q[i] : -1;
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, q);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (ok && lane == leader) base = atomicAdd(qcursor + q, __popc(grp));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (ok) {
+      const int pos = base + __popc(grp & ((1u << lane) - 1u));
+      sp[qpool_off[q] + pos] = pool_p[i];
+      slb[qpool_off[q] + pos] = pool_lb[i];
+    }
+  }
+}
+
+// Chunk list: chunk_q[choff[s] + c] = s for every chunk c of slot s.
+__global__ void k_chunk_fill(int64_t slots, int cap, const int* __restrict__ cand_n, const int* __restrict__ qpool_cnt,
+                             const int* __restrict__ choff, int* __restrict__ chunk_q) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= slots) return;
+  const int r = cand_n[q] < cap ? cand_n[q] : cap;
+  const int nch = (r + qpool_cnt[q] + RSORT - 1) / RSORT;
+  for (int c = 0; c < nch; ++c) chunk_q[choff[q] + c] = (int)q;
+}
+
+// ------------------------------------------------------------------------
 // Refinement (GEMINI's exact distance for the survivors of the bound, Sec.
 // II-A, visited in ascending bound order as in Sec. IV "Exact Similarity
 // Search").  Every chunk of RSORT candidates of a query gets its own CTA:
@@ -556,15 +751,19 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
 // (a real k-th distance of k distinct series, hence a valid bound), and each
 // round reads the current value, so all chunks of a query tighten together.
 // The first candidate whose bound exceeds the threshold ends the chunk.
-constexpr int RSORT = 4096;
 constexpr int RROUND = 64;  // candidates refined per round: 8 warps x 8 groups of 4 lanes
-__global__ void __launch_bounds__(256) k_refine(QueryParams P, int nchunk, const int* __restrict__ qsel,
-                                                const int* __restrict__ qslot,
-                                                const float* __restrict__ zq, const float* __restrict__ Z,
-                                                const uint32_t* __restrict__ cand_p,
+template <bool FILTER>
+__global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __restrict__ n_chunks_ptr,
+                                                const int* __restrict__ chunk_q, const int* __restrict__ choff,
+                                                const int* __restrict__ qof, const float* __restrict__ zq,
+                                                const float* __restrict__ Z, const uint32_t* __restrict__ cand_p,
                                                 const float* __restrict__ cand_lb, const int* __restrict__ cand_n,
+                                                const int* __restrict__ qpool_cnt, const int* __restrict__ qpool_off,
+                                                const uint32_t* __restrict__ sp, const float* __restrict__ slb,
                                                 float* __restrict__ thr, float* __restrict__ chunk_d,
                                                 uint32_t* __restrict__ chunk_p, int* __restrict__ chunk_n,
+                                                const int8_t* __restrict__ Z8, const float* __restrict__ s8,
+                                                const float* __restrict__ e8, float one_minus_g,
                                                 unsigned long long* __restrict__ counters, int* __restrict__ status) {
   extern __shared__ float4 rsm[];
   float* szq = reinterpret_cast<float*>(rsm);  // n
@@ -573,109 +772,242 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, int nchunk, const
   __shared__ uint32_t slp[KCAP];
   __shared__ float acc_d[RROUND];
   __shared__ uint32_t acc_p[RROUND];
-  __shared__ int s_nacc, s_nl, s_stop, s_lost;
-  __shared__ float s_lim;
-  const int64_t q = blockIdx.x / nchunk;
-  const int c = blockIdx.x - (int)(q * nchunk);
+  __shared__ int s_nacc, s_nl, s_stop, s_lost, s_nsurv;
+  __shared__ float s_lim, s_T0;
+  __shared__ uint32_t surv[FILTER ? 256 : 1];
+  constexpr int NBK = 32;  // bound buckets of a chunk
+  __shared__ int bcnt[NBK + 1], bcur[NBK + 1];
+  __shared__ uint16_t ord[RSORT];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (qsel && !qsel[q]) return;
-  const int64_t slot_q = qslot ? qslot[q] : q;
-  const int all = cand_n[slot_q];
-  const int cnt = all < P.cap ? all : P.cap;
+  unsigned long long refined = 0, filtered = 0;
+  const int n_chunks = *n_chunks_ptr;
+  for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+  __syncthreads();
+  const int slot_q = chunk_q[ch];
+  const int c = ch - choff[slot_q];
+  const int64_t q = qof ? qof[slot_q] : slot_q;
+  const int r = cand_n[slot_q] < P.cap ? cand_n[slot_q] : P.cap;
+  const int total = r + qpool_cnt[slot_q];
   const int c0 = c * RSORT;
-  int* const out_n = chunk_n + slot_q * nchunk + c;
-  if (c0 >= cnt) {
-    if (tid == 0) *out_n = 0;
-    return;
-  }
-  const int cc = cnt - c0 < RSORT ? cnt - c0 : RSORT;
+  const int cc = total - c0 < RSORT ? total - c0 : RSORT;
   for (int t = tid; t < P.n; t += blockDim.x) szq[t] = zq[q * P.n + t];
-  int pw = 1;
-  while (pw < cc) pw <<= 1;
-  for (int i = tid; i < pw; i += blockDim.x)
-    skey[i] = i < cc ? pack_key(cand_lb[slot_q * P.cap + c0 + i], cand_p[slot_q * P.cap + c0 + i]) : ~0ull;
+  volatile float* vthr = thr;
   if (tid == 0) {
     s_nl = 0;
     s_stop = 0;
     s_lost = 0;
     s_lim = INFINITY;
     s_nacc = 0;
+    s_T0 = vthr[q];
   }
-  block_bitonic(skey, pw);
-  volatile float* vthr = thr;
-  unsigned long long refined = 0;
-  for (int base = 0; base < cc; base += RROUND) {
-    const int slot = warp * 8 + (lane >> 2);
-    const int i = base + slot;
-    const float T = vthr[q];
-    bool active = false;
-    uint32_t p = 0xFFFFFFFFu;
-    if (i < cc) {
-      const float lb = __uint_as_float((uint32_t)(skey[i] >> 32));
-      active = lb <= T;
-      if (active) p = (uint32_t)skey[i];
+  for (int i = tid; i <= NBK; i += blockDim.x) bcnt[i] = 0;
+  __syncthreads();
+  // coarse ascending-bound order by a counting sort into NBK buckets of width
+  // T0 / NBK (T0 = the threshold now); bounds above T0 can never pass and are
+  // dropped, so no full sort is needed for the early stop below
+  const float T0 = s_T0;
+  const float bscale = T0 > 0.f ? (float)NBK / T0 : 0.f;
+  for (int i = tid; i < cc; i += blockDim.x) {
+    const int e = c0 + i;
+    unsigned long long kk;
+    if (e < r) kk = pack_key(cand_lb[(int64_t)slot_q * P.cap + e], cand_p[(int64_t)slot_q * P.cap + e]);
+    else kk = pack_key(slb[qpool_off[slot_q] + (e - r)], sp[qpool_off[slot_q] + (e - r)]);
+    skey[i] = kk;
+    const float lb = __uint_as_float((uint32_t)(kk >> 32));
+    const int b = lb <= T0 ? min(NBK - 1, (int)(lb * bscale)) : NBK;
+    atomicAdd(&bcnt[b], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int b = 0; b <= NBK; ++b) {
+      const int c_ = bcnt[b];
+      bcnt[b] = acc;  // bucket start
+      bcur[b] = acc;
+      acc += c_;
     }
-    if (tid == 0 && __uint_as_float((uint32_t)(skey[base] >> 32)) > T) s_stop = 1;  // sorted: the rest exceeds T
-    const float d2 = group4_sqdist(szq, Z, p, P.n, lane & 3, active);
-    if ((lane & 3) == 0 && active) {
-      ++refined;
-      if (d2 <= s_lim) {  // a candidate for the local kept list
-        const int a = atomicAdd(&s_nacc, 1);
-        acc_d[a] = d2;
-        acc_p[a] = p;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      int nl = s_nl;
-      float lim = s_lim;
-      const int na = s_nacc;
-      for (int w = 0; w < na; ++w) {
-        const float d = acc_d[w];
-        const uint32_t pp = acc_p[w];
-        if (!(d <= lim)) continue;
-        int j = nl - 1;  // insertion by (d2, pos)
-        while (j >= 0 && (sld[j] > d || (sld[j] == d && slp[j] > pp))) {
-          if (j + 1 < KCAP) {
-            sld[j + 1] = sld[j];
-            slp[j + 1] = slp[j];
-          }
-          --j;
-        }
+  }
+  __syncthreads();
+  for (int i = tid; i < cc; i += blockDim.x) {
+    const float lb = __uint_as_float((uint32_t)(skey[i] >> 32));
+    const int b = lb <= T0 ? min(NBK - 1, (int)(lb * bscale)) : NBK;
+    if (b < NBK) ord[atomicAdd(&bcur[b], 1)] = (uint16_t)i;
+  }
+  __syncthreads();
+  const int nlive = bcnt[NBK];  // candidates with bound <= T0, bucket-ordered in ord
+  // a lower bound of every bound at ordered positions >= j: the edge of the
+  // bucket below the one holding j (the bucket index was rounded, so a bound
+  // may sit a hair under its own bucket's edge, never under the previous one's)
+  auto edge_of = [&](int j) {
+    int b = 0;
+    while (b + 1 < NBK && bcnt[b + 1] <= j) ++b;
+    return b > 0 ? (float)(b - 1) / bscale : 0.f;
+  };
+  // thread 0: merge the accepted distances of a round into the chunk's kept
+  // list, tighten its window and publish the query's threshold
+  auto merge_round = [&]() {
+    int nl = s_nl;
+    float lim = s_lim;
+    const int na = s_nacc;
+    for (int w = 0; w < na; ++w) {
+      const float d = acc_d[w];
+      const uint32_t pp = acc_p[w];
+      if (!(d <= lim)) continue;
+      int j = nl - 1;  // insertion by (d2, pos)
+      while (j >= 0 && (sld[j] > d || (sld[j] == d && slp[j] > pp))) {
         if (j + 1 < KCAP) {
-          sld[j + 1] = d;
-          slp[j + 1] = pp;
+          sld[j + 1] = sld[j];
+          slp[j + 1] = slp[j];
         }
-        if (nl < KCAP) ++nl;
-        else s_lost = 1;
-        if (nl >= P.k) {
-          lim = __fmul_ru(sld[P.k - 1], P.f_keep);
-          while (nl > P.k && sld[nl - 1] > lim) --nl;  // drop entries that left the window
-        }
+        --j;
       }
-      s_nacc = 0;
-      s_nl = nl;
-      s_lim = lim;
+      if (j + 1 < KCAP) {
+        sld[j + 1] = d;
+        slp[j + 1] = pp;
+      }
+      if (nl < KCAP) ++nl;
+      else s_lost = 1;
       if (nl >= P.k) {
-        const float t = __fmul_ru(__fmul_ru(sld[P.k - 1], P.f_prune), 0.5f);
-        atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(t));  // t >= 0: int order = float order
+        lim = __fmul_ru(sld[P.k - 1], P.f_keep);
+        while (nl > P.k && sld[nl - 1] > lim) --nl;  // drop entries that left the window
       }
     }
-    __syncthreads();
-    if (s_stop) break;
+    s_nacc = 0;
+    s_nl = nl;
+    s_lim = lim;
+    if (nl >= P.k) {
+      const float t = __fmul_ru(__fmul_ru(sld[P.k - 1], P.f_prune), 0.5f);
+      atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(t));  // t >= 0: int order = float order
+    }
+  };
+  if constexpr (FILTER) {
+    // rounds of 256 candidates, one per thread: the int8 bound
+    // d(q, x) >= d(q, s v) - e (2 T is the squared distance bound, T in half
+    // units); only survivors get the FP32 distance, by groups of 4 lanes
+    for (int base = 0; base < nlive; base += 256) {
+      const float T = vthr[q];
+      if (tid == 0) {
+        s_nsurv = 0;
+        if (edge_of(base) > T) s_stop = 1;  // every later bucket starts above T
+      }
+      __syncthreads();
+      if ((P.n & 15) == 0) {
+        // 16 lanes per candidate row: lane `sub` reads 16-byte pieces sub,
+        // sub + 16, ... of the int8 row and the matching float4s of the query
+        const int half = lane >> 4, sub = lane & 15;
+        const int n16 = P.n >> 4;
+        const float4* zq4 = reinterpret_cast<const float4*>(szq);
+#pragma unroll 4
+        for (int it = 0; it < 16; ++it) {
+          const int j = base + warp * 32 + it * 2 + half;
+          const int i = j < nlive ? ord[j] : 0;
+          const bool act = j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T;
+          const uint32_t p = act ? (uint32_t)skey[i] : 0u;
+          float a0 = 0.f, a1 = 0.f;
+          if (act) {
+            const float sc = __ldg(s8 + p);
+            const uint4* r4 = reinterpret_cast<const uint4*>(Z8 + (int64_t)p * P.n);
+            for (int u = sub; u < n16; u += 16) {
+              const uint4 w = __ldg(r4 + u);
+              const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                const float4 qv4 = zq4[4 * u + b];
+                const float v0 = (float)((int)(ws[b] << 24) >> 24), v1 = (float)((int)(ws[b] << 16) >> 24);
+                const float v2 = (float)((int)(ws[b] << 8) >> 24), v3 = (float)((int)ws[b] >> 24);
+                const float d0 = fmaf(-sc, v0, qv4.x), d1 = fmaf(-sc, v1, qv4.y);
+                const float d2 = fmaf(-sc, v2, qv4.z), d3 = fmaf(-sc, v3, qv4.w);
+                a0 = fmaf(d0, d0, a0);
+                a1 = fmaf(d1, d1, a1);
+                a0 = fmaf(d2, d2, a0);
+                a1 = fmaf(d3, d3, a1);
+              }
+            }
+          }
+          float e2 = a0 + a1;
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, o);
+          if (act && sub == 0) {
+            const float lbd = __fsub_rd(__fsqrt_rd(__fmul_rd(e2, one_minus_g)), __ldg(e8 + p));
+            if (lbd > 0.f && __fmul_rd(lbd, lbd) > 2.0f * T) ++filtered;
+            else surv[atomicAdd(&s_nsurv, 1)] = p;
+          }
+        }
+      } else {
+        const int j = base + tid;
+        const int i = j < nlive ? ord[j] : 0;
+        if (j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T) {
+          const uint32_t p = (uint32_t)skey[i];
+          const float e2 = thread_sqdist8(szq, Z8, s8[p], p, P.n);
+          const float lbd = __fsub_rd(__fsqrt_rd(__fmul_rd(e2, one_minus_g)), e8[p]);
+          if (lbd > 0.f && __fmul_rd(lbd, lbd) > 2.0f * T) ++filtered;
+          else surv[atomicAdd(&s_nsurv, 1)] = p;
+        }
+      }
+      __syncthreads();
+      const int ns = s_nsurv;
+      for (int sb = 0; sb < ns; sb += RROUND) {
+        const int j = sb + warp * 8 + (lane >> 2);
+        const bool active = j < ns;
+        const uint32_t p = active ? surv[j] : 0u;
+        const float d2 = group4_sqdist(szq, Z, p, P.n, lane & 3, active);
+        if ((lane & 3) == 0 && active) {
+          ++refined;
+          if (d2 <= s_lim) {
+            const int a2 = atomicAdd(&s_nacc, 1);
+            acc_d[a2] = d2;
+            acc_p[a2] = p;
+          }
+        }
+        __syncthreads();
+        if (tid == 0) merge_round();
+        __syncthreads();
+      }
+      if (s_stop) break;
+    }
+  } else {
+    for (int base = 0; base < nlive; base += RROUND) {
+      const int slot = warp * 8 + (lane >> 2);
+      const int j = base + slot;
+      const float T = vthr[q];
+      bool active = false;
+      uint32_t p = 0xFFFFFFFFu;
+      if (j < nlive) {
+        const int i = ord[j];
+        const float lb = __uint_as_float((uint32_t)(skey[i] >> 32));
+        active = lb <= T;
+        if (active) p = (uint32_t)skey[i];
+      }
+      if (tid == 0 && edge_of(base) > T) s_stop = 1;  // every later bucket starts above T
+      const float d2 = group4_sqdist(szq, Z, p, P.n, lane & 3, active);
+      if ((lane & 3) == 0 && active) {
+        ++refined;
+        if (d2 <= s_lim) {  // a candidate for the local kept list
+          const int a2 = atomicAdd(&s_nacc, 1);
+          acc_d[a2] = d2;
+          acc_p[a2] = p;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) merge_round();
+      __syncthreads();
+      if (s_stop) break;
+    }
   }
   const int nl = s_nl;
-  float* od = chunk_d + (slot_q * nchunk + c) * KCAP;
-  uint32_t* op = chunk_p + (slot_q * nchunk + c) * KCAP;
+  float* od = chunk_d + (int64_t)ch * KCAP;
+  uint32_t* op = chunk_p + (int64_t)ch * KCAP;
   for (int i = tid; i < nl; i += blockDim.x) {
     od[i] = sld[i];
     op[i] = slp[i];
   }
   if (tid == 0) {
-    *out_n = nl;
+    chunk_n[ch] = nl;
     if (s_lost) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
   }
+  }
   if ((lane & 3) == 0 && refined) atomicAdd(counters + 3, refined);
+  if (FILTER && filtered) atomicAdd(counters + 12, filtered);
 }
 
 // Merge of a query's kept list with the lists of its refined chunks: drop
@@ -683,8 +1015,9 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, int nchunk, const
 // the window of the current threshold, sort by (d2, pos), emit the new kept
 // list and its threshold, and flag the query when its buffer overflowed.
 constexpr int MSORT = 4096;
-__global__ void __launch_bounds__(256) k_merge(QueryParams P, int nchunk, const int* __restrict__ qsel,
+__global__ void __launch_bounds__(256) k_merge(QueryParams P, const int* __restrict__ qsel,
                                                const int* __restrict__ qslot, const int* __restrict__ cand_n,
+                                               const int* __restrict__ qpool_cnt, const int* __restrict__ choff,
                                                const float* __restrict__ chunk_d, const uint32_t* __restrict__ chunk_p,
                                                const int* __restrict__ chunk_n, float* __restrict__ list_d,
                                                uint32_t* __restrict__ list_p, int* __restrict__ list_n,
@@ -711,10 +1044,13 @@ __global__ void __launch_bounds__(256) k_merge(QueryParams P, int nchunk, const 
       if (a < MSORT) skey[a] = pack_key(d, list_p[q * KCAP + i]);
     }
   }
-  for (int c = 0; c < nchunk; ++c) {
-    const int m = chunk_n[slot_q * nchunk + c];
-    const float* cd = chunk_d + (slot_q * nchunk + c) * KCAP;
-    const uint32_t* cp = chunk_p + (slot_q * nchunk + c) * KCAP;
+  const int rq = all < P.cap ? all : P.cap;
+  const int stored = rq + qpool_cnt[slot_q];
+  const int nch = (stored + RSORT - 1) / RSORT;
+  for (int c = choff[slot_q]; c < choff[slot_q] + nch; ++c) {
+    const int m = chunk_n[c];
+    const float* cd = chunk_d + (int64_t)c * KCAP;
+    const uint32_t* cp = chunk_p + (int64_t)c * KCAP;
     for (int i = tid; i < m; i += blockDim.x) {
       if (cd[i] <= lim) {
         const int a = atomicAdd(&s_cnt, 1);
@@ -742,7 +1078,7 @@ __global__ void __launch_bounds__(256) k_merge(QueryParams P, int nchunk, const 
   }
   __syncthreads();
   if (!emit_list(skey, s_u, P, q, list_d, list_p, list_n, thr) && tid == 0) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
-  if (tid == 0 && all > P.cap) {
+  if (tid == 0 && stored < all) {  // the pool ran out: scan this query again
     qflag_out[q] = 1;
     atomicAdd(n_overflow, 1);
   }
@@ -920,15 +1256,21 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
 
-  static int scan_blocks[2] = {0, 0};
-  const size_t scan_smem = (size_t)2 * LW * MAX_ALPHA * sizeof(float2);
-  SOFA_CUDA(cudaFuncSetAttribute(k_scan<LW, NYQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem));
-  int& nb = scan_blocks[LW == 32];
+  // series-bound arithmetic: FP32, or FP16x2 with the derived factor
+  // f16 = 1 + (LW/2 + 5) u16 (u16 = 2^-11) on the threshold
+  const bool h16 = ix->bound_precision == 1;
+  const float f16 = std::nextafter((float)(1.0 + (LW / 2 + 5) * std::ldexp(1.0, -11)), 2.0f);
+  const float inv_f16 = std::nextafter(1.0f / f16, 0.0f);
+  static int scan_blocks[2][2] = {{0, 0}, {0, 0}};
+  auto scan_fn = h16 ? k_scan<LW, NYQ, true> : k_scan<LW, NYQ, false>;
+  const size_t scan_smem = (size_t)LW * MAX_ALPHA * (sizeof(float2) + (h16 ? sizeof(__half2) : sizeof(float2)));
+  SOFA_CUDA(cudaFuncSetAttribute(scan_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem));
+  int& nb = scan_blocks[LW == 32][h16];
   if (nb == 0) {
     int per_sm = 0, sms = 0, dev = 0;
     SOFA_CUDA(cudaGetDevice(&dev));
     SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SOFA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<LW, NYQ>, 256, scan_smem));
+    SOFA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_fn, 256, scan_smem));
     nb = sms * (per_sm > 0 ? per_sm : 1);
   }
 
@@ -940,9 +1282,40 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   std::vector<int> hflag, hslot;
   int rc = 0;
   int64_t slots = Q;
+  int* qof = nullptr;  // slot -> query (identity in the first pass)
+  // shared candidate pool: sized for the batch, at most 2^29 entries
+  const int64_t pool_cap =
+      ix->pool_cap > 0 ? ix->pool_cap
+                       : std::min<int64_t>((int64_t)1 << 29, std::max<int64_t>((int64_t)1 << 20, Q * std::min<int64_t>(ix->N, 65536)));
+  TRYQ(s.pool_q.ensure((size_t)pool_cap * sizeof(int)));
+  TRYQ(s.pool_p.ensure((size_t)pool_cap * sizeof(uint32_t)));
+  TRYQ(s.pool_lb.ensure((size_t)pool_cap * sizeof(float)));
+  TRYQ(s.pool_sp.ensure((size_t)pool_cap * sizeof(uint32_t)));
+  TRYQ(s.pool_slb.ensure((size_t)pool_cap * sizeof(float)));
+  int* pool_n = status + 3;
+  int* n_chunks = status + 4;
+  static int refine_blocks = 0;
+  if (refine_blocks == 0) {
+    int per_sm = 0, sms = 0, dev = 0;
+    SOFA_CUDA(cudaGetDevice(&dev));
+    SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SOFA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine<false>, 256, 4096));
+    refine_blocks = sms * (per_sm > 0 ? per_sm : 1);
+  }
   for (int pass = 0;; ++pass) {
     TRYQ(s.cand_p.ensure((size_t)slots * P.cap * sizeof(uint32_t)));
     TRYQ(s.cand_lb.ensure((size_t)slots * P.cap * sizeof(float)));
+    TRYQ(s.qpool_cnt.ensure((size_t)(slots + 1) * sizeof(int)));
+    TRYQ(s.qpool_off.ensure((size_t)(slots + 1) * sizeof(int)));
+    TRYQ(s.qcursor.ensure((size_t)(slots + 1) * sizeof(int)));
+    TRYQ(s.choff.ensure((size_t)(slots + 1) * sizeof(int)));
+    const int64_t max_chunks = ceil_div(slots * (int64_t)P.cap, RSORT) + slots + ceil_div(pool_cap, RSORT);
+    TRYQ(s.chunk_q.ensure((size_t)max_chunks * sizeof(int)));
+    TRYQ(s.chunk_d.ensure((size_t)max_chunks * KCAP * sizeof(float)));
+    TRYQ(s.chunk_p.ensure((size_t)max_chunks * KCAP * sizeof(uint32_t)));
+    TRYQ(s.chunk_n.ensure((size_t)max_chunks * sizeof(int)));
+    SOFA_CUDA(cudaMemsetAsync(s.qpool_cnt.p, 0, (slots + 1) * sizeof(int), st));
+    SOFA_CUDA(cudaMemsetAsync(pool_n, 0, sizeof(int), st));
     SOFA_CUDA(cudaMemsetAsync(s.leaf_cnt.p, 0, (L + 1) * sizeof(int), st));
     SOFA_CUDA(cudaMemsetAsync(s.cand_n.p, 0, Q * sizeof(int), st));
     SOFA_CUDA(cudaMemsetAsync(qflag_out, 0, Q * sizeof(int), st));
@@ -971,26 +1344,37 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     SOFA_CUDA(cudaMemcpyAsync(n_units, s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToDevice, st));
     ix->prof.end(st);
     ix->prof.begin(3, st);
-    k_scan<LW, NYQ><<<nb, 256, scan_smem, st>>>(P, s.units.as<int4>(), n_units, s.leaf_q.as<int>(), qv, thr,
-                                                 ix->tenv, ix->words, ix->edge, ix->ch, qslot,
-                                                 s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(),
-                                                 counters);
+    scan_fn<<<nb, 256, scan_smem, st>>>(P, s.units.as<int4>(), n_units, s.leaf_q.as<int>(), qv, thr,
+                                         ix->tenv, ix->words, ix->edge, ix->ch, ix->ch16, f16, inv_f16, qslot,
+                                         s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(), pool_cap,
+                                         pool_n, s.pool_q.as<int>(), s.pool_p.as<uint32_t>(), s.pool_lb.as<float>(),
+                                         s.qpool_cnt.as<int>(), counters);
     ix->prof.end(st);
     SOFA_CUDA(cudaGetLastError());
-    const int nchunk = (int)ceil_div(P.cap, RSORT);
-    TRYQ(s.chunk_d.ensure((size_t)slots * nchunk * KCAP * sizeof(float)));
-    TRYQ(s.chunk_p.ensure((size_t)slots * nchunk * KCAP * sizeof(uint32_t)));
-    TRYQ(s.chunk_n.ensure((size_t)slots * nchunk * sizeof(int)));
+    ix->prof.begin(7, st, 3);
+    k_chunk_plan<<<1, 1024, 0, st>>>(slots, P.cap, s.cand_n.as<int>(), s.qpool_cnt.as<int>(), s.qpool_off.as<int>(),
+                                      s.qcursor.as<int>(), s.choff.as<int>(), n_chunks);
+    k_pool_scatter<<<nb, 256, 0, st>>>(pool_n, pool_cap, s.pool_q.as<int>(), s.pool_p.as<uint32_t>(),
+                                       s.pool_lb.as<float>(), s.qpool_off.as<int>(), s.qcursor.as<int>(),
+                                       s.pool_sp.as<uint32_t>(), s.pool_slb.as<float>());
+    k_chunk_fill<<<(unsigned)ceil_div(slots, 256), 256, 0, st>>>(slots, P.cap, s.cand_n.as<int>(),
+                                                                  s.qpool_cnt.as<int>(), s.choff.as<int>(),
+                                                                  s.chunk_q.as<int>());
+    ix->prof.end(st);
     ix->prof.begin(4, st, 2);
-    k_refine<<<(unsigned)(Q * nchunk), 256, nsm, st>>>(P, nchunk, qsel, qslot, zq, ix->Z, s.cand_p.as<uint32_t>(),
-                                                       s.cand_lb.as<float>(), s.cand_n.as<int>(), thr,
-                                                       s.chunk_d.as<float>(), s.chunk_p.as<uint32_t>(),
-                                                       s.chunk_n.as<int>(), counters, status);
+    auto refine_fn = (ix->refine_filter && ix->Z8) ? k_refine<true> : k_refine<false>;
+    const float one_minus_g = std::nextafter((float)(1.0 - (n + 4) * std::ldexp(1.0, -24) / (1.0 - (n + 4) * std::ldexp(1.0, -24))), 0.0f);
+    refine_fn<<<refine_blocks, 256, nsm, st>>>(P, n_chunks, s.chunk_q.as<int>(), s.choff.as<int>(), qof, zq, ix->Z,
+                                             s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(),
+                                             s.qpool_cnt.as<int>(), s.qpool_off.as<int>(), s.pool_sp.as<uint32_t>(),
+                                             s.pool_slb.as<float>(), thr, s.chunk_d.as<float>(),
+                                             s.chunk_p.as<uint32_t>(), s.chunk_n.as<int>(), ix->Z8, ix->s8, ix->e8,
+                                             one_minus_g, counters, status);
     SOFA_CUDA(cudaGetLastError());
-    k_merge<<<(unsigned)Q, 256, 0, st>>>(P, nchunk, qsel, qslot, s.cand_n.as<int>(), s.chunk_d.as<float>(),
-                                         s.chunk_p.as<uint32_t>(), s.chunk_n.as<int>(), s.list_d.as<float>(),
-                                         s.list_p.as<uint32_t>(), s.list_n.as<int>(), thr, qflag_out, n_overflow,
-                                         status);
+    k_merge<<<(unsigned)Q, 256, 0, st>>>(P, qsel, qslot, s.cand_n.as<int>(), s.qpool_cnt.as<int>(), s.choff.as<int>(),
+                                         s.chunk_d.as<float>(), s.chunk_p.as<uint32_t>(), s.chunk_n.as<int>(),
+                                         s.list_d.as<float>(), s.list_p.as<uint32_t>(), s.list_n.as<int>(), thr,
+                                         qflag_out, n_overflow, status);
     ix->prof.end(st);
     SOFA_CUDA(cudaGetLastError());
     SOFA_CUDA(cudaMemcpyAsync(h_over, n_overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1015,6 +1399,12 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     TRYQ(s.qslot.ensure(Q * sizeof(int)));
     SOFA_CUDA(cudaMemcpy(s.qslot.p, hslot.data(), Q * sizeof(int), cudaMemcpyHostToDevice));
     qslot = s.qslot.as<int>();
+    std::vector<int> hqof((size_t)std::max<int64_t>(m, 1));
+    for (int64_t i = 0; i < Q; ++i)
+      if (hflag[i]) hqof[hslot[i]] = (int)i;
+    TRYQ(s.qof.ensure((size_t)std::max<int64_t>(m, 1) * sizeof(int)));
+    SOFA_CUDA(cudaMemcpy(s.qof.p, hqof.data(), hqof.size() * sizeof(int), cudaMemcpyHostToDevice));
+    qof = s.qof.as<int>();
     int* prev = qflag_out;
     qflag_out = (qflag_out == s.qflag.as<int>()) ? s.qflag.as<int>() + Q : s.qflag.as<int>();
     qsel = prev;

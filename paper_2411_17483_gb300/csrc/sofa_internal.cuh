@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -58,6 +59,9 @@ struct QueryScratch {
   DevBuf cand_n;    // Q candidate counts
   DevBuf qflag;     // 2 x Q per-query flags (overflow), double-buffered
   DevBuf qslot;     // Q candidate-buffer slots of overflowed queries
+  DevBuf pool_q, pool_p, pool_lb;   // shared candidate pool (slot, position, bound)
+  DevBuf pool_sp, pool_slb;         // the pool grouped by slot
+  DevBuf qpool_cnt, qpool_off, qcursor, choff, chunk_q, qof;
   DevBuf chunk_d;   // refined chunk kept lists
   DevBuf chunk_p;
   DevBuf chunk_n;
@@ -102,9 +106,14 @@ struct Index {
   float* beta = nullptr;       // [LW][alpha+1]
   float2* edge = nullptr;      // [LW][256] widened (lo, hi) per symbol
   float2* ch = nullptr;        // [LW][256] (centre, half-width) per symbol
+  __half2* ch16 = nullptr;     // [LW][256] (centre, -half-width) for the FP16 bound
+  float outer = 0.f;           // magnitude bound of every value interval
   // layout
   uint8_t* words = nullptr;    // [N][LW] key-sorted
   float* Z = nullptr;          // [N][n] key-sorted canonical series
+  int8_t* Z8 = nullptr;        // [N][n] int8 copy (refinement filter), optional
+  float* s8 = nullptr;         // [N] its scales
+  float* e8 = nullptr;         // [N] its residual norms (rounded up)
   uint32_t* perm = nullptr;    // [N] sorted position -> original row
   uint64_t* keys = nullptr;    // [N] sorted layout keys
   uint8_t* keyorder = nullptr; // [64] key bit order (dim << 3 | bit)
@@ -114,8 +123,11 @@ struct Index {
   int64_t device_bytes = 0;
   // query state
   QueryScratch qs;
-  int group = 64, cand_cap = 131072, seed_count = 128, seed_window = 4096;
+  int group = 64, cand_cap = 65536, seed_count = 128, seed_window = 4096;
   int seed_mode = 0;
+  int bound_precision = 0;     // 0 FP32 series bounds, 1 FP16x2 series bounds
+  int64_t pool_cap = 0;        // shared candidate pool entries (0: automatic)
+  int refine_filter = 0;       // 1: int8 filter before the FP32 distance
   int status = 0;
   int64_t stats[8] = {0};
   Mlp* mlp = nullptr;

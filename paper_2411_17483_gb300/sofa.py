@@ -44,13 +44,15 @@ class TrainOpts(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("cand_cap", ctypes.c_int32), ("seed_count", ctypes.c_int32),
-                ("seed_window", ctypes.c_int32)]
+                ("seed_window", ctypes.c_int32), ("bound_precision", ctypes.c_int32), ("pool_cap", ctypes.c_int64),
+                ("refine_filter", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in
                 ("queries", "leaf_pairs", "tile_pairs", "candidates", "refined", "overflow_passes",
-                 "n_leaves", "n_tiles")] + [("seed_dist_sum", ctypes.c_double), ("final_dist_sum", ctypes.c_double)]
+                 "n_leaves", "n_tiles", "filtered")] + [("seed_dist_sum", ctypes.c_double),
+                                                        ("final_dist_sum", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -58,7 +60,7 @@ class Profile(ctypes.Structure):
                 ("scan_tile_loads", ctypes.c_int64), ("scan_tile_checks", ctypes.c_int64)]
 
 
-PHASES = ("qprep", "seed", "route", "scan", "refine", "final", "proposal", "p7")
+PHASES = ("qprep", "seed", "route", "scan", "refine", "final", "proposal", "pool")
 
 
 class Info(ctypes.Structure):
@@ -184,8 +186,9 @@ class Index:
         _check(load().sofa_query(self.h, _ptr(q), Q, k, _ptr(idx), _ptr(dist), _stream(stream)))
         return idx, dist
 
-    def set_tuning(self, group=0, cand_cap=0, seed_count=0, seed_window=0):
-        t = Tuning(group, cand_cap, seed_count, seed_window)
+    def set_tuning(self, group=0, cand_cap=0, seed_count=0, seed_window=0, bound_precision=0, pool_cap=0,
+                   refine_filter=0):
+        t = Tuning(group, cand_cap, seed_count, seed_window, bound_precision, pool_cap, refine_filter)
         _check(load().sofa_set_tuning(self.h, ctypes.byref(t)))
 
     def set_seed_mode(self, mode: int):
@@ -211,8 +214,8 @@ class Index:
     def profile(self, reset=False) -> dict:
         s = Profile()
         _check(load().sofa_profile(self.h, ctypes.byref(s), 1 if reset else 0))
-        return {"ms": {PHASES[i]: s.ms[i] for i in range(7)},
-                "launches": {PHASES[i]: s.launches[i] for i in range(7)},
+        return {"ms": {PHASES[i]: s.ms[i] for i in range(8)},
+                "launches": {PHASES[i]: s.launches[i] for i in range(8)},
                 "scan_tile_loads": s.scan_tile_loads, "scan_tile_checks": s.scan_tile_checks}
 
     def info(self) -> dict:

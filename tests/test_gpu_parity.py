@@ -157,6 +157,21 @@ def test_knn_matches_oracle(sofa, N, n, l, alpha, k, Q, gen):
     ix.close()
 
 
+@pytest.mark.parametrize("N,n,l,alpha,k,Q,gen", [CASES[1], CASES[3], CASES[4], CASES[5]])
+def test_knn_reduced_precision_match_oracle(sofa, N, n, l, alpha, k, Q, gen):
+    """FP16x2 series bounds and the int8 refinement filter, each with its
+    derived margin: the same exact answers."""
+    x = make(gen, N, n, seed=N + n + 1)
+    q = datagen.half_perturbed_queries(x, Q, seed=4)
+    ix = sofa.Index(x, l, alpha, precision=1)
+    ix.set_tuning(bound_precision=1, refine_filter=1)
+    gi, gd = ix.query(q, k)
+    oi, od = oracle_knn(x, q, k)
+    assert_knn_equal(gi, gd, oi, od)
+    assert ix.status() == 0
+    ix.close()
+
+
 def test_duplicates_and_member_queries(sofa):
     N, n = 5000, 64
     x = datagen.random_walks(N, n, seed=21, device=DEV)
@@ -173,18 +188,21 @@ def test_duplicates_and_member_queries(sofa):
 
 
 @pytest.mark.parametrize("tuning", [dict(group=1), dict(group=64), dict(cand_cap=1), dict(cand_cap=7, group=3),
+                                    dict(cand_cap=3, pool_cap=5), dict(cand_cap=64, pool_cap=1),
                                     dict(seed_count=1), dict(seed_count=256), dict(seed_window=4096, seed_count=128),
-                                    dict(seed_window=256)])
+                                    dict(seed_window=256), dict(bound_precision=1),
+                                    dict(bound_precision=1, cand_cap=5, group=7), dict(refine_filter=1),
+                                    dict(refine_filter=1, bound_precision=1, cand_cap=9, pool_cap=40)])
 def test_tuning_invariance(sofa, tuning):
     N, n = 15000, 128
     x = datagen.mixed_walks(N, n, seed=31, device=DEV)
     q = datagen.half_perturbed_queries(x, 40, seed=2)
-    ix = sofa.Index(x, 16, 256, leaf_tiles=4)
+    ix = sofa.Index(x, 16, 256, leaf_tiles=4, precision=1)
     gi0, gd0 = ix.query(q, 10)
     ix.set_tuning(**tuning)
     gi1, gd1 = ix.query(q, 10)
     assert torch.equal(gi0, gi1) and torch.equal(gd0, gd1)
-    if tuning.get("cand_cap") == 1:
+    if "pool_cap" in tuning:       # a full pool: the queries concerned are scanned again
         assert ix.stats()["overflow_passes"] > 0
     ix.close()
 
