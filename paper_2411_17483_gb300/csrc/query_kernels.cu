@@ -488,6 +488,8 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
   __shared__ __align__(16) float sq[MAX_GROUP][LW];
   __shared__ __align__(16) __half2 sq16[MAX_GROUP][LW / 2];
   __shared__ float sT[MAX_GROUP];
+  __shared__ float sTs[MAX_GROUP];  // thresholds in the unit's scaled units (FP32 path)
+  __shared__ float s_a, s_inva2;
   __shared__ int sslot[MAX_GROUP];
   __shared__ unsigned long long smask[MAX_LEAF_TILES];
   const int tid = threadIdx.x, lane = tid & 31;
@@ -518,6 +520,23 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
     }
     for (int t = tid; t < nt; t += blockDim.x) smask[t] = 0ull;
     __syncthreads();
+    if (!H16) {
+      // Scale a = 1/M with M^2 >= 2.5 max T: each value's term is computed as
+      // u = sat(|q - c| a - h a), clipping m at M; a clipped term alone exceeds
+      // every threshold of the unit, so clipping never keeps a series that the
+      // exact bound prunes (nor prunes one it keeps).
+      if (tid == 0) {
+        float tmax = 0.f;
+        for (int g = 0; g < cnt; ++g) tmax = fmaxf(tmax, sT[g]);
+        float a = __frcp_rd(__fsqrt_ru(__fmul_ru(2.5f, tmax)));
+        a = fminf(fmaxf(a, 0x1p-20f), 0x1p20f);
+        s_a = a;
+        s_inva2 = __frcp_rd(__fmul_ru(a, a));
+      }
+      __syncthreads();
+      for (int g = tid; g < cnt; g += blockDim.x) sTs[g] = __fmul_ru(__fmul_ru(sT[g], s_a), s_a);
+      __syncthreads();
+    }
     // all envelope checks of the unit
     for (int e = tid; e < nt * cnt; e += blockDim.x) {
       const int t = e / cnt, g = e - t * cnt;
@@ -564,11 +583,14 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
         }
       } else {
         load_word_bounds<LW>(words, p, valid, sch, c, h);
+        const float a = s_a;
+#pragma unroll
+        for (int j = 0; j < LW; ++j) h[j] = __fmul_ru(h[j], a);  // h a, rounded up
       }
       while (m) {
         const int g = __ffsll((long long)m) - 1;
         m &= m - 1;
-        const float T = H16 ? sT[g] * f16 : sT[g];
+        const float T = H16 ? sT[g] * f16 : sTs[g];
         bool live = valid;
         float acc;
         if constexpr (H16) {
@@ -596,9 +618,10 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
           const float2 af = __half22float2(a2);
           acc = __fmul_rd(af.x + af.y, inv_f16);  // deflated: a lower bound in exact units
         } else {
-          const float* qg = sq[g];
-          // two partial sums (even / odd values) halve the dependent FMA chain;
-          // the warp votes after 4, 8, 16 (and 32) values
+          const float4* qg4 = reinterpret_cast<const float4*>(sq[g]);
+          const float a = s_a;
+          // u = sat(|q - c| a - h a) (one FADD, one FFMA.SAT), two partial sums
+          // (even / odd values); the warp votes after 4, 8, 16 (and 32) values
           float a0 = 0.f, a1 = 0.f;
 #pragma unroll
           for (int stage = 0; stage < 8; ++stage) {
@@ -607,15 +630,20 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
             if (j0 >= LW) break;
             if (!__any_sync(0xFFFFFFFFu, live)) break;
 #pragma unroll
-            for (int j = j0; j < j1 && j < LW; j += 2) {
-              const float m0 = fmaxf(fabsf(qg[j] - c[j]) - h[j], 0.f);
-              const float m1 = fmaxf(fabsf(qg[j + 1] - c[j + 1]) - h[j + 1], 0.f);
-              a0 = fmaf((NYQ && j == 0) ? 0.5f * m0 : m0, m0, a0);
-              a1 = fmaf(m1, m1, a1);
+            for (int j = j0; j < j1 && j < LW; j += 4) {
+              const float4 q4 = qg4[j >> 2];
+              const float u0 = __saturatef(fmaf(fabsf(q4.x - c[j]), a, -h[j]));
+              const float u1 = __saturatef(fmaf(fabsf(q4.y - c[j + 1]), a, -h[j + 1]));
+              const float u2 = __saturatef(fmaf(fabsf(q4.z - c[j + 2]), a, -h[j + 2]));
+              const float u3 = __saturatef(fmaf(fabsf(q4.w - c[j + 3]), a, -h[j + 3]));
+              a0 = fmaf((NYQ && j == 0) ? 0.5f * u0 : u0, u0, a0);
+              a1 = fmaf(u1, u1, a1);
+              a0 = fmaf(u2, u2, a0);
+              a1 = fmaf(u3, u3, a1);
             }
             live = live && (a0 + a1) <= T;
           }
-          acc = a0 + a1;
+          acc = __fmul_rd(a0 + a1, s_inva2);  // back to half units, rounded down
         }
         const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
         if (hit) {
@@ -897,40 +925,59 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __rest
         const int half = lane >> 4, sub = lane & 15;
         const int n16 = P.n >> 4;
         const float4* zq4 = reinterpret_cast<const float4*>(szq);
-#pragma unroll 4
-        for (int it = 0; it < 16; ++it) {
-          const int j = base + warp * 32 + it * 2 + half;
-          const int i = j < nlive ? ord[j] : 0;
-          const bool act = j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T;
-          const uint32_t p = act ? (uint32_t)skey[i] : 0u;
-          float a0 = 0.f, a1 = 0.f;
-          if (act) {
-            const float sc = __ldg(s8 + p);
-            const uint4* r4 = reinterpret_cast<const uint4*>(Z8 + (int64_t)p * P.n);
-            for (int u = sub; u < n16; u += 16) {
-              const uint4 w = __ldg(r4 + u);
-              const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        // four candidates per half-warp at a time: all their loads are issued
+        // before any reduction, and the query float4s are shared by the four
+        for (int it = 0; it < 16; it += 4) {
+          bool act[4];
+          uint32_t pp[4];
+          float sc[4], a0[4], a1[4];
 #pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                const float4 qv4 = zq4[4 * u + b];
-                const float v0 = (float)((int)(ws[b] << 24) >> 24), v1 = (float)((int)(ws[b] << 16) >> 24);
-                const float v2 = (float)((int)(ws[b] << 8) >> 24), v3 = (float)((int)ws[b] >> 24);
-                const float d0 = fmaf(-sc, v0, qv4.x), d1 = fmaf(-sc, v1, qv4.y);
-                const float d2 = fmaf(-sc, v2, qv4.z), d3 = fmaf(-sc, v3, qv4.w);
-                a0 = fmaf(d0, d0, a0);
-                a1 = fmaf(d1, d1, a1);
-                a0 = fmaf(d2, d2, a0);
-                a1 = fmaf(d3, d3, a1);
+          for (int k = 0; k < 4; ++k) {
+            const int j = base + warp * 32 + (it + k) * 2 + half;
+            const int i = j < nlive ? ord[j] : 0;
+            act[k] = j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T;
+            pp[k] = act[k] ? (uint32_t)skey[i] : 0u;
+            sc[k] = act[k] ? __ldg(s8 + pp[k]) : 0.f;
+            a0[k] = 0.f;
+            a1[k] = 0.f;
+          }
+          for (int u = sub; u < n16; u += 16) {
+            uint4 w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              w[k] = act[k] ? __ldg(reinterpret_cast<const uint4*>(Z8 + (int64_t)pp[k] * P.n) + u)
+                            : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const float4 qv4 = zq4[4 * u + b];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const uint32_t ws = b == 0 ? w[k].x : b == 1 ? w[k].y : b == 2 ? w[k].z : w[k].w;
+                const float v0 = (float)((int)(ws << 24) >> 24), v1 = (float)((int)(ws << 16) >> 24);
+                const float v2 = (float)((int)(ws << 8) >> 24), v3 = (float)((int)ws >> 24);
+                const float d0 = fmaf(-sc[k], v0, qv4.x), d1 = fmaf(-sc[k], v1, qv4.y);
+                const float d2 = fmaf(-sc[k], v2, qv4.z), d3 = fmaf(-sc[k], v3, qv4.w);
+                a0[k] = fmaf(d0, d0, a0[k]);
+                a1[k] = fmaf(d1, d1, a1[k]);
+                a0[k] = fmaf(d2, d2, a0[k]);
+                a1[k] = fmaf(d3, d3, a1[k]);
               }
             }
           }
-          float e2 = a0 + a1;
+          float e2[4];
 #pragma unroll
-          for (int o = 8; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, o);
-          if (act && sub == 0) {
-            const float lbd = __fsub_rd(__fsqrt_rd(__fmul_rd(e2, one_minus_g)), __ldg(e8 + p));
-            if (lbd > 0.f && __fmul_rd(lbd, lbd) > 2.0f * T) ++filtered;
-            else surv[atomicAdd(&s_nsurv, 1)] = p;
+          for (int k = 0; k < 4; ++k) e2[k] = a0[k] + a1[k];
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e2[k] += __shfl_xor_sync(0xFFFFFFFFu, e2[k], o);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (act[k] && sub == 0) {
+              const float lbd = __fsub_rd(__fsqrt_rd(__fmul_rd(e2[k], one_minus_g)), __ldg(e8 + pp[k]));
+              if (lbd > 0.f && __fmul_rd(lbd, lbd) > 2.0f * T) ++filtered;
+              else surv[atomicAdd(&s_nsurv, 1)] = pp[k];
+            }
           }
         }
       } else {
