@@ -219,6 +219,22 @@ int sofa_export_perm(sofa_handle h, uint32_t* perm);
  * out is Q x N fp32, device memory; queries Q x n fp32 device memory. */
 int sofa_lower_bounds(sofa_handle h, const float* queries, int64_t Q, float* out, sofa_stream stream);
 
+/* Allocation-free variant of sofa_lower_bounds (the paper has no counterpart).
+ * For callers that cannot have the library allocate device memory during the
+ * call (a memory budget already spent, an allocator owned by the caller, a
+ * thread that must not take allocation locks, or a loop that cannot absorb an
+ * allocation's implicit synchronisation): its work space is a fixed 16 MiB
+ * array in the library's device image, held by every GPU that loads the
+ * library until the process exits.  Same arguments and output as
+ * sofa_lower_bounds (device pointers); Q <= 2^22 / (n + 2 * word_bytes)
+ * queries per call, larger Q is rejected with SOFA_ERR_INVALID_ARG before any
+ * work.  It calls no cudaMalloc or cudaFree.  The first call on a device looks
+ * up the work space's device address (cudaGetSymbolAddress) and should happen
+ * before any stream capture.  All calls share the one work space: calls whose
+ * device work overlaps (different streams, or host threads) race and must be
+ * serialised by the caller.  Nothing in it needs clearing between calls. */
+int sofa_lower_bounds_noalloc(sofa_handle h, const float* queries, int64_t Q, float* out, sofa_stream stream);
+
 /* Canonical z-normalisation of R rows (Sec. II Def. z-ED) as the index uses
  * it: device pointers, R x n fp32 in and out. */
 int sofa_znorm(const float* x, int64_t R, int32_t n, float* z, sofa_stream stream);

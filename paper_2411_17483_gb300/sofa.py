@@ -103,6 +103,7 @@ def load():
         "sofa_export_words": (ctypes.c_int, [P, P]),
         "sofa_export_perm": (ctypes.c_int, [P, P]),
         "sofa_lower_bounds": (ctypes.c_int, [P, P, i64, P, P]),
+        "sofa_lower_bounds_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "sofa_znorm": (ctypes.c_int, [P, i64, i32, P, P]),
         "sofa_free": (None, [P]),
         "sofa_last_error": (ctypes.c_char_p, []),
@@ -246,6 +247,14 @@ class Index:
         out = torch.empty((q.shape[0], self.N), dtype=torch.float32, device=q.device)
         _check(load().sofa_lower_bounds(self.h, _ptr(q), q.shape[0], _ptr(out), _stream(stream)))
         return out
+
+
+def lower_bounds_noalloc(index: "Index", q: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """sofa_lower_bounds_noalloc: the caller provides `out` (Q x N fp32, device);
+    the library allocates nothing during the call."""
+    q = q.contiguous()
+    _check(load().sofa_lower_bounds_noalloc(index.h, _ptr(q), q.shape[0], _ptr(out), _stream(stream)))
+    return out
 
 
 def mlp_grad(params: torch.Tensor, x: torch.Tensor, y: torch.Tensor, din: int, hidden: int, classes: int,
