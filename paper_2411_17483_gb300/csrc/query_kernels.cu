@@ -17,6 +17,8 @@ namespace sofa {
 
 
 
+constexpr int LEARN_CAP = 2048;  // learned-seed candidates kept beside the key window
+
 struct QueryParams {
   int64_t N, T, L;
   int n, NB, leaf_tiles, k, cap, group, seed_count, seed_window;
@@ -292,65 +294,57 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
     }
     __syncthreads();
   }
-  // learned seeding: the best tile (by envelope bound) of each of the
-  // proposal network's top-m blocks joins the key window
-  int m_eff = topm ? top_m : 0;
-  if (m_eff * TILE > P.seed_window / 2) m_eff = P.seed_window / (2 * TILE);
-  const int nlearn = m_eff * TILE;
-  __shared__ int64_t s_ltile[8];
-  for (int i = 0; i < m_eff; ++i) {
-    const int64_t b = topm[q * top_m + i];
-    const int64_t lo_t = (b * block) / TILE;
-    int64_t hi_p = (b + 1) * block < P.N ? (b + 1) * block : P.N;
-    const int64_t hi_t = (hi_p + TILE - 1) / TILE;
-    unsigned long long best = ~0ull;
-    for (int64_t t = lo_t + tid; t < hi_t && t < P.T; t += blockDim.x) {
-      const unsigned long long kk = pack_key(env_bound<LW, NYQ>(tenv + t * 2 * LW, sq, edge), (uint32_t)t);
-      best = kk < best ? kk : best;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-      best = v < best ? v : best;
-    }
-    if (lane == 0) sbest[warp] = best;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned long long v = sbest[0];
-      for (int w = 1; w < 8; ++w) v = sbest[w] < v ? sbest[w] : v;
-      s_ltile[i] = v == ~0ull ? -1 : (int64_t)(uint32_t)v;
-    }
-    __syncthreads();
-  }
-  const int wkey = P.seed_window - nlearn;
-  const int64_t W = P.N < wkey ? P.N : wkey;
+  const int64_t W = P.N < P.seed_window ? P.N : P.seed_window;
   int64_t p0 = s_lo - W / 2;
   if (p0 > P.N - W) p0 = P.N - W;
   if (p0 < 0) p0 = 0;
 
-  // (3) series bounds of the key window (and the learned tiles); the
-  // seed_count smallest distinct ones are refined
+  // (3) series bounds of the key window; its seed_count smallest are the
+  // approximate answer's candidates
   for (int i = tid; i < P.seed_window; i += blockDim.x) {
-    int64_t p;
-    bool valid;
-    if (i < wkey) {
-      p = p0 + i;
-      valid = i < W;
-    } else {
-      const int j = i - wkey;
-      const int64_t tt = s_ltile[j / TILE];
-      p = tt * TILE + (j % TILE);
-      valid = tt >= 0 && p < P.N;
-    }
+    const int64_t p = p0 + i;
+    const bool valid = i < W;
     float c[LW], h[LW];
     load_word_bounds<LW>(words, p, valid, ch, c, h);
     skey[i] = valid ? pack_key(word_bound<LW, NYQ>(c, h, sq), (uint32_t)p) : ~0ull;
   }
   block_bitonic(skey, P.seed_window);
   int cnt = P.seed_count > P.k ? P.seed_count : P.k;
+  if (cnt > W) cnt = (int)W;
+  // learned seeding: every series of the proposal network's top-m blocks whose
+  // bound beats the window's cnt-th joins the candidates (up to LEARN_CAP)
+  __shared__ int s_nl2;
+  if (tid == 0) s_nl2 = 0;
+  __syncthreads();
+  if (topm) {
+    const float tau = __uint_as_float((uint32_t)(skey[cnt - 1] >> 32));
+    for (int i = 0; i < top_m; ++i) {
+      const int64_t b = topm[q * top_m + i];
+      const int64_t lo = b * block;
+      const int64_t hi = (b + 1) * block < P.N ? (b + 1) * block : P.N;
+      for (int64_t p = lo + tid; p < hi; p += blockDim.x) {
+        float c[LW], h[LW];
+        load_word_bounds<LW>(words, p, true, ch, c, h);
+        const float a = word_bound<LW, NYQ>(c, h, sq);
+        if (a < tau) {
+          const int slot = atomicAdd(&s_nl2, 1);
+          if (slot < LEARN_CAP) skey[cnt + slot] = pack_key(a, (uint32_t)p);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  int len = cnt + (s_nl2 < LEARN_CAP ? s_nl2 : LEARN_CAP);
+  if (len > cnt) {
+    int pw2 = 1;
+    while (pw2 < len) pw2 <<= 1;
+    for (int i = len + tid; i < pw2; i += blockDim.x) skey[i] = ~0ull;
+    block_bitonic(skey, pw2);
+  }
   __shared__ int s_avail;
-  if (tid == 0) {  // a learned tile may overlap the key window: drop repeats
+  if (tid == 0) {  // a learned block may overlap the key window: drop repeats
     int u = 0;
-    for (int i = 0; i < P.seed_window && u < cnt; ++i) {
+    for (int i = 0; i < len && u < cnt; ++i) {
       if (skey[i] == ~0ull) break;
       if (u == 0 || skey[i] != skey[u - 1]) skey[u++] = skey[i];
     }
