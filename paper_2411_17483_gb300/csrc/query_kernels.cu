@@ -18,6 +18,7 @@ namespace sofa {
 
 
 constexpr int LEARN_CAP = 2048;  // learned-seed candidates kept beside the key window
+constexpr int SEED_TL = 512;     // tiles of a predicted block examined per pass
 
 struct QueryParams {
   int64_t N, T, L;
@@ -41,6 +42,31 @@ __device__ __forceinline__ float env_bound(const uint8_t* __restrict__ env, cons
       const int j = 4 * w + b;
       float elo = edge[j * MAX_ALPHA + ((lo >> (8 * b)) & 0xFFu)].x;
       float ehi = edge[j * MAX_ALPHA + ((hi >> (8 * b)) & 0xFFu)].y;
+      float m = fmaxf(fmaxf(elo - q[j], q[j] - ehi), 0.f);
+      float mm = (NYQ && j == 0) ? 0.5f * m : m;
+      acc = fmaf(mm, m, acc);
+    }
+  }
+  return acc;
+}
+
+// Envelope bound from the (centre, half-width) table: the interval of
+// symbols lo_j..hi_j is contained in [c(lo) - h(lo), c(hi) + h(hi)], both ends
+// rounded outward (a hair looser than the edge table, never tighter).
+template <int LW, bool NYQ>
+__device__ __forceinline__ float env_bound_ch(const uint8_t* __restrict__ env, const float* q,
+                                              const float2* __restrict__ chs) {
+  const uint32_t* e32 = reinterpret_cast<const uint32_t*>(env);
+  float acc = 0.f;
+#pragma unroll
+  for (int w = 0; w < LW / 4; ++w) {
+    uint32_t lo = e32[w], hi = e32[LW / 4 + w];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = 4 * w + b;
+      const float2 vl = chs[j * MAX_ALPHA + ((lo >> (8 * b)) & 0xFFu)];
+      const float2 vh = chs[j * MAX_ALPHA + ((hi >> (8 * b)) & 0xFFu)];
+      const float elo = __fsub_rd(vl.x, vl.y), ehi = __fadd_ru(vh.x, vh.y);
       float m = fmaxf(fmaxf(elo - q[j], q[j] - ehi), 0.f);
       float mm = (NYQ && j == 0) ? 0.5f * m : m;
       acc = fmaf(mm, m, acc);
@@ -318,18 +344,35 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
   __syncthreads();
   if (topm) {
     const float tau = __uint_as_float((uint32_t)(skey[cnt - 1] >> 32));
+    __shared__ int s_tl[SEED_TL];
+    __shared__ int s_nt;
     for (int i = 0; i < top_m; ++i) {
       const int64_t b = topm[q * top_m + i];
       const int64_t lo = b * block;
       const int64_t hi = (b + 1) * block < P.N ? (b + 1) * block : P.N;
-      for (int64_t p = lo + tid; p < hi; p += blockDim.x) {
-        float c[LW], h[LW];
-        load_word_bounds<LW>(words, p, true, ch, c, h);
-        const float a = word_bound<LW, NYQ>(c, h, sq);
-        if (a < tau) {
-          const int slot = atomicAdd(&s_nl2, 1);
-          if (slot < LEARN_CAP) skey[cnt + slot] = pack_key(a, (uint32_t)p);
+      for (int64_t tb = lo / TILE; tb * TILE < hi; tb += SEED_TL) {
+        // tiles of the block whose envelope bound is below the cut-off
+        if (tid == 0) s_nt = 0;
+        __syncthreads();
+        for (int j = tid; j < SEED_TL; j += blockDim.x) {
+          const int64_t t = tb + j;
+          if (t * TILE < hi && t < P.T && env_bound<LW, NYQ>(tenv + t * 2 * LW, sq, edge) < tau)
+            s_tl[atomicAdd(&s_nt, 1)] = (int)(t - tb);
         }
+        __syncthreads();
+        const int nt2 = s_nt;
+        for (int j = 0; j < nt2; ++j) {
+          const int64_t p = (tb + s_tl[j]) * TILE + tid;
+          if (p < lo || p >= hi) continue;
+          float c[LW], h[LW];
+          load_word_bounds<LW>(words, p, true, ch, c, h);
+          const float a = word_bound<LW, NYQ>(c, h, sq);
+          if (a < tau) {
+            const int slot = atomicAdd(&s_nl2, 1);
+            if (slot < LEARN_CAP) skey[cnt + slot] = pack_key(a, (uint32_t)p);
+          }
+        }
+        __syncthreads();
       }
     }
   }
@@ -476,9 +519,8 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
                                               uint32_t* __restrict__ pool_p, float* __restrict__ pool_lb,
                                               int* __restrict__ qpool_cnt, unsigned long long* __restrict__ counters) {
   extern __shared__ float2 tabs[];
-  float2* sedge = tabs;                                                 // LW x 256
-  float2* sch = tabs + LW * MAX_ALPHA;                                  // LW x 256 (FP32 mode)
-  __half2* sch16 = reinterpret_cast<__half2*>(tabs + LW * MAX_ALPHA);   // LW x 256 (FP16 mode)
+  float2* sch = tabs;                                                   // LW x 256 (tile checks, FP32 bounds)
+  __half2* sch16 = reinterpret_cast<__half2*>(tabs + LW * MAX_ALPHA);   // LW x 256 (FP16 bounds)
   __shared__ __align__(16) float sq[MAX_GROUP][LW];
   __shared__ __align__(16) __half2 sq16[MAX_GROUP][LW / 2];
   __shared__ float sT[MAX_GROUP];
@@ -488,9 +530,8 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
   __shared__ unsigned long long smask[MAX_LEAF_TILES];
   const int tid = threadIdx.x, lane = tid & 31;
   for (int e = tid; e < LW * MAX_ALPHA; e += blockDim.x) {
+    sch[e] = ch[e];
     if (H16) sch16[e] = ch16[e];
-    else sch[e] = ch[e];
-    sedge[e] = edge[e];
   }
   unsigned long long n_tile_pairs = 0, n_cand = 0, n_loads = 0, n_checks = 0;
   const int n_units = *n_units_ptr;
@@ -534,7 +575,7 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
     // all envelope checks of the unit
     for (int e = tid; e < nt * cnt; e += blockDim.x) {
       const int t = e / cnt, g = e - t * cnt;
-      float a = env_bound<LW, NYQ>(tenv + (t0 + t) * 2 * LW, sq[g], sedge);
+      float a = env_bound_ch<LW, NYQ>(tenv + (t0 + t) * 2 * LW, sq[g], sch);
       if (a <= sT[g]) atomicOr(&smask[t], 1ull << g);
     }
     n_checks += (tid == 0) ? (unsigned long long)nt : 0ull;
@@ -1304,7 +1345,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   const float inv_f16 = std::nextafter(1.0f / f16, 0.0f);
   static int scan_blocks[2][2] = {{0, 0}, {0, 0}};
   auto scan_fn = h16 ? k_scan<LW, NYQ, true> : k_scan<LW, NYQ, false>;
-  const size_t scan_smem = (size_t)LW * MAX_ALPHA * (sizeof(float2) + (h16 ? sizeof(__half2) : sizeof(float2)));
+  const size_t scan_smem = (size_t)LW * MAX_ALPHA * (sizeof(float2) + (h16 ? sizeof(__half2) : 0));
   SOFA_CUDA(cudaFuncSetAttribute(scan_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem));
   int& nb = scan_blocks[LW == 32][h16];
   if (nb == 0) {
