@@ -326,6 +326,26 @@ def run_sofa(a, ws, rank, local):
                "d2h_bytes_per_step": a.Q * a.k * 12}
         assert torch.equal(ih, idx.cpu())
 
+    # small-batch latency of the chosen mode, eager vs recorded CUDA graph
+    latency = None
+    if not a.no_e2e:
+        qs = q[:64].contiguous()
+        li = torch.empty((64, a.k), dtype=torch.int64, device=dev)
+        ld = torch.empty((64, a.k), dtype=torch.float32, device=dev)
+        lat = {}
+        for use_graph in (0, 1):
+            ix.set_tuning(refine_filter=1, use_graph=use_graph)
+            for _ in range(3):
+                ix.query(qs, a.k, li, ld)
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            for _ in range(20):
+                ix.query(qs, a.k, li, ld)
+            torch.cuda.synchronize()
+            lat["graph_ms" if use_graph else "eager_ms"] = (time.perf_counter() - w0) / 20 * 1e3
+        ix.set_tuning(refine_filter=1)
+        latency = {"queries": 64, **lat, "graph_replays": ix.stats()["graph_replays"]}
+
     cpu = None
     if cpu_rows is not None:
         from oracle import sofa_oracle as orc
@@ -360,6 +380,7 @@ def run_sofa(a, ws, rank, local):
                           "phases_ms_per_step": {k: v / a.steps for k, v in results[m]["prof"]["ms"].items()}}
                       for m in results},
             "proposal_training": train,
+            "latency_64_queries": latency,
             "index": {"n_leaves": info["n_leaves"], "n_tiles": info["n_tiles"], "device_GB": info["device_bytes"] / 1e9},
         }
         print(json.dumps(out), flush=True)

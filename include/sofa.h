@@ -150,8 +150,23 @@ typedef struct {
   int32_t refine_filter; /* 1: before its FP32 distance, a candidate is bounded
                             from its int8 copy (triangle inequality with the
                             stored quantisation error); needs precision 1      */
+  int32_t use_graph;    /* 1: each batch shape is run once eagerly and recorded
+                           as a CUDA graph, later batches of that shape replay
+                           it (inputs and outputs staged through fixed buffers;
+                           a batch whose candidate pool ran full is recomputed
+                           eagerly).  Ignored while profiling is on.            */
 } sofa_tuning;
 int sofa_set_tuning(sofa_handle h, const sofa_tuning* t);
+
+/* Autotuner: times candidate tunings (unit size, seed window and count, the
+ * refinement filter when the index has its int8 copy) on Q sample queries
+ * (device memory) at this k, keeps the fastest and applies it to the handle.
+ * Every candidate returns the same exact answers.  cache_path (may be NULL):
+ * a text file of earlier choices, one line per (device, N, n, l, k bucket,
+ * Q bucket, filter, seed mode) key; a hit applies the stored choice without
+ * timing, a miss appends the new one.  chosen (may be NULL) receives it. */
+int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int32_t k, const char* cache_path,
+                  sofa_tuning* chosen, sofa_stream stream);
 
 /* Status word of the last sofa_query on this handle (after the caller has
  * synchronised the stream): 0 or a negative SOFA_ERR_* code. */
@@ -168,6 +183,8 @@ typedef struct {
   int64_t n_leaves;         /* leaf blocks in the index                          */
   int64_t n_tiles;          /* tiles in the index                                */
   int64_t filtered;         /* candidates read from the int8 copy only           */
+  int64_t graph_replays;    /* query batches answered by replaying a CUDA graph  */
+  int64_t graphs_recorded;  /* CUDA graphs recorded                              */
   double seed_dist_sum;     /* sum over queries of the seed's k-th distance      */
   double final_dist_sum;    /* sum over queries of the answer's k-th distance    */
 } sofa_stats_t;

@@ -18,8 +18,11 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+unsigned long long g_buf_generation = 0;
+
 int DevBuf::ensure(size_t want) {
   if (want <= bytes && p) return 0;
+  ++g_buf_generation;
   if (p) cudaFree(p);
   p = nullptr;
   bytes = 0;
@@ -106,10 +109,17 @@ static void free_index(Index* ix) {
                     &ix->qs.unit_off, &ix->qs.units, &ix->qs.cand_p, &ix->qs.cand_lb, &ix->qs.cand_n,
                     &ix->qs.qflag, &ix->qs.qslot, &ix->qs.chunk_d, &ix->qs.chunk_p, &ix->qs.chunk_n, &ix->qs.pool_q, &ix->qs.pool_p, &ix->qs.pool_lb,
                     &ix->qs.pool_sp, &ix->qs.pool_slb, &ix->qs.qpool_cnt, &ix->qs.qpool_off, &ix->qs.qcursor,
-                    &ix->qs.choff, &ix->qs.chunk_q, &ix->qs.qof, &ix->qs.counters, &ix->qs.stage_in, &ix->qs.stage_out, &ix->qs.pinned_dummy};
+                    &ix->qs.choff, &ix->qs.chunk_q, &ix->qs.qof, &ix->qs.counters, &ix->qs.stage_in, &ix->qs.stage_out, &ix->qs.graph_in, &ix->qs.graph_out, &ix->qs.pinned_dummy};
   for (DevBuf* b : bufs) b->release();
   if (ix->mlp) mlp_free(ix->mlp);
   ix->prof.release();
+  for (auto& g : ix->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  ix->graphs.clear();
+  if (ix->gstream) cudaStreamDestroy(ix->gstream);
+  for (cudaEvent_t e : ix->gev)
+    if (e) cudaEventDestroy(e);
+  if (ix->qs.h_pinned) cudaFreeHost(ix->qs.h_pinned);
   delete static_cast<sofa_index*>(ix);
 }
 
@@ -250,6 +260,8 @@ int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset) {
   out->refined = (int64_t)c[3];
   out->overflow_passes = h->stats[5];
   out->filtered = (int64_t)c[12];
+  out->graph_replays = h->stats[6];
+  out->graphs_recorded = h->stats[7];
   out->seed_dist_sum = (double)c[6] * 1e-6;
   out->final_dist_sum = (double)c[7] * 1e-6;
   out->n_leaves = h->L;
@@ -262,6 +274,7 @@ int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset) {
     }
     h->stats[0] = 0;
     h->stats[5] = 0;
+    h->stats[6] = 0;
   }
   return 0;
 }
@@ -277,6 +290,7 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   if (t->pool_cap < 0 || t->pool_cap > ((int64_t)1 << 30)) return fail(SOFA_ERR_INVALID_ARG, "pool_cap must lie in [0, 2^30]");
   if (t->refine_filter < 0 || t->refine_filter > 1) return fail(SOFA_ERR_INVALID_ARG, "refine_filter must be 0 or 1");
   if (t->refine_filter == 1 && !h->Z8) return fail(SOFA_ERR_INVALID_ARG, "refine_filter needs an index built with precision 1");
+  if (t->use_graph < 0 || t->use_graph > 1) return fail(SOFA_ERR_INVALID_ARG, "use_graph must be 0 or 1");
   h->group = t->group ? t->group : 64;
   h->cand_cap = t->cand_cap ? t->cand_cap : 65536;
   h->seed_count = t->seed_count ? t->seed_count : 128;
@@ -284,6 +298,7 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   h->bound_precision = t->bound_precision;
   h->pool_cap = t->pool_cap;
   h->refine_filter = t->refine_filter;
+  h->use_graph = t->use_graph;
   return 0;
 }
 

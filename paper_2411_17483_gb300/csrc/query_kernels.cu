@@ -1286,9 +1286,13 @@ static QueryParams make_params(const Index* ix, int k) {
   return P;
 }
 
+// One batch of queries.  With `capturing` the sequence is being recorded into
+// a CUDA graph: every buffer has been sized by an earlier eager call, the
+// routed-list sizes are upper bounds instead of read-back totals, and only the
+// first scan pass is recorded (a full pool is detected after the replay).
 template <int LW, bool NYQ>
 static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* idx, float* dist,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool capturing = false) {
   QueryScratch& s = ix->qs;
   const int n = ix->n, NB = ix->NB;
   const int64_t L = ix->L;
@@ -1359,9 +1363,15 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   int* qsel = nullptr;     // queries scanned in this pass (all in the first)
   int* qslot = nullptr;    // their candidate-buffer slots (identity in the first)
   int* qflag_out = s.qflag.as<int>();
-  int* h_over = nullptr;
-  SOFA_CUDA(cudaMallocHost((void**)&h_over, sizeof(int)));
+  if (!s.h_pinned) SOFA_CUDA(cudaMallocHost((void**)&s.h_pinned, 4 * sizeof(int)));
+  int* h_over = s.h_pinned;
   std::vector<int> hflag, hslot;
+  // graph-eligible batches size the routed lists by their upper bounds
+  const bool upper = ix->use_graph && Q * L <= ((int64_t)1 << 28);
+  if (upper) {
+    TRYQ(s.leaf_q.ensure(((size_t)Q * L + 1) * sizeof(int)));
+    TRYQ(s.units.ensure(((size_t)(Q * L / P.group + L) + 1) * sizeof(int4)));
+  }
   int rc = 0;
   int64_t slots = Q;
   int* qof = nullptr;  // slot -> query (identity in the first pass)
@@ -1413,12 +1423,15 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     SOFA_CUDA(cudaGetLastError());
     // sizes of the routed list and the unit list are only known on the device:
     // read the two totals back (one small copy per pass)
-    int tot[2];
-    SOFA_CUDA(cudaMemcpyAsync(&tot[0], s.leaf_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SOFA_CUDA(cudaMemcpyAsync(&tot[1], s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SOFA_CUDA(cudaStreamSynchronize(st));
-    TRYQ(s.leaf_q.ensure(((size_t)tot[0] + 1) * sizeof(int)));
-    TRYQ(s.units.ensure(((size_t)tot[1] + 1) * sizeof(int4)));
+    if (!(upper && pass == 0)) {
+      if (capturing) return fail(SOFA_ERR_CUDA, "capture needs upper-bound buffers");
+      int* tot = h_over + 2;
+      SOFA_CUDA(cudaMemcpyAsync(&tot[0], s.leaf_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SOFA_CUDA(cudaMemcpyAsync(&tot[1], s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SOFA_CUDA(cudaStreamSynchronize(st));
+      TRYQ(s.leaf_q.ensure(((size_t)tot[0] + 1) * sizeof(int)));
+      TRYQ(s.units.ensure(((size_t)tot[1] + 1) * sizeof(int4)));
+    }
     ix->prof.begin(2, st, 2);
     k_route_fill<<<rb, 256, 0, st>>>(Q, L, llb, thr, qsel, s.leaf_off.as<int>(), cursor, s.leaf_q.as<int>());
     k_units<<<(unsigned)ceil_div(L, 256), 256, 0, st>>>(L, P.group, s.leaf_cnt.as<int>(), s.leaf_off.as<int>(),
@@ -1459,6 +1472,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
                                          qflag_out, n_overflow, status);
     ix->prof.end(st);
     SOFA_CUDA(cudaGetLastError());
+    if (capturing) break;  // a full pool is detected after the replay
     SOFA_CUDA(cudaMemcpyAsync(h_over, n_overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
     SOFA_CUDA(cudaStreamSynchronize(st));
     if (*h_over == 0) break;
@@ -1491,13 +1505,98 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     qflag_out = (qflag_out == s.qflag.as<int>()) ? s.qflag.as<int>() + Q : s.qflag.as<int>();
     qsel = prev;
   }
-  cudaFreeHost(h_over);
   if (rc) return rc;
   ix->prof.begin(5, st);
   k_final<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(), idx,
                                          dist, counters);
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
+static int dispatch_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* ip, float* dp, cudaStream_t st,
+                          bool capturing) {
+  if (ix->LW == 16)
+    return ix->nyq_first ? query_batch<16, true>(ix, qp, qb, k, ip, dp, st, capturing)
+                         : query_batch<16, false>(ix, qp, qb, k, ip, dp, st, capturing);
+  return ix->nyq_first ? query_batch<32, true>(ix, qp, qb, k, ip, dp, st, capturing)
+                       : query_batch<32, false>(ix, qp, qb, k, ip, dp, st, capturing);
+}
+
+// A batch through a recorded CUDA graph.  The first batch of a shape runs
+// eagerly (sizing every buffer and producing its answers) and is then recorded
+// from fixed staging buffers; later batches copy their queries in, replay the
+// graph and copy the answers out.  If a replay's candidate pool ran full, the
+// batch is recomputed eagerly, so answers are always exact.
+static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* ip, float* dp, cudaStream_t st) {
+  QueryScratch& s = ix->qs;
+  if (!ix->gstream) {
+    SOFA_CUDA(cudaStreamCreateWithFlags(&ix->gstream, cudaStreamNonBlocking));
+    SOFA_CUDA(cudaEventCreateWithFlags(&ix->gev[0], cudaEventDisableTiming));
+    SOFA_CUDA(cudaEventCreateWithFlags(&ix->gev[1], cudaEventDisableTiming));
+  }
+  const int64_t key[12] = {qb, k, ix->bound_precision, ix->refine_filter, ix->seed_mode, ix->group, ix->cand_cap,
+                           ix->seed_count, ix->seed_window, ix->pool_cap, ix->LW, ix->nyq_first};
+  Index::GraphEntry* e = nullptr;
+  for (auto& g : ix->graphs)
+    if (std::equal(key, key + 12, g.key)) e = &g;
+  if (e && !e->failed && e->gen != g_buf_generation) {  // buffers moved since the recording
+    cudaGraphExecDestroy(e->exec);
+    e->exec = nullptr;
+    e = nullptr;
+    ix->graphs.erase(std::remove_if(ix->graphs.begin(), ix->graphs.end(),
+                                    [&](const Index::GraphEntry& g) { return std::equal(key, key + 12, g.key); }),
+                     ix->graphs.end());
+  }
+  if (e && e->failed) return dispatch_batch(ix, qp, qb, k, ip, dp, st, false);
+  if (!e) {
+    TRYQ(s.graph_in.ensure((size_t)qb * ix->n * sizeof(float)));
+    TRYQ(s.graph_out.ensure((size_t)qb * k * (sizeof(int64_t) + sizeof(float))));
+    TRYQ(dispatch_batch(ix, qp, qb, k, ip, dp, st, false));  // sizes every buffer; the answers
+    SOFA_CUDA(cudaStreamSynchronize(st));
+    const unsigned long long gen0 = g_buf_generation;
+    Index::GraphEntry ne;
+    std::copy(key, key + 12, ne.key);
+    ne.exec = nullptr;
+    ne.failed = true;
+    const bool prof_on = ix->prof.on;
+    ix->prof.on = false;
+    cudaGraph_t graph = nullptr;
+    int rc = 0;
+    if (cudaStreamBeginCapture(ix->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      int64_t* gi = s.graph_out.as<int64_t>();
+      float* gd = reinterpret_cast<float*>(gi + qb * k);
+      rc = dispatch_batch(ix, s.graph_in.as<float>(), qb, k, gi, gd, ix->gstream, true);
+      cudaError_t ec = cudaStreamEndCapture(ix->gstream, &graph);
+      if (!rc && ec == cudaSuccess && graph && g_buf_generation == gen0 &&
+          cudaGraphInstantiate(&ne.exec, graph, 0) == cudaSuccess)
+        ne.failed = false;
+    }
+    cudaGetLastError();  // a refused recording only disables the graph for this shape
+    if (graph) cudaGraphDestroy(graph);
+    ix->prof.on = prof_on;
+    ne.gen = g_buf_generation;
+    if (!ne.failed) ix->stats[7] += 1;
+    ix->graphs.push_back(ne);
+    (void)rc;
+    return 0;
+  }
+  SOFA_CUDA(cudaEventRecord(ix->gev[0], st));
+  SOFA_CUDA(cudaStreamWaitEvent(ix->gstream, ix->gev[0], 0));
+  SOFA_CUDA(cudaMemcpyAsync(s.graph_in.p, qp, (size_t)qb * ix->n * sizeof(float), cudaMemcpyDeviceToDevice,
+                            ix->gstream));
+  SOFA_CUDA(cudaGraphLaunch(e->exec, ix->gstream));
+  ix->stats[6] += 1;
+  int* status = reinterpret_cast<int*>(s.counters.as<unsigned long long>() + 8);
+  SOFA_CUDA(cudaMemcpyAsync(s.h_pinned, status + 1, sizeof(int), cudaMemcpyDeviceToHost, ix->gstream));
+  SOFA_CUDA(cudaStreamSynchronize(ix->gstream));
+  if (*s.h_pinned > 0) return dispatch_batch(ix, qp, qb, k, ip, dp, st, false);  // pool ran full
+  int64_t* gi = s.graph_out.as<int64_t>();
+  float* gd = reinterpret_cast<float*>(gi + qb * k);
+  SOFA_CUDA(cudaMemcpyAsync(ip, gi, (size_t)qb * k * sizeof(int64_t), cudaMemcpyDeviceToDevice, ix->gstream));
+  SOFA_CUDA(cudaMemcpyAsync(dp, gd, (size_t)qb * k * sizeof(float), cudaMemcpyDeviceToDevice, ix->gstream));
+  SOFA_CUDA(cudaEventRecord(ix->gev[1], ix->gstream));
+  SOFA_CUDA(cudaStreamWaitEvent(st, ix->gev[1], 0));
   return 0;
 }
 
@@ -1514,11 +1613,8 @@ int run_query(Index* ix, const float* q, int64_t Q, int k, int64_t* idx, float* 
     const float* qp = q + q0 * ix->n;
     int64_t* ip = idx + q0 * k;
     float* dp = dist + q0 * k;
-    int rc;
-    if (ix->LW == 16)
-      rc = ix->nyq_first ? query_batch<16, true>(ix, qp, qb, k, ip, dp, st) : query_batch<16, false>(ix, qp, qb, k, ip, dp, st);
-    else
-      rc = ix->nyq_first ? query_batch<32, true>(ix, qp, qb, k, ip, dp, st) : query_batch<32, false>(ix, qp, qb, k, ip, dp, st);
+    const bool graph = ix->use_graph && !ix->prof.on && qb * ix->L <= ((int64_t)1 << 28);
+    int rc = graph ? graph_batch(ix, qp, qb, k, ip, dp, st) : dispatch_batch(ix, qp, qb, k, ip, dp, st, false);
     if (rc) return rc;
   }
   ix->stats[0] += Q;

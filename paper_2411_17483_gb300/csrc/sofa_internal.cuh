@@ -31,6 +31,10 @@ int fail(int code, const std::string& msg);
                           std::string(#call) + ": " + cudaGetErrorString(e_));        \
   } while (0)
 
+// Bumped whenever any scratch buffer is reallocated: recorded graphs that
+// captured older addresses are then discarded.
+extern unsigned long long g_buf_generation;
+
 // Device buffers that grow on demand and are reused across calls.
 struct DevBuf {
   void* p = nullptr;
@@ -66,6 +70,8 @@ struct QueryScratch {
   DevBuf chunk_p;
   DevBuf chunk_n;
   DevBuf counters;  // misc device counters (int64)
+  DevBuf graph_in, graph_out;  // fixed input / output of recorded query graphs
+  int* h_pinned = nullptr;      // pinned host words for small read-backs
   DevBuf stage_in;  // staging for host queries
   DevBuf stage_out;
   DevBuf pinned_dummy;
@@ -128,6 +134,16 @@ struct Index {
   int bound_precision = 0;     // 0 FP32 series bounds, 1 FP16x2 series bounds
   int64_t pool_cap = 0;        // shared candidate pool entries (0: automatic)
   int refine_filter = 0;       // 1: int8 filter before the FP32 distance
+  int use_graph = 0;           // 1: replay recorded CUDA graphs of query batches
+  struct GraphEntry {
+    int64_t key[12];
+    unsigned long long gen;
+    cudaGraphExec_t exec;
+    bool failed;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
   int status = 0;
   int64_t stats[8] = {0};
   Mlp* mlp = nullptr;

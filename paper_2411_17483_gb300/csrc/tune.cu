@@ -1,0 +1,165 @@
+// Autotuner: picks the run-time tuning of an index by timing candidate
+// settings on a sample of queries.  Every setting returns the same exact
+// answers, so the choice only affects speed.  Choices can be cached in a text
+// file, one line per (device, N, n, l, k bucket, Q bucket) key.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "sofa_internal.cuh"
+
+namespace sofa {
+
+static std::string tune_key(const Index* ix, int k, int64_t Q) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::memset(&prop, 0, sizeof(prop));
+  cudaGetDeviceProperties(&prop, dev);
+  int kb = k <= 1 ? 1 : k <= 8 ? 8 : 64;
+  int64_t qb = Q <= 256 ? 256 : Q <= 4096 ? 4096 : 65536;
+  std::ostringstream s;
+  s << prop.name << "|N=" << ix->N << "|n=" << ix->n << "|l=" << ix->l << "|k<=" << kb << "|Q<=" << qb
+    << "|filter=" << (ix->Z8 ? 1 : 0) << "|learned=" << ix->seed_mode;
+  std::string key = s.str();
+  for (char& c : key)
+    if (c == ' ') c = '_';
+  return key;
+}
+
+static bool cache_lookup(const char* path, const std::string& key, sofa_tuning* t) {
+  if (!path) return false;
+  std::ifstream in(path);
+  std::string line;
+  while (std::getline(in, line)) {
+    std::istringstream ls(line);
+    std::string k;
+    sofa_tuning c;
+    std::memset(&c, 0, sizeof(c));
+    long long pool = 0;
+    if (ls >> k >> c.group >> c.cand_cap >> c.seed_count >> c.seed_window >> c.bound_precision >> pool >>
+        c.refine_filter) {
+      c.pool_cap = pool;
+      if (k == key) {
+        *t = c;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+static void cache_store(const char* path, const std::string& key, const sofa_tuning& c) {
+  if (!path) return;
+  std::ofstream out(path, std::ios::app);
+  out << key << " " << c.group << " " << c.cand_cap << " " << c.seed_count << " " << c.seed_window << " "
+      << c.bound_precision << " " << (long long)c.pool_cap << " " << c.refine_filter << "\n";
+}
+
+static void apply(Index* ix, const sofa_tuning& t) {
+  ix->group = t.group;
+  ix->cand_cap = t.cand_cap;
+  ix->seed_count = t.seed_count;
+  ix->seed_window = t.seed_window;
+  ix->bound_precision = t.bound_precision;
+  ix->pool_cap = t.pool_cap;
+  ix->refine_filter = t.refine_filter;
+  ix->use_graph = t.use_graph;
+}
+
+}  // namespace sofa
+
+using namespace sofa;
+
+extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int32_t k, const char* cache_path,
+                             sofa_tuning* chosen, sofa_stream stream) {
+  if (!h || !queries || Q < 1 || k < 1 || k > SOFA_MAX_K || k > h->N)
+    return fail(SOFA_ERR_INVALID_ARG, "bad autotune argument");
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, queries) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(SOFA_ERR_INVALID_ARG, "autotune queries must be device memory");
+  }
+  Index* ix = h;
+  cudaStream_t st = (cudaStream_t)stream;
+  const std::string key = tune_key(ix, k, Q);
+  sofa_tuning best;
+  std::memset(&best, 0, sizeof(best));
+  if (cache_lookup(cache_path, key, &best)) {
+    apply(ix, best);
+    if (chosen) *chosen = best;
+    return 0;
+  }
+  // candidate grid (all exact); the current setting is the first candidate
+  std::vector<sofa_tuning> cands;
+  sofa_tuning cur;
+  std::memset(&cur, 0, sizeof(cur));
+  cur.group = ix->group;
+  cur.cand_cap = ix->cand_cap;
+  cur.seed_count = ix->seed_count;
+  cur.seed_window = ix->seed_window;
+  cur.bound_precision = ix->bound_precision;
+  cur.pool_cap = ix->pool_cap;
+  cur.refine_filter = ix->refine_filter;
+  cur.use_graph = ix->use_graph;
+  cands.push_back(cur);
+  const int groups[] = {32, 64};
+  const int windows[] = {1024, 4096};
+  const int counts[] = {64, 128, 256};
+  for (int g : groups)
+    for (int w : windows)
+      for (int c : counts)
+        for (int f = 0; f <= (ix->Z8 ? 1 : 0); ++f) {
+          sofa_tuning t = cur;
+          t.group = g;
+          t.seed_window = w;
+          t.seed_count = c;
+          t.refine_filter = f;
+          t.bound_precision = 0;
+          cands.push_back(t);
+        }
+  DevBuf outi, outd;
+  if (int rc = outi.ensure((size_t)Q * k * sizeof(int64_t))) return rc;
+  if (int rc = outd.ensure((size_t)Q * k * sizeof(float))) return rc;
+  cudaEvent_t e0, e1;
+  SOFA_CUDA(cudaEventCreate(&e0));
+  SOFA_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int rc = 0;
+  for (const sofa_tuning& t : cands) {
+    apply(ix, t);
+    rc = run_query(ix, queries, Q, k, outi.as<int64_t>(), outd.as<float>(), st);  // warm-up
+    if (rc) break;
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 2 && !rc; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = run_query(ix, queries, Q, k, outi.as<int64_t>(), outd.as<float>(), st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(SOFA_ERR_CUDA, "autotune timing failed");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_min = std::min(ms_min, ms);
+    }
+    if (rc) break;
+    if (ms_min < best_ms) {
+      best_ms = ms_min;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  outi.release();
+  outd.release();
+  if (rc) {
+    apply(ix, cur);
+    return rc;
+  }
+  apply(ix, best);
+  cache_store(cache_path, key, best);
+  if (chosen) *chosen = best;
+  return 0;
+}

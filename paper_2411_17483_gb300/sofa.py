@@ -45,13 +45,14 @@ class TrainOpts(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("cand_cap", ctypes.c_int32), ("seed_count", ctypes.c_int32),
                 ("seed_window", ctypes.c_int32), ("bound_precision", ctypes.c_int32), ("pool_cap", ctypes.c_int64),
-                ("refine_filter", ctypes.c_int32)]
+                ("refine_filter", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in
                 ("queries", "leaf_pairs", "tile_pairs", "candidates", "refined", "overflow_passes",
-                 "n_leaves", "n_tiles", "filtered")] + [("seed_dist_sum", ctypes.c_double),
+                 "n_leaves", "n_tiles", "filtered", "graph_replays", "graphs_recorded")] + [
+                    ("seed_dist_sum", ctypes.c_double),
                                                         ("final_dist_sum", ctypes.c_double)]
 
 
@@ -94,6 +95,7 @@ def load():
         "sofa_set_seed_mode": (ctypes.c_int, [P, i32]),
         "sofa_mlp_grad": (ctypes.c_int, [i32, i32, i32, P, P, P, i32, P, ctypes.POINTER(ctypes.c_float), P]),
         "sofa_set_tuning": (ctypes.c_int, [P, ctypes.POINTER(Tuning)]),
+        "sofa_autotune": (ctypes.c_int, [P, P, i64, i32, ctypes.c_char_p, ctypes.POINTER(Tuning), P]),
         "sofa_query_status": (ctypes.c_int, [P]),
         "sofa_stats": (ctypes.c_int, [P, ctypes.POINTER(Stats), i32]),
         "sofa_info": (ctypes.c_int, [P, ctypes.POINTER(Info)]),
@@ -188,9 +190,17 @@ class Index:
         return idx, dist
 
     def set_tuning(self, group=0, cand_cap=0, seed_count=0, seed_window=0, bound_precision=0, pool_cap=0,
-                   refine_filter=0):
-        t = Tuning(group, cand_cap, seed_count, seed_window, bound_precision, pool_cap, refine_filter)
+                   refine_filter=0, use_graph=0):
+        t = Tuning(group, cand_cap, seed_count, seed_window, bound_precision, pool_cap, refine_filter, use_graph)
         _check(load().sofa_set_tuning(self.h, ctypes.byref(t)))
+
+    def autotune(self, q: torch.Tensor, k: int = 1, cache_path: str | None = None, stream=None) -> dict:
+        """Time candidate tunings on the sample queries q, apply the fastest."""
+        q = q.contiguous()
+        t = Tuning()
+        _check(load().sofa_autotune(self.h, _ptr(q), q.shape[0], k,
+                                    cache_path.encode() if cache_path else None, ctypes.byref(t), _stream(stream)))
+        return {name: getattr(t, name) for name, _ in Tuning._fields_}
 
     def set_seed_mode(self, mode: int):
         _check(load().sofa_set_seed_mode(self.h, mode))

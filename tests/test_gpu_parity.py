@@ -247,3 +247,41 @@ def test_query_multi(sofa):
         assert list(idx[oo[i]:oo[i] + qk[i]].cpu().numpy()) == list(oi[0])
     for ix in ixs:
         ix.close()
+
+
+def test_autotune_keeps_answers_and_caches(sofa, tmp_path):
+    N, n = 40000, 128
+    x = datagen.random_walks(N, n, seed=61, device=DEV)
+    q = datagen.half_perturbed_queries(x, 64, seed=62)
+    ix = sofa.Index(x, 16, 256, precision=1)
+    gi0, gd0 = ix.query(q, 3)
+    cache = str(tmp_path / "tune.txt")
+    t1 = ix.autotune(q, 3, cache)
+    gi1, gd1 = ix.query(q, 3)
+    assert torch.equal(gi0, gi1) and torch.equal(gd0, gd1)
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1
+    ix.set_tuning()                          # back to defaults, then a cache hit
+    t2 = ix.autotune(q, 3, cache)
+    assert t1 == t2 and len(open(cache).read().splitlines()) == 1
+    ix.close()
+
+
+@pytest.mark.parametrize("extra", [dict(), dict(pool_cap=3, cand_cap=2), dict(refine_filter=1)])
+def test_graph_replay_matches_eager(sofa, extra):
+    N, n = 50000, 128
+    x = datagen.mixed_walks(N, n, seed=71, device=DEV)
+    ix = sofa.Index(x, 16, 256, precision=1)
+    batches = [datagen.half_perturbed_queries(x, 96, seed=72 + i) for i in range(4)]
+    ix.set_tuning(**extra)
+    eager = [ix.query(q, 4) for q in batches]
+    ix.set_tuning(use_graph=1, **extra)
+    for _ in range(2):                      # first call records, later calls replay
+        for q, (ei, ed) in zip(batches, eager):
+            gi, gd = ix.query(q, 4)
+            torch.cuda.synchronize()
+            assert torch.equal(gi, ei) and torch.equal(gd, ed)
+    assert ix.status() == 0
+    st = ix.stats()
+    assert st["graphs_recorded"] >= 1 and st["graph_replays"] >= 4
+    ix.close()
