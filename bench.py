@@ -52,6 +52,26 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM traffic of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum
+# per launch, averaged over the two launches of one step: the 8192- and the
+# 1808-query batch) from one ncu capture of the default workload, chosen mode;
+# summary and command in profiles/k_scan_dram_rw100M_q10k.md.  Reported only
+# while the kernel's source is the one that was captured.
+SCAN_TRAFFIC = {"bytes_per_launch": 6093278592, "source_sha": "dcf394f6580b02b9",
+                "workload": (100_000_000, 256, 10_000, 1, 16)}
+
+
+def kernel_source_sha(name="k_scan"):
+    """sha256 (16 hex digits) of a kernel template's text in query_kernels.cu."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_2411_17483_gb300", "csrc", "query_kernels.cu")
+    s = open(path).read()
+    i = s.index(f"{name}(QueryParams P")
+    a = s.rindex("template <", 0, i)
+    b = s.index("\n}\n", i) + 3
+    return hashlib.sha256(s[a:b].encode()).hexdigest()[:16]
+
+
 def workload_name(a):
     return f"random walks {a.N}x{a.n} fp32, {a.Q} fresh random-walk queries, exact {a.k}-NN, l={a.l}, alphabet {a.alphabet}"
 
@@ -263,6 +283,9 @@ def run_sofa(a, ws, rank, local):
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         clocks = clk.stop()
+        code = ix.status()
+        if code != 0:
+            raise RuntimeError(f"query status {code} in mode {mode_name}: answers not valid")
         barrier(ws)
         ix.set_profiling(False)
         prof = ix.profile(reset=True)
@@ -293,19 +316,28 @@ def run_sofa(a, ws, rank, local):
         hbm.update(achieved=ach, frac=ach / hbm_peak)
     roof = hbm
     if phase == "scan":
-        # ALU roofline: one (query, series) bound is LW interval distances of 4
-        # FP32 instructions each; peak = SMs x 128 lanes x SM clock / (4 LW)
+        # ALU roofline: one (query, series) bound needs, per value, 3 FP32 lane
+        # operations (q - c, the scaled clamp, the square-accumulate); the FP32
+        # pipe does 128 lane operations per SM per clock, packed or not:
+        # peak = SMs x 128 x SM clock / (3 LW)
         clk = (r["clocks"].get("sm_mhz") or 1920.0) * 1e6
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_b = sms * 128 * clk / (4 * LW) / 1e9
+        peak_b = sms * 128 * clk / (3 * LW) / 1e9
         bounds = stats["tile_pairs"] * 256 / launches
         ach_b = bounds / per_launch_s / 1e9
+        traffic = None
+        if ((a.N, a.n, a.Q, a.k, a.l) == SCAN_TRAFFIC["workload"] and chosen == "learned"
+                and kernel_source_sha("k_scan") == SCAN_TRAFFIC["source_sha"]):
+            traffic = SCAN_TRAFFIC["bytes_per_launch"]
+        hbm["traffic"] = traffic
         roof = {"kernel": "scan", "bound": "alu", "achieved": ach_b, "peak": peak_b,
-                "unit": "G (query, series) bounds/s", "frac": ach_b / peak_b, "traffic": None,
-                "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz / (4 x {LW})",
+                "unit": "G (query, series) bounds/s", "frac": ach_b / peak_b, "traffic": traffic,
+                "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz / (3 x {LW})",
                 "hbm_view": hbm}
-    # whole-step algorithmic bytes (SFA words scanned per query + refined raw series)
-    step_bytes = ((stats["tile_pairs"] * 256 * LW) + stats["refined"] * a.n * 4) / a.steps
+    # whole-step algorithmic bytes (SFA words scanned per query + int8 rows
+    # filtered + refined raw series)
+    step_bytes = ((stats["tile_pairs"] * 256 * LW) + stats["refined"] * a.n * 4
+                  + stats.get("filtered", 0) * a.n) / a.steps
     step_roof = step_bytes / (r["ms"] / 1e3) / 1e9
 
     # end to end through the public API with host buffers

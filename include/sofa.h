@@ -43,7 +43,10 @@ enum {
   SOFA_ERR_CUDA = -3,         /* a CUDA call failed; see sofa_last_error()      */
   SOFA_ERR_TIMEOUT = -4,      /* a bounded device wait ran out                  */
   SOFA_ERR_NOT_TRAINED = -5,  /* learned seeding asked for before training      */
-  SOFA_ERR_TIE_OVERFLOW = -6  /* more near-tied results than the kept list holds */
+  SOFA_ERR_TIE_OVERFLOW = -6, /* more near-tied results than the kept list holds */
+  SOFA_ERR_INTERNAL = -7      /* a device-side consistency check failed: a
+                                 candidate position out of range was skipped,
+                                 so the answers of that call are not valid      */
 };
 
 /* Limits. */

@@ -348,6 +348,49 @@ def knn(Z: np.ndarray, Zq: np.ndarray, k: int):
     return idx, dist
 
 
+def knn_chunked(chunks, Zq: np.ndarray, k: int, keep: int = 64):
+    """Same result as knn_full over a dataset too large to hold at once.
+    `chunks` yields (row0, Z_chunk) with the canonical rows row0.. of the
+    dataset, in any order, covering every row once.  Per query, each chunk
+    contributes its k + keep smallest squared distances; the merged set is then
+    cut by the rule of `knn` (d <= D_k + 1e-6 D_k) and ordered by tie_order.
+    A chunk whose (k + keep)-th distance lies inside the final window could
+    have dropped a member of it: that raises instead of returning a guess."""
+    Q = Zq.shape[0]
+    m = k + keep
+    best_d2 = [np.empty(0, np.float64) for _ in range(Q)]
+    best_id = [np.empty(0, np.int64) for _ in range(Q)]
+    cuts = [[] for _ in range(Q)]  # squared distance of the last kept row of a truncated chunk
+    total = 0
+    for row0, Zc in chunks:
+        rows = Zc.shape[0]
+        total += rows
+        for q in range(Q):
+            d2 = sqdist(Zc, Zq[q])
+            if rows > m:
+                sel = np.argpartition(d2, m - 1)[:m]
+                cuts[q].append(float(d2[sel].max()))
+            else:
+                sel = np.arange(rows)
+            best_d2[q] = np.concatenate([best_d2[q], d2[sel]])
+            best_id[q] = np.concatenate([best_id[q], sel.astype(np.int64) + int(row0)])
+    if k > total:
+        raise ValueError("k > N")
+    idx = np.empty((Q, k), np.int64)
+    dist = np.empty((Q, k), np.float64)
+    for q in range(Q):
+        d = np.sqrt(best_d2[q])
+        Dk = np.partition(d, k - 1)[k - 1]
+        lim = Dk + 1e-6 * Dk
+        if cuts[q] and np.sqrt(min(cuts[q])) <= lim:
+            raise RuntimeError("a chunk's kept distances do not cover the tie window: raise `keep`")
+        sel = np.nonzero(d <= lim)[0]
+        oi, od = tie_order(best_d2[q][sel], best_id[q][sel])
+        idx[q] = oi[:k]
+        dist[q] = od[:k]
+    return idx, dist
+
+
 def gemini_knn(Z: np.ndarray, W: np.ndarray, Zq: np.ndarray, summ, k: int):
     """GEMINI filter-and-refine (Sec. II-A, Sec. IV "Exact Similarity Search"):
     visit series in ascending SFA lower bound, compute the exact distance only

@@ -816,7 +816,7 @@ __global__ void k_chunk_fill(int64_t slots, int cap, const int* __restrict__ can
 // The first candidate whose bound exceeds the threshold ends the chunk.
 constexpr int RROUND = 64;  // candidates refined per round: 8 warps x 8 groups of 4 lanes
 template <bool FILTER>
-__global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __restrict__ n_chunks_ptr,
+__global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, const int* __restrict__ n_chunks_ptr,
                                                 const int* __restrict__ chunk_q, const int* __restrict__ choff,
                                                 const int* __restrict__ qof, const float* __restrict__ zq,
                                                 const float* __restrict__ Z, const uint32_t* __restrict__ cand_p,
@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __rest
   __shared__ uint32_t slp[KCAP];
   __shared__ float acc_d[RROUND];
   __shared__ uint32_t acc_p[RROUND];
-  __shared__ int s_nacc, s_nl, s_stop, s_lost, s_nsurv;
+  __shared__ int s_nacc, s_nl, s_lost, s_nsurv, s_stop0;  // s_stop0: thread 0 only
   __shared__ float s_lim, s_T0;
   __shared__ uint32_t surv[FILTER ? 256 : 1];
   constexpr int NBK = 32;  // bound buckets of a chunk
@@ -857,7 +857,6 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __rest
   volatile float* vthr = thr;
   if (tid == 0) {
     s_nl = 0;
-    s_stop = 0;
     s_lost = 0;
     s_lim = INFINITY;
     s_nacc = 0;
@@ -875,6 +874,10 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __rest
     unsigned long long kk;
     if (e < r) kk = pack_key(cand_lb[(int64_t)slot_q * P.cap + e], cand_p[(int64_t)slot_q * P.cap + e]);
     else kk = pack_key(slb[qpool_off[slot_q] + (e - r)], sp[qpool_off[slot_q] + (e - r)]);
+    if ((uint32_t)kk >= P.N) {  // consistency check: record it; the NaN key below drops the entry
+      atomicExch(status, SOFA_ERR_INTERNAL);
+      kk = ~0ull;
+    }
     skey[i] = kk;
     const float lb = __uint_as_float((uint32_t)(kk >> 32));
     const int b = lb <= T0 ? min(NBK - 1, (int)(lb * bscale)) : NBK;
@@ -949,9 +952,13 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __rest
     // units); only survivors get the FP32 distance, by groups of 4 lanes
     for (int base = 0; base < nlive; base += 256) {
       const float T = vthr[q];
+      // thread 0's verdict (every later bucket starts above T) is kept in a
+      // word only thread 0 touches and joined by __syncthreads_or at the end
+      // of the round: no shared flag that the next round could overwrite
+      // while a warp still reads it
       if (tid == 0) {
         s_nsurv = 0;
-        if (edge_of(base) > T) s_stop = 1;  // every later bucket starts above T
+        s_stop0 = edge_of(base) > T;
       }
       __syncthreads();
       if ((P.n & 15) == 0) {
@@ -1045,7 +1052,7 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __rest
         if (tid == 0) merge_round();
         __syncthreads();
       }
-      if (s_stop) break;
+      if (__syncthreads_or(tid == 0 && s_stop0)) break;
     }
   } else {
     for (int base = 0; base < nlive; base += RROUND) {
@@ -1060,7 +1067,7 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __rest
         active = lb <= T;
         if (active) p = (uint32_t)skey[i];
       }
-      if (tid == 0 && edge_of(base) > T) s_stop = 1;  // every later bucket starts above T
+      const bool stop_after = tid == 0 && edge_of(base) > T;  // every later bucket starts above T
       const float d2 = group4_sqdist(szq, Z, p, P.n, lane & 3, active);
       if ((lane & 3) == 0 && active) {
         ++refined;
@@ -1072,8 +1079,7 @@ __global__ void __launch_bounds__(256) k_refine(QueryParams P, const int* __rest
       }
       __syncthreads();
       if (tid == 0) merge_round();
-      __syncthreads();
-      if (s_stop) break;
+      if (__syncthreads_or(stop_after)) break;  // barrier and block-wide verdict in one
     }
   }
   const int nl = s_nl;
@@ -1175,7 +1181,7 @@ __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __res
                                                const float* __restrict__ Z, const uint32_t* __restrict__ perm,
                                                const uint32_t* __restrict__ list_p, const int* __restrict__ list_n,
                                                int64_t* __restrict__ idx, float* __restrict__ dist,
-                                               unsigned long long* __restrict__ counters) {
+                                               unsigned long long* __restrict__ counters, int* __restrict__ status) {
   extern __shared__ float dsm[];
   float* szq = dsm;
   __shared__ double sd[128];
@@ -1187,8 +1193,9 @@ __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __res
   __syncthreads();
   double d = INFINITY;
   uint32_t id = 0xFFFFFFFFu;
-  if (tid < nl) {
-    const uint32_t p = list_p[q * KCAP + tid];
+  const uint32_t p = tid < nl ? list_p[q * KCAP + tid] : 0u;
+  if (tid < nl && p >= P.N) atomicExch(status, SOFA_ERR_INTERNAL);  // consistency check: skip the row
+  if (tid < nl && p < P.N) {
     const float* row = Z + (int64_t)p * P.n;
     double acc = 0.0;
     for (int t = 0; t < P.n; ++t) {
@@ -1386,12 +1393,15 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   TRYQ(s.pool_slb.ensure((size_t)pool_cap * sizeof(float)));
   int* pool_n = status + 3;
   int* n_chunks = status + 4;
-  static int refine_blocks = 0;
+  // persistent refinement grid: resident CTAs of the instantiation that runs
+  auto refine_fn = (ix->refine_filter && ix->Z8) ? k_refine<true> : k_refine<false>;
+  static int refine_grid[2] = {0, 0};
+  int& refine_blocks = refine_grid[(ix->refine_filter && ix->Z8) ? 1 : 0];
   if (refine_blocks == 0) {
     int per_sm = 0, sms = 0, dev = 0;
     SOFA_CUDA(cudaGetDevice(&dev));
     SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SOFA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine<false>, 256, 4096));
+    SOFA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_fn, 256, nsm));
     refine_blocks = sms * (per_sm > 0 ? per_sm : 1);
   }
   for (int pass = 0;; ++pass) {
@@ -1457,7 +1467,6 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
                                                                   s.chunk_q.as<int>());
     ix->prof.end(st);
     ix->prof.begin(4, st, 2);
-    auto refine_fn = (ix->refine_filter && ix->Z8) ? k_refine<true> : k_refine<false>;
     const float one_minus_g = std::nextafter((float)(1.0 - (n + 4) * std::ldexp(1.0, -24) / (1.0 - (n + 4) * std::ldexp(1.0, -24))), 0.0f);
     refine_fn<<<refine_blocks, 256, nsm, st>>>(P, n_chunks, s.chunk_q.as<int>(), s.choff.as<int>(), qof, zq, ix->Z,
                                              s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(),
@@ -1508,7 +1517,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   if (rc) return rc;
   ix->prof.begin(5, st);
   k_final<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(), idx,
-                                         dist, counters);
+                                         dist, counters, status);
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
   return 0;

@@ -55,37 +55,52 @@ def random_walks(N: int, n: int, seed: int = 0, device="cpu", out: torch.Tensor 
     return out
 
 
-def mixed_walks(N: int, n: int, seed: int = 0, device="cpu") -> torch.Tensor:
-    """First half random walks, second half random walks plus N(0, 0.5^2) noise."""
+def mixed_walks(N: int, n: int, seed: int = 0, device="cpu", total: int | None = None,
+                row0: int = 0) -> torch.Tensor:
+    """Rows row0..row0+N-1 of a set of `total` rows (default N): the first
+    half random walks, the second half random walks plus N(0, 0.5^2) noise."""
+    total = N if total is None else total
     out = torch.empty((N, n), dtype=torch.float32, device=torch.device(device))
-    h = N // 2
-    random_walks(h, n, seed, device, out=out[:h])
-    random_walks(N - h, n, seed + 1, device, out=out[h:], noise_sigma=0.5)
+    h = total // 2
+    a = max(0, min(N, h - row0))        # rows of this range in the first half
+    if a > 0:
+        random_walks(a, n, seed, device, out=out[:a], row0=row0)
+    if N - a > 0:
+        random_walks(N - a, n, seed + 1, device, out=out[a:], noise_sigma=0.5, row0=row0 + a - h)
     return out
 
 
 def sinusoid_mix(N: int, n: int, seed: int = 0, device="cpu", n_waves: int = 8,
-                 noise_sigma: float = 0.3) -> torch.Tensor:
+                 noise_sigma: float = 0.3, row0: int = 0) -> torch.Tensor:
     """Sum of n_waves sinusoids with non-integer frequencies in (0, n/2) cycles
-    per series, uniform phases, LogNormal(0, 1) amplitudes, plus white noise."""
+    per series, uniform phases, LogNormal(0, 1) amplitudes, plus white noise;
+    rows row0..row0+N-1 of the seeded stream."""
     device = torch.device(device)
     out = torch.empty((N, n), dtype=torch.float32, device=device)
     t = torch.arange(n, dtype=torch.float64, device=device)
     done = 0
-    c = 0
     while done < N:
-        rows = min(CHUNK, N - done)
+        r = row0 + done
+        c = r // CHUNK
+        s0 = r - c * CHUNK
+        rows = min(CHUNK - s0, N - done)
         g = _gen(seed, c, device)
-        f = torch.rand((rows, n_waves), generator=g, dtype=torch.float64, device=device) * (n / 2)
-        ph = torch.rand((rows, n_waves), generator=g, dtype=torch.float64, device=device) * (2 * math.pi)
-        amp = torch.exp(torch.randn((rows, n_waves), generator=g, dtype=torch.float64, device=device))
+        f = torch.rand((CHUNK, n_waves), generator=g, dtype=torch.float64, device=device)[s0:s0 + rows] * (n / 2)
+        ph = torch.rand((CHUNK, n_waves), generator=g, dtype=torch.float64, device=device)[s0:s0 + rows]
+        ph = ph * (2 * math.pi)
+        amp = torch.exp(torch.randn((CHUNK, n_waves), generator=g, dtype=torch.float64, device=device)[s0:s0 + rows])
         x = torch.zeros((rows, n), dtype=torch.float64, device=device)
         for i in range(n_waves):
             x += amp[:, i:i + 1] * torch.sin(2 * math.pi * f[:, i:i + 1] * t[None, :] / n + ph[:, i:i + 1])
-        x += noise_sigma * torch.randn((rows, n), generator=g, dtype=torch.float64, device=device)
+        noise = torch.empty((rows, n), dtype=torch.float64, device=device)
+        for b in range(0, CHUNK, 2048):   # the chunk's noise in slabs, keeping only this range
+            lo, hi = max(b, s0), min(b + 2048, s0 + rows)
+            slab = torch.randn((2048, n), generator=g, dtype=torch.float64, device=device)
+            if lo < hi:
+                noise[lo - s0:hi - s0] = slab[lo - b:hi - b]
+        x += noise_sigma * noise
         out[done:done + rows] = x.to(torch.float32)
         done += rows
-        c += 1
     return out
 
 

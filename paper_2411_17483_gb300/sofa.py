@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsofa.so")
 
 SOFA_OK = 0
-ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "NOT_TRAINED", -6: "TIE_OVERFLOW"}
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "NOT_TRAINED", -6: "TIE_OVERFLOW", -7: "INTERNAL"}
 MAX_K = 64
 MAX_WORD = 32
 

@@ -73,6 +73,28 @@ def test_window_knn_equals_full_sort(k):
     assert np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("k,chunk,keep", [(1, 97, 4), (5, 250, 8), (50, 700, 64), (3, 5000, 1)])
+def test_chunked_knn_equals_full_sort(k, chunk, keep):
+    rng = np.random.default_rng(10 + k)
+    z, _, _ = orc.znorm(rw(2000, 32, 6))
+    q = z[:8].copy()
+    q += 1e-3 * rng.standard_normal(q.shape).astype(np.float32)
+    z[1700] = z[1]                          # exact duplicate across chunks
+    z[1701] = z[2] * np.float32(1 + 1e-8)   # near tie across chunks
+    order = list(range(0, 2000, chunk))[::-1]   # chunks in reverse order
+    a = orc.knn_full(z, q, k)
+    b = orc.knn_chunked(((r, z[r:r + chunk]) for r in order), q, k, keep=keep)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1])
+
+
+def test_chunked_knn_refuses_a_truncated_window():
+    z, _, _ = orc.znorm(rw(400, 16, 7))
+    z[:] = z[0]                              # every row ties with every other
+    with pytest.raises(RuntimeError):
+        orc.knn_chunked(((r, z[r:r + 100]) for r in range(0, 400, 100)), z[:1], 1, keep=4)
+
+
 @pytest.mark.parametrize("n,alpha,k", [(8, 2, 1), (16, 4, 5), (64, 256, 50), (64, 4, 1), (16, 256, 5)])
 def test_gemini_equals_bruteforce(n, alpha, k):
     """GEMINI (Sec. II-A) with the SFA bound returns exactly the brute-force
