@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--classes", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gen", default="rw", choices=["rw", "mixed", "sin"],
+                    help="rw: random walks (default); mixed: half walks + noisy walks with half perturbed-member "
+                         "queries; sin: 8-sinusoid mixtures (high-frequency stress, bounds prune little)")
     return ap.parse_args()
 
 
@@ -73,7 +76,33 @@ def kernel_source_sha(name="k_scan"):
 
 
 def workload_name(a):
-    return f"random walks {a.N}x{a.n} fp32, {a.Q} fresh random-walk queries, exact {a.k}-NN, l={a.l}, alphabet {a.alphabet}"
+    data = {"rw": "random walks", "mixed": "random walks + noisy random walks",
+            "sin": "8-sinusoid mixtures + N(0,0.3^2) noise"}[a.gen]
+    queries = {"rw": "fresh random-walk queries", "mixed": "queries (half perturbed members, half fresh walks)",
+               "sin": "queries of the same generator"}[a.gen]
+    return f"{data} {a.N}x{a.n} fp32, {a.Q} {queries}, exact {a.k}-NN, l={a.l}, alphabet {a.alphabet}"
+
+
+def make_rows(a, rows, seed, device, out=None, row0=0):
+    """Rows row0.. of the workload's data (seed 0) or query (seed 1 + rank) stream."""
+    from paper_2411_17483_gb300 import datagen
+    if a.gen == "sin":
+        x = datagen.sinusoid_mix(rows, a.n, seed=seed, device=device, row0=row0)
+    elif a.gen == "mixed" and seed == 0:
+        x = datagen.mixed_walks(rows, a.n, seed=seed, device=device, total=a.N, row0=row0)
+    else:
+        return datagen.random_walks(rows, a.n, seed=seed, device=device, out=out, row0=row0)
+    if out is not None:
+        out.copy_(x)
+        return out
+    return x
+
+
+def make_queries(a, x, seed, device):
+    from paper_2411_17483_gb300 import datagen
+    if a.gen == "mixed":
+        return datagen.half_perturbed_queries(x, a.Q, seed=seed)
+    return make_rows(a, a.Q, seed, device)
 
 
 # ---------------------------------------------------------------- clocks
@@ -183,8 +212,8 @@ def run_reference(a, ws, rank):
     from paper_2411_17483_gb300 import datagen
     dev = "cuda:0" if torch.cuda.is_available() else "cpu"
     rows = min(a.N, 2_000_000)
-    xs = datagen.random_walks(rows, a.n, seed=0, device=dev).cpu().numpy()
-    q = datagen.random_walks(a.Q, a.n, seed=1, device=dev).cpu().numpy()
+    xs = make_rows(a, rows, 0, dev).cpu().numpy()
+    q = make_queries(a, make_rows(a, rows, 0, dev), 1, dev).cpu().numpy()
     from oracle import sofa_oracle as orc
     zq, _, _ = orc.znorm(q)
     xs, _, _ = orc.znorm(xs)
@@ -219,7 +248,12 @@ def run_sofa(a, ws, rank, local):
 
     t0 = time.perf_counter()
     x = torch.empty((a.N, a.n), dtype=torch.float32, device=dev)
-    datagen.random_walks(a.N, a.n, seed=0, device=dev, out=x)
+    if a.gen == "sin":   # chunk by chunk: the generator works in FP64
+        for r0 in range(0, a.N, 1 << 22):
+            r = min(1 << 22, a.N - r0)
+            make_rows(a, r, 0, dev, out=x[r0:r0 + r], row0=r0)
+    else:
+        make_rows(a, a.N, 0, dev, out=x)
     cpu_rows = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cpu_rows = x[: min(a.N, 2_000_000)].cpu().numpy()
@@ -228,12 +262,11 @@ def run_sofa(a, ws, rank, local):
     ix = sofa.Index(x, a.l, a.alphabet, sample_ratio=0.1, precision=1)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
+    # each rank answers its own batch: rank r uses query stream seed 1 + r
+    q = make_queries(a, x, 1 + rank, dev)
     del x
     torch.cuda.empty_cache()
     info = ix.info()
-
-    # each rank answers its own batch: rank r uses query stream seed 1 + r
-    q = datagen.random_walks(a.Q, a.n, seed=1 + rank, device=dev)
     idx = torch.empty((a.Q, a.k), dtype=torch.int64, device=dev)
     dist = torch.empty((a.Q, a.k), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
@@ -255,9 +288,9 @@ def run_sofa(a, ws, rank, local):
     results = {}
     for mode_name, mode in modes.items():
         # plain: FP32 bounds and refinement, key-window seed; chosen: learned
-        # seed and the int8 refinement filter (both exact)
+        # seed and the two refinement filters: value codes, then int8 rows (all exact)
         ix.set_seed_mode(mode)
-        ix.set_tuning(refine_filter=1 if mode_name != "plain" else 0)
+        ix.set_tuning(refine_filter=2 if mode_name != "plain" else 0)
         for _ in range(a.warmup):
             ix.query(q, a.k, idx, dist)
         torch.cuda.synchronize()
@@ -315,7 +348,24 @@ def run_sofa(a, ws, rank, local):
         ach = alg_bytes / per_launch_s / 1e9
         hbm.update(achieved=ach, frac=ach / hbm_peak)
     roof = hbm
-    if phase == "scan":
+    dense_pairs = stats.get("dense_pairs", 0)
+    if phase == "scan" and dense_pairs > 0:
+        # dense batches: the bound phase is the tcgen05 TF32 contraction;
+        # tensor roofline against the measured bf16 burst peak times the
+        # nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16 = float(json.load(f)["bf16_tflops"])
+            pk_kind = "measured bf16 x 1.1/2.25 (nominal tf32/bf16)"
+        except (OSError, KeyError, ValueError):
+            bf16, pk_kind = 1900.0, "fallback bf16 x 1.1/2.25 (nominal tf32/bf16)"
+        peak_t = bf16 * 1.1 / 2.25
+        npad = (a.n + 31) // 32 * 32
+        flops = 2.0 * dense_pairs * npad / launches
+        ach_t = flops / per_launch_s / 1e12
+        roof = {"kernel": "dense", "bound": "tensor", "achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s",
+                "frac": ach_t / peak_t, "traffic": None, "peak_kind": pk_kind, "hbm_view": hbm}
+    elif phase == "scan":
         # ALU roofline: one (query, series) bound needs, per value, 3 FP32 lane
         # operations (q - c, the scaled clamp, the square-accumulate); the FP32
         # pipe does 128 lane operations per SM per clock, packed or not:
@@ -334,10 +384,14 @@ def run_sofa(a, ws, rank, local):
                 "unit": "G (query, series) bounds/s", "frac": ach_b / peak_b, "traffic": traffic,
                 "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz / (3 x {LW})",
                 "hbm_view": hbm}
-    # whole-step algorithmic bytes (SFA words scanned per query + int8 rows
-    # filtered + refined raw series)
-    step_bytes = ((stats["tile_pairs"] * 256 * LW) + stats["refined"] * a.n * 4
-                  + stats.get("filtered", 0) * a.n) / a.steps
+    # whole-step algorithmic bytes: SFA words of every bounded series; for
+    # each candidate reaching a filter, its value codes (2 LW bytes + scale
+    # and margin) and / or its int8 row; the fp32 rows refined
+    vf, f8, rf = stats.get("value_filtered", 0), stats.get("filtered", 0), stats["refined"]
+    value_checked = vf + f8 + rf if vf else 0
+    int8_rows = f8 + rf if (vf or f8) else 0
+    step_bytes = ((stats["tile_pairs"] * 256 * LW) + value_checked * (2 * LW + 8) + int8_rows * a.n
+                  + rf * a.n * 4) / a.steps
     step_roof = step_bytes / (r["ms"] / 1e3) / 1e9
 
     # end to end through the public API with host buffers
@@ -366,7 +420,7 @@ def run_sofa(a, ws, rank, local):
         ld = torch.empty((64, a.k), dtype=torch.float32, device=dev)
         lat = {}
         for use_graph in (0, 1):
-            ix.set_tuning(refine_filter=1, use_graph=use_graph)
+            ix.set_tuning(refine_filter=2, use_graph=use_graph)
             for _ in range(3):
                 ix.query(qs, a.k, li, ld)
             torch.cuda.synchronize()
@@ -375,8 +429,33 @@ def run_sofa(a, ws, rank, local):
                 ix.query(qs, a.k, li, ld)
             torch.cuda.synchronize()
             lat["graph_ms" if use_graph else "eager_ms"] = (time.perf_counter() - w0) / 20 * 1e3
-        ix.set_tuning(refine_filter=1)
+        ix.set_tuning(refine_filter=2)
         latency = {"queries": 64, **lat, "graph_replays": ix.stats()["graph_replays"]}
+
+    # the approximate search alone (same seed mode): throughput and recall@k
+    # against this run's exact answers
+    approx = None
+    if not a.no_e2e:
+        ix.query(q, a.k, idx, dist)                     # exact answers of the chosen mode
+        exact = idx.clone()
+        ix.set_tuning(refine_filter=2, approximate=1)
+        ai = torch.empty_like(idx)
+        ad = torch.empty_like(dist)
+        for _ in range(2):
+            ix.query(q, a.k, ai, ad)
+        st = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(3):
+            ix.query(q, a.k, ai, ad)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        A, E = ai.cpu().numpy(), exact.cpu().numpy()
+        hits = sum(len(set(A[i]) & set(E[i])) for i in range(a.Q))
+        approx = {"queries_per_s": a.Q / (ms / 1e3), "ms_per_step": ms, "recall_at_k": hits / (a.Q * a.k)}
+        ix.set_tuning(refine_filter=2)
 
     cpu = None
     if cpu_rows is not None:
@@ -394,7 +473,7 @@ def run_sofa(a, ws, rank, local):
             "warmup": a.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "N": a.N, "n": a.n, "Q_per_gpu": a.Q, "k": a.k, "l": a.l,
-                       "alphabet": a.alphabet, "seed_mode": chosen, "precision": "chosen: fp32 bounds, int8 refinement filter (derived margin), fp32 refine, fp64 final re-score",
+                       "alphabet": a.alphabet, "seed_mode": chosen, "precision": "chosen: fp32 bounds (packed f32x2), int8 value-code and int8 row filters (derived margins), fp32 refine, fp64 final re-score",
                        "l2": "flushed between timed steps (256 MB write)", "build_s": round(t2 - t1, 3),
                        "gen_s": round(t1 - t0, 3), "parallelism": f"replicas x{ws}"},
             "roofline": roof,
@@ -413,6 +492,7 @@ def run_sofa(a, ws, rank, local):
                       for m in results},
             "proposal_training": train,
             "latency_64_queries": latency,
+            "approximate_search": approx,
             "index": {"n_leaves": info["n_leaves"], "n_tiles": info["n_tiles"], "device_GB": info["device_bytes"] / 1e9},
         }
         print(json.dumps(out), flush=True)

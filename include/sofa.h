@@ -152,12 +152,29 @@ typedef struct {
                            error: the queries concerned are scanned again.      */
   int32_t refine_filter; /* 1: before its FP32 distance, a candidate is bounded
                             from its int8 copy (triangle inequality with the
-                            stored quantisation error); needs precision 1      */
+                            stored quantisation error); 2: first from int8
+                            codes of its selected Fourier values (Eq. (1) on
+                            those values, triangle inequality with the stored
+                            margin), then as 1.  Both need precision 1         */
   int32_t use_graph;    /* 1: each batch shape is run once eagerly and recorded
                            as a CUDA graph, later batches of that shape replay
                            it (inputs and outputs staged through fixed buffers;
                            a batch whose candidate pool ran full is recomputed
                            eagerly).  Ignored while profiling is on.            */
+  int64_t cand_budget;  /* candidate-region entries one overflow pass may use
+                           (queries beyond it wait for a later pass); 0 ->
+                           2^30                                                 */
+  int32_t dense;        /* 0: a batch whose leaf bounds pass more than half of
+                           the (query, leaf block) pairs is bounded by the
+                           dense tensor-core contraction instead of the series
+                           scan (needs n % 4 == 0 and k <= 16); 1: never;
+                           2: always when supported                            */
+  int32_t approximate;  /* 1: answer from the seed alone -- the approximate
+                           search (key window, and the proposal network's
+                           blocks in learned mode) without the pruning scan;
+                           answers are real distances re-scored in FP64 and
+                           ordered by the tie rule, but not necessarily the
+                           exact k-NN.  0: exact (default)                     */
 } sofa_tuning;
 int sofa_set_tuning(sofa_handle h, const sofa_tuning* t);
 
@@ -190,6 +207,11 @@ typedef struct {
   int64_t graphs_recorded;  /* CUDA graphs recorded                              */
   double seed_dist_sum;     /* sum over queries of the seed's k-th distance      */
   double final_dist_sum;    /* sum over queries of the answer's k-th distance    */
+  int64_t value_filtered;   /* candidates dropped by the value-code bound
+                               (refine_filter 2)                                */
+  int64_t dense_pairs;      /* (query slot, series) pairs of the dense
+                               contraction (query slots x series per launch)   */
+  int64_t dense_passes;     /* batch passes bounded by the dense contraction    */
 } sofa_stats_t;
 int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset);
 
@@ -254,6 +276,28 @@ int sofa_lower_bounds(sofa_handle h, const float* queries, int64_t Q, float* out
  * device work overlaps (different streams, or host threads) race and must be
  * serialised by the caller.  Nothing in it needs clearing between calls. */
 int sofa_lower_bounds_noalloc(sofa_handle h, const float* queries, int64_t Q, float* out, sofa_stream stream);
+
+/* Index persistence (the paper builds its index once per dataset, Sec. V
+ * "Index creation"; this saves that work across processes).  sofa_save
+ * writes every array of the index -- summary, bins, bound tables, key-sorted
+ * words and series, permutation, envelopes, the optional precision copies
+ * and a trained proposal network -- to `path` (overwritten; removed again on
+ * failure).  sofa_load recreates a handle on the current device from such a
+ * file (NULL on error, see sofa_last_error); run-time tuning starts at its
+ * defaults.  The file is specific to this library version and byte order. */
+int sofa_save(sofa_handle h, const char* path);
+sofa_handle sofa_load(const char* path, sofa_stream stream);
+
+/* Approximate squared distances of the dense tensor-core contraction (a test
+ * and inspection aid; the paper has no counterpart).  For every query q (raw,
+ * z-normalised here) and every series at sorted position p (see
+ * sofa_export_perm): out[q * N + p] = ||q||^2 + ||x_p||^2 - 2 q.x_p from TF32
+ * operands with FP32 accumulation on the tensor cores.  *margin (may be NULL)
+ * receives the bound M >= |out - d^2| that the query path's dense form relies
+ * on.  queries (Q x n) and out (Q x N) are device memory; 1 <= Q <= 8192,
+ * Q * N <= 2^31, n % 4 == 0.  Returns 0 or a negative SOFA_ERR_* code. */
+int sofa_dense_sqdist(sofa_handle h, const float* queries, int64_t Q, float* out, float* margin,
+                      sofa_stream stream);
 
 /* Canonical z-normalisation of R rows (Sec. II Def. z-ED) as the index uses
  * it: device pointers, R x n fp32 in and out. */

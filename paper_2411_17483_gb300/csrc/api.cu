@@ -98,16 +98,16 @@ static int num_candidates_host(int n, int pool) {
   return 2 * K - ((n % 2 == 0 && 2 * K == n) ? 1 : 0);
 }
 
-static void free_index(Index* ix) {
+void destroy_index(Index* ix) {
   if (!ix) return;
   void* ptrs[] = {ix->sel, ix->sel_k, ix->sel_part, ix->var, ix->basis, ix->beta, ix->edge, ix->ch, ix->ch16,
-                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
+                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->VC, ix->vsr, ix->vw, ix->xn, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  DevBuf* bufs[] = {&ix->qs.zq, &ix->qs.qv, &ix->qs.llb, &ix->qs.thr, &ix->qs.list_d, &ix->qs.list_p,
+  DevBuf* bufs[] = {&ix->qs.zq, &ix->qs.qv, &ix->qs.qn, &ix->qs.llb, &ix->qs.thr, &ix->qs.list_d, &ix->qs.list_p,
                     &ix->qs.list_n, &ix->qs.leaf_cnt, &ix->qs.leaf_off, &ix->qs.leaf_q, &ix->qs.leaf_cursor,
                     &ix->qs.unit_off, &ix->qs.units, &ix->qs.cand_p, &ix->qs.cand_lb, &ix->qs.cand_n,
-                    &ix->qs.qflag, &ix->qs.qslot, &ix->qs.chunk_d, &ix->qs.chunk_p, &ix->qs.chunk_n, &ix->qs.pool_q, &ix->qs.pool_p, &ix->qs.pool_lb,
+                    &ix->qs.qflag, &ix->qs.qslot, &ix->qs.qsel, &ix->qs.chunk_d, &ix->qs.chunk_p, &ix->qs.chunk_n, &ix->qs.pool_q, &ix->qs.pool_p, &ix->qs.pool_lb,
                     &ix->qs.pool_sp, &ix->qs.pool_slb, &ix->qs.qpool_cnt, &ix->qs.qpool_off, &ix->qs.qcursor,
                     &ix->qs.choff, &ix->qs.chunk_q, &ix->qs.qof, &ix->qs.counters, &ix->qs.stage_in, &ix->qs.stage_out, &ix->qs.graph_in, &ix->qs.graph_out, &ix->qs.pinned_dummy};
   for (DevBuf* b : bufs) b->release();
@@ -178,13 +178,13 @@ sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, in
     cudaError_t e = cudaMalloc(&owned, (size_t)N * n * sizeof(float));
     if (e != cudaSuccess) {
       cudaGetLastError();
-      free_index(ix);
+      destroy_index(ix);
       return bad("device allocation for the input copy failed");
     }
     e = cudaMemcpyAsync(owned, data, (size_t)N * n * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
       cudaFree(owned);
-      free_index(ix);
+      destroy_index(ix);
       return bad(std::string("input copy failed: ") + cudaGetErrorString(e));
     }
     x = owned;
@@ -197,7 +197,7 @@ sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, in
   if (rc) {
     std::string m = g_err;
     cudaStreamSynchronize(st);
-    free_index(ix);
+    destroy_index(ix);
     set_error(m);
     return nullptr;
   }
@@ -264,15 +264,19 @@ int sofa_stats(sofa_handle h, sofa_stats_t* out, int32_t reset) {
   out->graphs_recorded = h->stats[7];
   out->seed_dist_sum = (double)c[6] * 1e-6;
   out->final_dist_sum = (double)c[7] * 1e-6;
+  out->value_filtered = (int64_t)c[13];
+  out->dense_pairs = (int64_t)c[11];
+  out->dense_passes = h->stats[1];
   out->n_leaves = h->L;
   out->n_tiles = h->T;
   if (reset) {
     if (h->qs.counters.p) {
       SOFA_CUDA(cudaMemset(h->qs.counters.p, 0, 4 * sizeof(unsigned long long)));
       SOFA_CUDA(cudaMemset(h->qs.counters.as<unsigned long long>() + 6, 0, 2 * sizeof(unsigned long long)));
-      SOFA_CUDA(cudaMemset(h->qs.counters.as<unsigned long long>() + 12, 0, sizeof(unsigned long long)));
+      SOFA_CUDA(cudaMemset(h->qs.counters.as<unsigned long long>() + 11, 0, 3 * sizeof(unsigned long long)));
     }
     h->stats[0] = 0;
+    h->stats[1] = 0;
     h->stats[5] = 0;
     h->stats[6] = 0;
   }
@@ -288,8 +292,12 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
     return fail(SOFA_ERR_INVALID_ARG, "seed_window must be 0 or a power of two <= 4096");
   if (t->bound_precision < 0 || t->bound_precision > 1) return fail(SOFA_ERR_INVALID_ARG, "bound_precision must be 0 or 1");
   if (t->pool_cap < 0 || t->pool_cap > ((int64_t)1 << 30)) return fail(SOFA_ERR_INVALID_ARG, "pool_cap must lie in [0, 2^30]");
-  if (t->refine_filter < 0 || t->refine_filter > 1) return fail(SOFA_ERR_INVALID_ARG, "refine_filter must be 0 or 1");
-  if (t->refine_filter == 1 && !h->Z8) return fail(SOFA_ERR_INVALID_ARG, "refine_filter needs an index built with precision 1");
+  if (t->refine_filter < 0 || t->refine_filter > 2) return fail(SOFA_ERR_INVALID_ARG, "refine_filter must be 0, 1 or 2");
+  if (t->refine_filter >= 1 && (!h->Z8 || !h->VC))
+    return fail(SOFA_ERR_INVALID_ARG, "refine_filter needs an index built with precision 1");
+  if (t->cand_budget < 0) return fail(SOFA_ERR_INVALID_ARG, "cand_budget must be >= 0");
+  if (t->dense < 0 || t->dense > 2) return fail(SOFA_ERR_INVALID_ARG, "dense must be 0, 1 or 2");
+  if (t->approximate < 0 || t->approximate > 1) return fail(SOFA_ERR_INVALID_ARG, "approximate must be 0 or 1");
   if (t->use_graph < 0 || t->use_graph > 1) return fail(SOFA_ERR_INVALID_ARG, "use_graph must be 0 or 1");
   h->group = t->group ? t->group : 64;
   h->cand_cap = t->cand_cap ? t->cand_cap : 65536;
@@ -299,6 +307,9 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   h->pool_cap = t->pool_cap;
   h->refine_filter = t->refine_filter;
   h->use_graph = t->use_graph;
+  h->cand_budget = t->cand_budget ? t->cand_budget : ((int64_t)1 << 30);
+  h->dense_mode = t->dense;
+  h->approximate = t->approximate;
   return 0;
 }
 
@@ -395,7 +406,7 @@ int sofa_profile(sofa_handle h, sofa_profile_t* out, int32_t reset) {
 void sofa_free(sofa_handle h) {
   if (!h) return;
   cudaDeviceSynchronize();
-  free_index(h);
+  destroy_index(h);
 }
 
 }  // extern "C"

@@ -467,6 +467,80 @@ __global__ void k_quant8(const float* __restrict__ Z, int64_t N, int n, int8_t* 
   }
 }
 
+// Eq. (1) weight of each projection column: 2 for a value of coefficient
+// 0 < k < n/2 (it stands for itself and its conjugate), 1 for the Nyquist
+// value, 0 for an unused column.  Columns [0, LW) hold the word values
+// (0..l-1), columns [LW, NB) the remaining selected values (l..nsel-1).
+__global__ void k_vweights(int n, int NB, int LW, int l, int nsel, const int32_t* __restrict__ sel_k,
+                           float* __restrict__ vw) {
+  const int col = threadIdx.x;
+  if (col >= NB) return;
+  const int j = col < LW ? (col < l ? col : -1) : (l + col - LW < nsel ? l + col - LW : -1);
+  vw[col] = j < 0 ? 0.f : (2 * sel_k[j] == n ? 1.f : 2.f);
+}
+
+// Value codes for the refinement's first filter.  Each canonical series'
+// NB selected Fourier values v~ (the FP32 projection of the word kernel, so
+// |v~ - v| <= delta_d per value) become int8 codes c with one scale s per
+// series; y = s c is an exact real vector.  The stored margin is
+//   r = ||v~ - y||_w (FP64, rounded up) + sqrt(W) (delta_d + delta_q),
+// W = sum of the weights, so that for the exact values v of the series and q
+// of a query (computed as q~):  ||q - v||_w >= ||q~ - y||_w - r  by the
+// triangle inequality in the weighted norm, and Eq. (1) restricted to the
+// selected values gives ||q - v||_w <= ED.  Thread per series, rows staged in
+// shared memory.
+template <int NBT>
+__global__ void k_quantv(const float* __restrict__ Z, int64_t N, int n, const float* __restrict__ basis,
+                         const float* __restrict__ vw, float dmargin, int8_t* __restrict__ vc,
+                         float2* __restrict__ vsr) {
+  extern __shared__ float sm[];
+  const int64_t first = (int64_t)blockIdx.x * ROWS;
+  stage_rows(Z, first, N, 1, n, sm);
+  const int r = threadIdx.x;
+  const int64_t row = first + r;
+  if (r >= ROWS || row >= N) return;
+  const float* my = sm + r * (n + 1);
+  float acc[NBT];
+#pragma unroll
+  for (int j = 0; j < NBT; ++j) acc[j] = 0.f;
+  for (int t = 0; t < n; ++t) {
+    const float zt = my[t];
+    const float4* b = reinterpret_cast<const float4*>(basis + (int64_t)t * NBT);
+#pragma unroll
+    for (int j4 = 0; j4 < NBT / 4; ++j4) {
+      const float4 bb = __ldg(b + j4);
+      acc[4 * j4 + 0] = fmaf(zt, bb.x, acc[4 * j4 + 0]);
+      acc[4 * j4 + 1] = fmaf(zt, bb.y, acc[4 * j4 + 1]);
+      acc[4 * j4 + 2] = fmaf(zt, bb.z, acc[4 * j4 + 2]);
+      acc[4 * j4 + 3] = fmaf(zt, bb.w, acc[4 * j4 + 3]);
+    }
+  }
+  float mx = 0.f;
+#pragma unroll
+  for (int j = 0; j < NBT; ++j) mx = fmaxf(mx, fabsf(acc[j]));
+  const float sc = mx > 0.f ? mx / 127.0f : 1.0f;
+  double e2 = 0.0;
+  uint32_t packed[NBT / 4];
+#pragma unroll
+  for (int j4 = 0; j4 < NBT / 4; ++j4) {
+    uint32_t w = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = 4 * j4 + b;
+      const float c = fminf(fmaxf(rintf(acc[j] / sc), -127.f), 127.f);
+      const double d = (double)acc[j] - (double)sc * (double)c;
+      e2 += (double)__ldg(vw + j) * d * d;
+      w |= ((uint32_t)(int)c & 0xFFu) << (8 * b);
+    }
+    packed[j4] = w;
+  }
+  uint4* o = reinterpret_cast<uint4*>(vc + row * NBT);
+#pragma unroll
+  for (int q = 0; q < NBT / 16; ++q)
+    o[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+  vsr[row] = make_float2(sc, __double2float_ru(sqrt(e2) * (1.0 + 1e-6) + (double)dmargin + 1e-30));
+}
+
 // Symbol envelope (per word value min and max symbol) of each tile of 256
 // consecutive key-sorted series, using byte-wise SIMD min / max.
 template <int LW>
@@ -756,7 +830,31 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
     TRY(dalloc(&ix->e8, N, acct));
     k_quant8<<<(unsigned)ceil_div(N * 32, 256), 256, 0, st>>>(ix->Z, N, n, ix->Z8, ix->s8, ix->e8);
     SOFA_CUDA(cudaGetLastError());
+    // value codes (the refinement's first filter), in key order
+    TRY(dalloc(&ix->VC, N * NB, acct));
+    TRY(dalloc(&ix->vsr, N, acct));
+    TRY(dalloc(&ix->vw, NB, acct));
+    k_vweights<<<1, NB_MAX, 0, st>>>(n, NB, LW, l, ix->nsel, ix->sel_k, ix->vw);
+    SOFA_CUDA(cudaGetLastError());
+    // sqrt(W) (delta_d + delta_q) with W <= 2 nsel, rounded up
+    const float dmargin = std::nextafter(
+        (float)(std::sqrt(2.0 * ix->nsel) * (ix->delta_d + ix->delta_q) * 1.0001), INFINITY);
+    const size_t vsmem = (size_t)ROWS * (n + 1) * sizeof(float);
+    if (NB == 32) {
+      SOFA_CUDA(cudaFuncSetAttribute(k_quantv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
+      k_quantv<32><<<(unsigned)ceil_div(N, ROWS), ROWS, vsmem, st>>>(ix->Z, N, n, ix->basis, ix->vw, dmargin,
+                                                                     ix->VC, ix->vsr);
+    } else {
+      SOFA_CUDA(cudaFuncSetAttribute(k_quantv<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
+      k_quantv<64><<<(unsigned)ceil_div(N, ROWS), ROWS, vsmem, st>>>(ix->Z, N, n, ix->basis, ix->vw, dmargin,
+                                                                     ix->VC, ix->vsr);
+    }
+    SOFA_CUDA(cudaGetLastError());
   }
+
+  // ---- squared norms of the canonical series (dense path)
+  TRY(dalloc(&ix->xn, N, acct));
+  TRY(launch_row_norms(ix, st));
 
   // ---- envelopes
   ix->T = ceil_div(N, TILE);

@@ -1,0 +1,527 @@
+// Dense form of the query for batches whose lower bounds prune (almost)
+// nothing.  GEMINI's refinement computes exact distances of the survivors of
+// the bound (Sec. II-A); when the bound passes every series -- high-frequency
+// data whose selected Fourier values carry little of the energy -- the
+// survivors are the whole collection, and the distances of a batch are one
+// dense contraction: d^2(q, x) = ||q||^2 + ||x||^2 - 2 q.x.
+//
+// The contraction runs on the tensor cores (tcgen05, kind::tf32) straight
+// from the fp32 canonical series: operands are staged by TMA into 128-byte
+// swizzled shared-memory tiles, the accumulator lives in tensor memory.  A CTA
+// holds 128 queries (the MMA's M, one TMEM lane each) and walks a chunk of
+// tiles of 256 series (N, the TMEM columns), K in blocks of 32 values.  Its
+// epilogue turns each accumulator column into an approximate squared distance
+// and emits every series whose lower bound (d~^2 - M) / 2 may still reach the
+// query's answer into the same candidate store the series scan fills, so the
+// exact refinement, merge and final re-score are unchanged.  M bounds
+// |d~^2 - d^2| (TF32 operands, FP32 accumulation; derived on the host).  Each
+// thread keeps the k smallest d~^2 it has seen, which tightens the emission
+// threshold as the chunk proceeds and is published to the query's threshold.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "sofa_internal.cuh"
+
+namespace sofa {
+
+constexpr int DM = 128;                  // queries per CTA: MMA M, TMEM lanes
+constexpr int DN = 256;                  // series per tile: MMA N, TMEM columns
+constexpr int DK = 32;                   // fp32 values per k-block: one 128-byte swizzled row
+constexpr int DSTAGES = 4;               // TMA pipeline depth
+constexpr int A_BYTES = DM * DK * 4;     // 16 KB
+constexpr int B_BYTES = DN * DK * 4;     // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int DENSE_SMEM = DSTAGES * STAGE_BYTES + 1024;  // + alignment slack
+constexpr int DKMAX = 16;                // largest k of the dense path
+constexpr unsigned long long WAIT_NS = 2000000000ull;     // bounded waits: 2 s
+
+// Instruction descriptor of tcgen05.mma kind::tf32: D fp32 (bits 4-5 = 1),
+// A and B tf32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t DENSE_IDESC =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(DN >> 3) << 17) | ((uint32_t)(DM >> 4) << 24);
+
+struct DenseParams {
+  int64_t N;           // series
+  int Q;               // queries of the batch
+  int n;               // values per series
+  int k;               // neighbours
+  int cap;             // candidate region per query slot
+  int64_t pool_cap;    // shared pool entries
+  int64_t tiles_per_cta;
+  float margin;        // M >= |d~^2 - d^2|
+  float f_half;        // f_prune / 2: threshold of a real k-th squared distance
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Wait for the completion of the phase with the given parity; false when the
+// wait ran out (2 s).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && global_ns() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzled layout TMA writes: rows of 128 bytes, 8-row atoms of 1024 bytes
+// (stride byte offset), descriptor version 1, layout type 2 (128B swizzle).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading byte offset: unused for swizzled K-major tiles
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(DENSE_IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {  // whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // whole warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// ||x||^2 of every canonical series: left-to-right FP64 sum, rounded to fp32.
+__global__ void k_row_norms(const float* __restrict__ Z, int64_t N, int n, float* __restrict__ out) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  double s = 0.0;
+  for (int t = lane; t < n; t += 32) {
+    const double z = Z[row * n + t];
+    s += z * z;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) out[row] = (float)s;
+}
+
+// The k smallest approximate squared distances seen by a thread (ascending);
+// KD = 1 for k = 1, else DKMAX.
+template <int KD>
+__device__ __forceinline__ void topk_insert(float* top, float x) {
+#pragma unroll
+  for (int i = 0; i < KD; ++i) {
+    const float lo = fminf(top[i], x);
+    x = fmaxf(top[i], x);
+    top[i] = lo;
+  }
+}
+
+template <int KD>
+__device__ __forceinline__ float topk_kth(const float* top, int k) {
+  float v = top[0];
+#pragma unroll
+  for (int i = 1; i < KD; ++i)
+    if (i == k - 1) v = top[i];
+  return v;
+}
+
+template <int KD>
+__global__ void __launch_bounds__(DM, 1) k_dense(const __grid_constant__ CUtensorMap tmQ,
+                                                 const __grid_constant__ CUtensorMap tmX, DenseParams D,
+                                                 const float* __restrict__ qn, const float* __restrict__ xn,
+                                                 const int* __restrict__ qsel, const int* __restrict__ qslot,
+                                                 float* __restrict__ thr, uint32_t* __restrict__ cand_p,
+                                                 float* __restrict__ cand_lb, int* __restrict__ cand_n,
+                                                 unsigned long long* __restrict__ pool_n, int* __restrict__ pool_q,
+                                                 uint32_t* __restrict__ pool_p, float* __restrict__ pool_lb,
+                                                 int* __restrict__ qpool_cnt, float* __restrict__ dump,
+                                                 unsigned long long* __restrict__ counters, int* __restrict__ status) {
+  extern __shared__ uint8_t dsm_raw[];
+  __shared__ __align__(8) uint64_t full[DSTAGES], empty[DSTAGES], accf;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
+  __shared__ float sxn[DN];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t n_tiles = (D.N + DN - 1) / DN;
+  const int64_t t_begin = (int64_t)blockIdx.y * D.tiles_per_cta;
+  const int64_t t_end = t_begin + D.tiles_per_cta < n_tiles ? t_begin + D.tiles_per_cta : n_tiles;
+  if (t_begin >= t_end) return;  // the whole CTA, before any barrier or allocation
+  // stage buffers on a 1024-byte boundary (the 128-byte swizzle atom)
+  const uint32_t raw = smem_u32(dsm_raw);
+  uint8_t* stages = dsm_raw + (((raw + 1023u) & ~1023u) - raw);
+  const int q0 = blockIdx.x * DM;
+  const int kblocks = (D.n + DK - 1) / DK;
+  const int64_t total = (t_end - t_begin) * kblocks;
+
+  if (warp == 0) tmem_alloc(&s_tmem, DN);
+  if (tid == 0) {
+    for (int s = 0; s < DSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accf, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  // this thread's query (its TMEM lane)
+  const int q = q0 + tid;
+  const bool qa = q < D.Q && (!qsel || qsel[q]);
+  const int nq_active = __syncthreads_count(qa);  // for the pair counter
+  const int qs = qa ? (qslot ? qslot[q] : q) : 0;
+  const float qnr = qa ? qn[q] : 0.f;
+  volatile float* vthr = thr;
+  float T = qa ? vthr[q] : -1.f;  // emission threshold, half units
+  float top[KD];
+#pragma unroll
+  for (int i = 0; i < KD; ++i) top[i] = INFINITY;
+  unsigned long long emitted = 0;
+
+  // thread 0 drives TMA and the MMAs: loads run DSTAGES - 1 k-blocks ahead
+  int64_t issued = 0;
+  auto issue = [&](int64_t idx) -> bool {
+    const int s = (int)(idx % DSTAGES);
+    if (idx >= DSTAGES && !mbar_wait(&empty[s], (uint32_t)((idx / DSTAGES - 1) & 1))) return false;
+    const int64_t tile = t_begin + idx / kblocks;
+    const int kb = (int)(idx % kblocks);
+    uint8_t* a = stages + s * STAGE_BYTES;
+    mbar_expect_tx(&full[s], STAGE_BYTES);
+    tma_load_2d(a, &tmQ, kb * DK, q0, &full[s]);
+    tma_load_2d(a + A_BYTES, &tmX, kb * DK, (int)(tile * DN), &full[s]);
+    return true;
+  };
+  if (tid == 0)
+    while (issued < total && issued < DSTAGES - 1) {
+      if (!issue(issued)) {
+        s_fail = 1;
+        break;
+      }
+      ++issued;
+    }
+
+  int64_t ti = 0;
+  for (int64_t t = t_begin; t < t_end; ++t, ++ti) {
+    if (tid == 0 && !s_fail) {
+      bool ok = true;
+      for (int kb = 0; kb < kblocks && ok; ++kb) {
+        const int64_t idx = ti * kblocks + kb;
+        const int s = (int)(idx % DSTAGES);
+        if (!mbar_wait(&full[s], (uint32_t)((idx / DSTAGES) & 1))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a = smem_u32(stages + s * STAGE_BYTES);
+        const uint64_t ad = sw128_desc(a), bd = sw128_desc(a + A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < DK / 8; ++kk)  // K = 8 tf32 values (32 bytes) per MMA
+          mma_tf32(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0 ? 1u : 0u);
+        mma_commit(&empty[s]);
+        if (issued < total) {
+          if (!issue(issued)) ok = false;
+          ++issued;
+        }
+      }
+      if (ok) mma_commit(&accf);
+      else s_fail = 1;
+    }
+    // every thread: the accumulator of this tile
+    if (!mbar_wait(&accf, (uint32_t)(ti & 1))) atomicExch(&s_fail, 1);
+    tc_fence_after();
+    const int64_t s0 = t * DN;
+    for (int j = tid; j < DN; j += DM) sxn[j] = s0 + j < D.N ? xn[s0 + j] : 0.f;
+    __syncthreads();
+    if (s_fail) break;  // the same value for every thread after the barrier
+    if (qa) T = fminf(T, vthr[q]);
+    const float T_in = T;
+#pragma unroll 1
+    for (int c0 = 0; c0 < DN; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);  // warp-collective
+      if (!qa) continue;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int64_t sidx = s0 + c0 + i;
+        if (sidx >= D.N) break;
+        const float d2 = fmaf(-2.f, v[i], qnr + sxn[c0 + i]);
+        if (dump) {
+          dump[(int64_t)q * D.N + sidx] = d2;
+          continue;
+        }
+        const float lb = __fmul_rd(__fsub_rd(d2, D.margin), 0.5f);  // lower bound, half units
+        if (lb > T) continue;
+        // a candidate: into the query's region, its excess into the pool
+        ++emitted;
+        const int slot = atomicAdd(cand_n + qs, 1);
+        if (slot < D.cap) {
+          cand_p[(int64_t)qs * D.cap + slot] = (uint32_t)sidx;
+          cand_lb[(int64_t)qs * D.cap + slot] = fmaxf(lb, 0.f);
+        } else {
+          const unsigned long long pb = atomicAdd(pool_n, 1ull);
+          if ((int64_t)pb < D.pool_cap) {
+            pool_q[pb] = qs;
+            pool_p[pb] = (uint32_t)sidx;
+            pool_lb[pb] = fmaxf(lb, 0.f);
+            atomicAdd(qpool_cnt + qs, 1);
+          }
+        }
+        if (d2 < top[KD - 1]) {
+          topk_insert<KD>(top, d2);
+          const float kth = topk_kth<KD>(top, D.k);
+          // k series with d^2 <= d~^2 + M each: a valid threshold
+          if (kth < INFINITY) T = fminf(T, __fmul_ru(__fadd_ru(kth, D.margin), D.f_half));
+        }
+      }
+    }
+    if (qa && T < T_in) atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(T));  // T >= 0
+    tc_fence_before();
+    __syncthreads();  // the accumulator and sxn are free for the next tile
+  }
+  if (s_fail && tid == 0) atomicExch(status, SOFA_ERR_TIMEOUT);
+  if (emitted) atomicAdd(counters + 2, emitted);
+  if (tid == 0) {
+    const int64_t s_hi = t_end * DN < D.N ? t_end * DN : D.N;
+    atomicAdd(counters + 11, (unsigned long long)nq_active * (unsigned long long)(s_hi - t_begin * DN));
+  }
+  // loads still in flight after a failure: wait for them (bounded) before the
+  // shared memory goes away
+  if (tid == 0 && s_fail)
+    for (int64_t idx = ti * kblocks; idx < issued; ++idx) mbar_wait(&full[idx % DSTAGES], (uint32_t)((idx / DSTAGES) & 1));
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, DN);
+}
+
+// ------------------------------------------------------------------------
+// host side
+
+#define TRYD(x)          \
+  do {                   \
+    int rc_ = (x);       \
+    if (rc_) return rc_; \
+  } while (0)
+
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+static EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+            cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-d map of a row-major fp32 matrix (rows x n), boxes of DK x box_rows,
+// 128-byte swizzle; elements outside the matrix read as zero.
+static int make_map(CUtensorMap* m, const float* base, int64_t rows, int n, int box_rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return fail(SOFA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)DK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SOFA_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return 0;
+}
+
+bool dense_supported(const Index* ix, int k) {
+  return ix->xn && ix->n % 4 == 0 && k <= DKMAX && ix->N < ((int64_t)1 << 31) - 2 * DN && encode_fn() != nullptr;
+}
+
+// |d~^2 - d^2| for canonical series (||x||^2 <= n (1 + 4u)) with TF32
+// operands (relative error < 2^-10 each, truncated or rounded) and an FP32
+// accumulation whose additions may lose up to 2 bits against IEEE:
+//   |q.x~ - q.x| <= n' (2^-9 + 2^-20 + n 2^-22 (1 + 2^-9)),  n' = n (1 + 4u),
+// twice that for -2 q.x, plus the fp32 roundings of ||x||^2 and ||q||^2 and
+// of the two fp32 operations forming d~^2 (8.2 u n'); 1 % on top.
+static float dense_margin(int n) {
+  const double u = std::ldexp(1.0, -24);
+  const double np = n * (1.0 + 4 * u);
+  const double dot = np * (std::ldexp(1.0, -9) + std::ldexp(1.0, -20) + n * std::ldexp(1.0, -22) * (1.0 + std::ldexp(1.0, -9)));
+  return std::nextafter((float)((2.0 * dot + 8.2 * u * np) * 1.01), INFINITY);
+}
+
+float dense_margin_of(int n) { return dense_margin(n); }
+
+// ||q||^2 of each canonical query (FP64 sum rounded to fp32).
+__global__ void k_qnorms(const float* __restrict__ zq, int Q, int n, float* __restrict__ out) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= Q) return;
+  double s = 0.0;
+  for (int t = lane; t < n; t += 32) {
+    const double z = zq[row * n + t];
+    s += z * z;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) out[row] = (float)s;
+}
+
+int launch_row_norms(Index* ix, cudaStream_t st) {
+  k_row_norms<<<(unsigned)ceil_div(ix->N * 32, 256), 256, 0, st>>>(ix->Z, ix->N, ix->n, ix->xn);
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int launch_dense(Index* ix, const DenseArgs& A, cudaStream_t st) {
+  CUtensorMap tq, tx;
+  TRYD(make_map(&tq, A.zq, A.Q, ix->n, DM));
+  TRYD(make_map(&tx, ix->Z, ix->N, ix->n, DN));
+  TRYD(A.qn_buf->ensure((size_t)A.Q * sizeof(float)));
+  float* qn = A.qn_buf->as<float>();
+  k_qnorms<<<(unsigned)ceil_div((int64_t)A.Q * 32, 256), 256, 0, st>>>(A.zq, A.Q, ix->n, qn);
+  SOFA_CUDA(cudaGetLastError());
+  int sms = 0, dev = 0;
+  SOFA_CUDA(cudaGetDevice(&dev));
+  SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int gx = (int)ceil_div(A.Q, DM);
+  const int64_t n_tiles = ceil_div(ix->N, DN);
+  // about two waves of one CTA per SM; the query blocks of a chunk are
+  // adjacent in launch order, so its series tiles are read once from HBM
+  const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(n_tiles, (2 * sms + gx - 1) / gx));
+  DenseParams D;
+  D.N = ix->N;
+  D.Q = A.Q;
+  D.n = ix->n;
+  D.k = A.k;
+  D.cap = A.cap;
+  D.pool_cap = A.pool_cap;
+  D.tiles_per_cta = ceil_div(n_tiles, chunks);
+  D.margin = dense_margin(ix->n);
+  D.f_half = std::nextafter(A.f_prune * 0.5f, INFINITY);
+  const dim3 grid((unsigned)gx, (unsigned)ceil_div(n_tiles, D.tiles_per_cta));
+  if (A.k == 1) {
+    SOFA_CUDA(cudaFuncSetAttribute(k_dense<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, DENSE_SMEM));
+    k_dense<1><<<grid, DM, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p, A.cand_lb,
+                                             A.cand_n, A.pool_n, A.pool_q, A.pool_p, A.pool_lb, A.qpool_cnt, A.dump,
+                                             A.counters, A.status);
+  } else {
+    SOFA_CUDA(cudaFuncSetAttribute(k_dense<DKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, DENSE_SMEM));
+    k_dense<DKMAX><<<grid, DM, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p,
+                                                 A.cand_lb, A.cand_n, A.pool_n, A.pool_q, A.pool_p, A.pool_lb,
+                                                 A.qpool_cnt, A.dump, A.counters, A.status);
+  }
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace sofa
+
+using namespace sofa;
+
+extern "C" int sofa_dense_sqdist(sofa_handle h, const float* queries, int64_t Q, float* out, float* margin,
+                                 sofa_stream stream) {
+  if (!h || !queries || !out) return fail(SOFA_ERR_INVALID_ARG, "null argument");
+  if (Q < 1 || Q > 8192) return fail(SOFA_ERR_INVALID_ARG, "Q must lie in [1, 8192]");
+  if (Q * h->N > ((int64_t)1 << 31)) return fail(SOFA_ERR_INVALID_ARG, "Q * N must be <= 2^31");
+  if (!dense_supported(h, 1)) return fail(SOFA_ERR_INVALID_ARG, "the dense contraction needs n % 4 == 0");
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, queries) != cudaSuccess || a.type != cudaMemoryTypeDevice ||
+      cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(SOFA_ERR_INVALID_ARG, "queries and out must be device memory");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  QueryScratch& s = h->qs;
+  TRYD(s.zq.ensure((size_t)Q * h->n * sizeof(float)));
+  TRYD(s.qv.ensure((size_t)Q * h->NB * sizeof(float)));
+  TRYD(s.thr.ensure((size_t)Q * sizeof(float)));
+  TRYD(s.counters.ensure(16 * sizeof(unsigned long long)));
+  TRYD(launch_qprep(h, queries, Q, s.zq.as<float>(), s.qv.as<float>(), st));
+  SOFA_CUDA(cudaMemsetAsync(s.thr.p, 0x7F, (size_t)Q * sizeof(float), st));  // huge thresholds
+  DenseArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.zq = s.zq.as<float>();
+  A.Q = (int)Q;
+  A.k = 1;
+  A.cap = 1;
+  A.f_prune = 1.f;
+  A.thr = s.thr.as<float>();
+  A.dump = out;
+  A.counters = s.counters.as<unsigned long long>();
+  A.status = reinterpret_cast<int*>(s.counters.as<unsigned long long>() + 8);
+  A.qn_buf = &s.qn;
+  TRYD(launch_dense(h, A, st));
+  if (margin) *margin = dense_margin(h->n);
+  return 0;
+}

@@ -10,6 +10,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -642,6 +644,54 @@ const int32_t* mlp_topm(Index* ix, int* m, int64_t* block) {
   *m = ix->mlp->top_m;
   *block = ix->mlp->block;
   return ix->mlp->topm.as<int32_t>();
+}
+
+// Proposal network in an index file: shape, state and statistics, then the
+// FP32 master weights (the BF16 copy is derived again on loading).
+int mlp_save(const Index* ix, void* file) {
+  FILE* f = static_cast<FILE*>(file);
+  const Mlp* m = ix->mlp;
+  const int64_t hdr[8] = {m->din, m->H, m->C, m->top_m, m->block, m->trained ? 1 : 0, m->n_train, m->total};
+  const double stats[3] = {m->train_loss, m->val_top1, m->val_topm};
+  std::vector<float> w((size_t)m->total);
+  if (m->total) SOFA_CUDA(cudaMemcpy(w.data(), m->P, (size_t)m->total * sizeof(float), cudaMemcpyDeviceToHost));
+  if (fwrite(hdr, sizeof(hdr), 1, f) != 1 || fwrite(stats, sizeof(stats), 1, f) != 1 ||
+      fwrite(w.data(), sizeof(float), w.size(), f) != w.size())
+    return fail(SOFA_ERR_INVALID_ARG, "write failed");
+  return 0;
+}
+
+int mlp_load(Index* ix, void* file, cudaStream_t st) {
+  FILE* f = static_cast<FILE*>(file);
+  int64_t hdr[8];
+  double stats[3];
+  if (fread(hdr, sizeof(hdr), 1, f) != 1 || fread(stats, sizeof(stats), 1, f) != 1)
+    return fail(SOFA_ERR_INVALID_ARG, "truncated index file (proposal network)");
+  if (hdr[0] != 32 || hdr[1] < 1 || hdr[1] > 4096 || hdr[2] < 1 || hdr[2] > (1 << 20) || hdr[3] < 1 ||
+      hdr[3] > 16 || hdr[3] > hdr[2] || hdr[4] < 1)
+    return fail(SOFA_ERR_INVALID_ARG, "index file: inconsistent proposal network header");
+  Mlp* m = new (std::nothrow) Mlp();
+  if (!m) return fail(SOFA_ERR_OOM, "host allocation failed");
+  m->din = (int)hdr[0];
+  m->H = (int)hdr[1];
+  m->C = (int)hdr[2];
+  m->top_m = (int)hdr[3];
+  m->block = hdr[4];
+  m->n_train = hdr[6];
+  m->train_loss = stats[0];
+  m->val_top1 = stats[1];
+  m->val_topm = stats[2];
+  ix->mlp = m;  // freed with the index on any error below
+  TRYM(m->alloc());
+  if (m->total != hdr[7]) return fail(SOFA_ERR_INVALID_ARG, "index file: proposal network size mismatch");
+  std::vector<float> w((size_t)m->total);
+  if (fread(w.data(), sizeof(float), w.size(), f) != w.size())
+    return fail(SOFA_ERR_INVALID_ARG, "truncated index file (proposal network)");
+  SOFA_CUDA(cudaMemcpy(m->P, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice));
+  TRYM(m->sync_bf16(st));
+  SOFA_CUDA(cudaStreamSynchronize(st));
+  m->trained = hdr[5] != 0;
+  return 0;
 }
 
 void mlp_report(Index* ix, double* loss, double* top1, double* topm, int64_t* classes, int64_t* n_train) {

@@ -258,7 +258,6 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
   float* szq = reinterpret_cast<float*>(ssm);            // n
   __shared__ float sq[LW];
   __shared__ unsigned long long skey[SEED_MAX];
-  __shared__ unsigned long long sbest[8];
   const int64_t q = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid < LW) sq[tid] = qv[q * P.NB + tid];
@@ -515,7 +514,8 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
                                               const __half2* __restrict__ ch16, float f16, float inv_f16,
                                               const int* __restrict__ qslot, uint32_t* __restrict__ cand_p,
                                               float* __restrict__ cand_lb, int* __restrict__ cand_n,
-                                              int64_t pool_cap, int* __restrict__ pool_n, int* __restrict__ pool_q,
+                                              int64_t pool_cap, unsigned long long* __restrict__ pool_n,
+                                              int* __restrict__ pool_q,
                                               uint32_t* __restrict__ pool_p, float* __restrict__ pool_lb,
                                               int* __restrict__ qpool_cnt, unsigned long long* __restrict__ counters) {
   extern __shared__ float2 tabs[];
@@ -684,15 +684,16 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
         if (hit) {
           const int qs = sslot[g];
           const int npop = __popc(hit);
-          int base = 0, pbase = 0;
+          int base = 0;
+          unsigned long long pbase = 0;  // 64-bit: appends are counted even after the pool is full
           if (lane == 0) base = atomicAdd(cand_n + qs, npop);
           base = __shfl_sync(0xFFFFFFFFu, base, 0);
           // slots beyond the query's region go to the shared pool
           const int over0 = base > P.cap ? base : P.cap;
           const int nover = base + npop - over0;
           if (lane == 0 && nover > 0) {
-            pbase = atomicAdd(pool_n, nover);
-            const int64_t room = pool_cap - pbase;
+            pbase = atomicAdd(pool_n, (unsigned long long)nover);
+            const int64_t room = pool_cap - (int64_t)pbase;
             const int written = room <= 0 ? 0 : (room < nover ? (int)room : nover);
             if (written > 0) atomicAdd(qpool_cnt + qs, written);
           }
@@ -767,11 +768,12 @@ __global__ void __launch_bounds__(1024) k_chunk_plan(int64_t slots, int cap, con
 }
 
 // Counting-sort scatter of the pool into per-slot segments (grid-stride).
-__global__ void k_pool_scatter(const int* __restrict__ pool_n, int64_t pool_cap, const int* __restrict__ pool_q,
+__global__ void k_pool_scatter(const unsigned long long* __restrict__ pool_n, int64_t pool_cap,
+                               const int* __restrict__ pool_q,
                                const uint32_t* __restrict__ pool_p, const float* __restrict__ pool_lb,
                                const int* __restrict__ qpool_off, int* __restrict__ qcursor,
                                uint32_t* __restrict__ sp, float* __restrict__ slb) {
-  const int64_t n = *pool_n < pool_cap ? *pool_n : pool_cap;
+  const int64_t n = *pool_n < (unsigned long long)pool_cap ? (int64_t)*pool_n : pool_cap;
   const int lane = threadIdx.x & 31;
   // the scan wrote each query's entries in runs: lanes with the same query
   // share one atomic (warp-uniform loop bounds keep every lane in the vote)
@@ -815,7 +817,7 @@ __global__ void k_chunk_fill(int64_t slots, int cap, const int* __restrict__ can
 // round reads the current value, so all chunks of a query tighten together.
 // The first candidate whose bound exceeds the threshold ends the chunk.
 constexpr int RROUND = 64;  // candidates refined per round: 8 warps x 8 groups of 4 lanes
-template <bool FILTER>
+template <int FILTER>  // 0: FP32 only; 1: int8 rows first; 2: value codes, then int8 rows
 __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, const int* __restrict__ n_chunks_ptr,
                                                 const int* __restrict__ chunk_q, const int* __restrict__ choff,
                                                 const int* __restrict__ qof, const float* __restrict__ zq,
@@ -827,6 +829,9 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
                                                 uint32_t* __restrict__ chunk_p, int* __restrict__ chunk_n,
                                                 const int8_t* __restrict__ Z8, const float* __restrict__ s8,
                                                 const float* __restrict__ e8, float one_minus_g,
+                                                const float* __restrict__ qv, const int8_t* __restrict__ VC,
+                                                const float2* __restrict__ vsr, const float* __restrict__ vw,
+                                                float one_minus_gv,
                                                 unsigned long long* __restrict__ counters, int* __restrict__ status) {
   extern __shared__ float4 rsm[];
   float* szq = reinterpret_cast<float*>(rsm);  // n
@@ -838,11 +843,15 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
   __shared__ int s_nacc, s_nl, s_lost, s_nsurv, s_stop0;  // s_stop0: thread 0 only
   __shared__ float s_lim, s_T0;
   __shared__ uint32_t surv[FILTER ? 256 : 1];
+  __shared__ uint32_t s1[FILTER == 2 ? 256 : 1];      // survivors of the value-code bound
+  __shared__ float sqv[FILTER == 2 ? NB_MAX : 1];     // the query's selected values
+  __shared__ float sw[FILTER == 2 ? NB_MAX : 1];      // their Eq. (1) weights
+  __shared__ int s_n1;
   constexpr int NBK = 32;  // bound buckets of a chunk
   __shared__ int bcnt[NBK + 1], bcur[NBK + 1];
   __shared__ uint16_t ord[RSORT];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned long long refined = 0, filtered = 0;
+  unsigned long long refined = 0, filtered = 0, vfiltered = 0;
   const int n_chunks = *n_chunks_ptr;
   for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
   __syncthreads();
@@ -854,6 +863,11 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
   const int c0 = c * RSORT;
   const int cc = total - c0 < RSORT ? total - c0 : RSORT;
   for (int t = tid; t < P.n; t += blockDim.x) szq[t] = zq[q * P.n + t];
+  if constexpr (FILTER == 2)
+    for (int t = tid; t < P.NB; t += blockDim.x) {
+      sqv[t] = qv[q * P.NB + t];
+      sw[t] = vw[t];
+    }
   volatile float* vthr = thr;
   if (tid == 0) {
     s_nl = 0;
@@ -946,7 +960,7 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
       atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(t));  // t >= 0: int order = float order
     }
   };
-  if constexpr (FILTER) {
+  if constexpr (FILTER != 0) {
     // rounds of 256 candidates, one per thread: the int8 bound
     // d(q, x) >= d(q, s v) - e (2 T is the squared distance bound, T in half
     // units); only survivors get the FP32 distance, by groups of 4 lanes
@@ -958,9 +972,45 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
       // while a warp still reads it
       if (tid == 0) {
         s_nsurv = 0;
+        s_n1 = 0;
         s_stop0 = edge_of(base) > T;
       }
       __syncthreads();
+      // candidates of this round entering the int8 stage: the value-code
+      // survivors (compacted into s1), or the round's ordered candidates
+      int n1 = nlive - base < 256 ? nlive - base : 256;
+      if constexpr (FILTER == 2) {
+        // Eq. (1) on the selected values from their int8 codes, one candidate
+        // per thread: ||q~ - s c||_w - r <= ||q - v||_w <= d(q, x)
+        const int j = base + tid;
+        const int i = j < nlive ? ord[j] : 0;
+        if (j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T) {
+          const uint32_t p = (uint32_t)skey[i];
+          const float2 sr = __ldg(vsr + p);
+          const uint4* cp = reinterpret_cast<const uint4*>(VC + (int64_t)p * P.NB);
+          float a0 = 0.f, a1 = 0.f;
+          for (int u = 0; u < P.NB / 16; ++u) {
+            const uint4 w4 = __ldg(cp + u);
+            const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+              for (int e = 0; e < 4; e += 2) {
+                const int t0 = 16 * u + 4 * b + e;
+                const float c0 = (float)((int)(ws[b] << (24 - 8 * e)) >> 24);
+                const float c1 = (float)((int)(ws[b] << (16 - 8 * e)) >> 24);
+                const float d0 = fmaf(-sr.x, c0, sqv[t0]), d1 = fmaf(-sr.x, c1, sqv[t0 + 1]);
+                a0 = fmaf(d0 * sw[t0], d0, a0);          // weight 0, 1 or 2: exact products
+                a1 = fmaf(d1 * sw[t0 + 1], d1, a1);
+              }
+          }
+          const float lbv = __fsub_rd(__fsqrt_rd(__fmul_rd(a0 + a1, one_minus_gv)), sr.y);
+          if (lbv > 0.f && __fmul_rd(lbv, lbv) > 2.0f * T) ++vfiltered;
+          else s1[atomicAdd(&s_n1, 1)] = p;
+        }
+        __syncthreads();
+        n1 = s_n1;
+      }
       if ((P.n & 15) == 0) {
         // 16 lanes per candidate row: lane `sub` reads 16-byte pieces sub,
         // sub + 16, ... of the int8 row and the matching float4s of the query
@@ -970,15 +1020,23 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
         // four candidates per half-warp at a time: all their loads are issued
         // before any reduction, and the query float4s are shared by the four
         for (int it = 0; it < 16; it += 4) {
+          if (FILTER == 2 && it * 16 >= n1) break;  // n1 is the same for the whole block
           bool act[4];
           uint32_t pp[4];
           float sc[4], a0[4], a1[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const int j = base + warp * 32 + (it + k) * 2 + half;
-            const int i = j < nlive ? ord[j] : 0;
-            act[k] = j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T;
-            pp[k] = act[k] ? (uint32_t)skey[i] : 0u;
+            if constexpr (FILTER == 2) {
+              // compacted survivors, spread over all half-warps first
+              const int jj = (it + k) * 16 + warp * 2 + half;
+              act[k] = jj < n1;
+              pp[k] = act[k] ? s1[jj] : 0u;
+            } else {
+              const int j = base + warp * 32 + (it + k) * 2 + half;
+              const int i = j < nlive ? ord[j] : 0;
+              act[k] = j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T;
+              pp[k] = act[k] ? (uint32_t)skey[i] : 0u;
+            }
             sc[k] = act[k] ? __ldg(s8 + pp[k]) : 0.f;
             a0[k] = 0.f;
             a1[k] = 0.f;
@@ -1023,10 +1081,18 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
           }
         }
       } else {
-        const int j = base + tid;
-        const int i = j < nlive ? ord[j] : 0;
-        if (j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T) {
-          const uint32_t p = (uint32_t)skey[i];
+        bool act;
+        uint32_t p = 0u;
+        if constexpr (FILTER == 2) {
+          act = tid < n1;
+          if (act) p = s1[tid];
+        } else {
+          const int j = base + tid;
+          const int i = j < nlive ? ord[j] : 0;
+          act = j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T;
+          if (act) p = (uint32_t)skey[i];
+        }
+        if (act) {
           const float e2 = thread_sqdist8(szq, Z8, s8[p], p, P.n);
           const float lbd = __fsub_rd(__fsqrt_rd(__fmul_rd(e2, one_minus_g)), e8[p]);
           if (lbd > 0.f && __fmul_rd(lbd, lbd) > 2.0f * T) ++filtered;
@@ -1096,6 +1162,7 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
   }
   if ((lane & 3) == 0 && refined) atomicAdd(counters + 3, refined);
   if (FILTER && filtered) atomicAdd(counters + 12, filtered);
+  if (FILTER == 2 && vfiltered) atomicAdd(counters + 13, vfiltered);
 }
 
 // Merge of a query's kept list with the lists of its refined chunks: drop
@@ -1119,12 +1186,58 @@ __global__ void __launch_bounds__(256) k_merge(QueryParams P, const int* __restr
   const int64_t slot_q = qslot ? qslot[q] : q;
   const int all = cand_n[slot_q];
   if (all == 0) return;
-  // the threshold is an upper bound of (k-th d2) * f_prune / 2: entries above
-  // that k-th estimate widened by the keep factor cannot reach the window
-  const float lim = __fmul_ru(__fdiv_ru(__fmul_ru(thr[q], 2.0f), P.f_prune), P.f_keep);
+  const int rq = all < P.cap ? all : P.cap;
+  const int stored = rq + qpool_cnt[slot_q];
+  const int nch = (stored + RSORT - 1) / RSORT;
+  const int c_first = choff[slot_q];
+  // The window limit: D_k f_keep, D_k the k-th smallest distance among the
+  // kept list and this pass's chunk lists.  Three upper bounds of D_k: the
+  // threshold (a k-th distance of k real entries, times f_prune / 2), the kept
+  // list's own k-th, and the k-th smallest over the chunk lists.  The last is
+  // found exactly by bisection on the fp32 bit pattern (distances are >= 0,
+  // so bit order is value order), counting with a binary search in each
+  // chunk's sorted list; a series occurs at most once among one pass's chunks.
+  // The entries under the smallest bound number at most about 2k, so none is
+  // lost however many chunks the query has.
+  __shared__ unsigned s_count;
+  __shared__ int s_total;
+  if (tid == 0) s_total = 0;
+  __syncthreads();
+  for (int c = c_first + tid; c < c_first + nch; c += blockDim.x) atomicAdd(&s_total, chunk_n[c]);
+  __syncthreads();
+  float lim_c = INFINITY;
+  if (s_total >= P.k) {
+    uint32_t lo = 0u, hi = 0x7F800000u;  // count(<= hi) >= k holds for hi = +inf
+    while (lo < hi) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      const float x = __uint_as_float(mid);
+      if (tid == 0) s_count = 0;
+      __syncthreads();
+      unsigned cnt = 0;
+      for (int c = c_first + tid; c < c_first + nch; c += blockDim.x) {
+        const float* cd = chunk_d + (int64_t)c * KCAP;
+        int a = 0, b = chunk_n[c];  // first index with cd > x
+        while (a < b) {
+          const int m = (a + b) >> 1;
+          if (cd[m] <= x) a = m + 1;
+          else b = m;
+        }
+        cnt += (unsigned)a;
+      }
+      if (cnt) atomicAdd(&s_count, cnt);
+      __syncthreads();
+      if (s_count >= (unsigned)P.k) hi = mid;
+      else lo = mid + 1;
+      __syncthreads();
+    }
+    lim_c = __uint_as_float(hi);
+  }
+  const int nl = list_n[q];
+  const float lim_k = nl >= P.k ? list_d[q * KCAP + P.k - 1] : INFINITY;
+  const float lim = fminf(__fmul_ru(__fdiv_ru(__fmul_ru(thr[q], 2.0f), P.f_prune), P.f_keep),
+                          __fmul_ru(fminf(lim_c, lim_k), P.f_keep));
   if (tid == 0) s_cnt = 0;
   __syncthreads();
-  const int nl = list_n[q];
   for (int i = tid; i < nl; i += blockDim.x) {
     const float d = list_d[q * KCAP + i];
     if (i < P.k || d <= lim) {
@@ -1132,10 +1245,7 @@ __global__ void __launch_bounds__(256) k_merge(QueryParams P, const int* __restr
       if (a < MSORT) skey[a] = pack_key(d, list_p[q * KCAP + i]);
     }
   }
-  const int rq = all < P.cap ? all : P.cap;
-  const int stored = rq + qpool_cnt[slot_q];
-  const int nch = (stored + RSORT - 1) / RSORT;
-  for (int c = choff[slot_q]; c < choff[slot_q] + nch; ++c) {
+  for (int c = c_first; c < c_first + nch; ++c) {
     const int m = chunk_n[c];
     const float* cd = chunk_d + (int64_t)c * KCAP;
     const uint32_t* cp = chunk_p + (int64_t)c * KCAP;
@@ -1348,6 +1458,14 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
                                                   s.list_n.as<int>(), thr, status, counters, topm, top_m, block);
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
+  if (ix->approximate) {  // the approximate search's answer: the seed's kept list, re-scored
+    ix->prof.begin(5, st);
+    k_final<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(), idx,
+                                           dist, counters, status);
+    ix->prof.end(st);
+    SOFA_CUDA(cudaGetLastError());
+    return 0;
+  }
 
   // series-bound arithmetic: FP32, or FP16x2 with the derived factor
   // f16 = 1 + (LW/2 + 5) u16 (u16 = 2^-11) on the threshold
@@ -1372,7 +1490,8 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   int* qflag_out = s.qflag.as<int>();
   if (!s.h_pinned) SOFA_CUDA(cudaMallocHost((void**)&s.h_pinned, 4 * sizeof(int)));
   int* h_over = s.h_pinned;
-  std::vector<int> hflag, hslot;
+  std::vector<int> hflag, hslot, deferred;
+  const int max_passes = 64 + 8 * (int)std::min<int64_t>(Q, 1 << 20);
   // graph-eligible batches size the routed lists by their upper bounds
   const bool upper = ix->use_graph && Q * L <= ((int64_t)1 << 28);
   if (upper) {
@@ -1391,13 +1510,16 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   TRYQ(s.pool_lb.ensure((size_t)pool_cap * sizeof(float)));
   TRYQ(s.pool_sp.ensure((size_t)pool_cap * sizeof(uint32_t)));
   TRYQ(s.pool_slb.ensure((size_t)pool_cap * sizeof(float)));
-  int* pool_n = status + 3;
+  unsigned long long* pool_n = counters + 14;  // attempted pool appends (64-bit)
   int* n_chunks = status + 4;
   // persistent refinement grid: resident CTAs of the instantiation that runs
-  auto refine_fn = (ix->refine_filter && ix->Z8) ? k_refine<true> : k_refine<false>;
-  static int refine_grid[2] = {0, 0};
-  int& refine_blocks = refine_grid[(ix->refine_filter && ix->Z8) ? 1 : 0];
-  if (refine_blocks == 0) {
+  // (with the value-code stage the static and dynamic shared memory may pass
+  // 48 KB, so the dynamic part is declared)
+  const int rlevel = (ix->refine_filter && ix->Z8) ? (ix->refine_filter == 2 && ix->VC ? 2 : 1) : 0;
+  auto refine_fn = rlevel == 2 ? k_refine<2> : rlevel == 1 ? k_refine<1> : k_refine<0>;
+  SOFA_CUDA(cudaFuncSetAttribute(refine_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm));
+  int refine_blocks = 0;
+  {
     int per_sm = 0, sms = 0, dev = 0;
     SOFA_CUDA(cudaGetDevice(&dev));
     SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1417,7 +1539,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     TRYQ(s.chunk_p.ensure((size_t)max_chunks * KCAP * sizeof(uint32_t)));
     TRYQ(s.chunk_n.ensure((size_t)max_chunks * sizeof(int)));
     SOFA_CUDA(cudaMemsetAsync(s.qpool_cnt.p, 0, (slots + 1) * sizeof(int), st));
-    SOFA_CUDA(cudaMemsetAsync(pool_n, 0, sizeof(int), st));
+    SOFA_CUDA(cudaMemsetAsync(pool_n, 0, sizeof(unsigned long long), st));
     SOFA_CUDA(cudaMemsetAsync(s.leaf_cnt.p, 0, (L + 1) * sizeof(int), st));
     SOFA_CUDA(cudaMemsetAsync(s.cand_n.p, 0, Q * sizeof(int), st));
     SOFA_CUDA(cudaMemsetAsync(qflag_out, 0, Q * sizeof(int), st));
@@ -1433,28 +1555,66 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     SOFA_CUDA(cudaGetLastError());
     // sizes of the routed list and the unit list are only known on the device:
     // read the two totals back (one small copy per pass)
+    // When the leaf bounds pass more than half of the (query, leaf block)
+    // pairs, the series bounds would prune little: the batch is bounded by the
+    // dense tensor-core contraction instead (same candidate store).
+    bool dense = false;
     if (!(upper && pass == 0)) {
       if (capturing) return fail(SOFA_ERR_CUDA, "capture needs upper-bound buffers");
       int* tot = h_over + 2;
       SOFA_CUDA(cudaMemcpyAsync(&tot[0], s.leaf_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
       SOFA_CUDA(cudaMemcpyAsync(&tot[1], s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
       SOFA_CUDA(cudaStreamSynchronize(st));
-      TRYQ(s.leaf_q.ensure(((size_t)tot[0] + 1) * sizeof(int)));
-      TRYQ(s.units.ensure(((size_t)tot[1] + 1) * sizeof(int4)));
+      const int64_t active = pass == 0 ? Q : slots;
+      dense = ix->dense_mode != 1 && dense_supported(ix, k) &&
+              (ix->dense_mode == 2 || 2 * (int64_t)tot[0] > active * L);
+      if (!dense) {
+        TRYQ(s.leaf_q.ensure(((size_t)tot[0] + 1) * sizeof(int)));
+        TRYQ(s.units.ensure(((size_t)tot[1] + 1) * sizeof(int4)));
+      }
     }
-    ix->prof.begin(2, st, 2);
-    k_route_fill<<<rb, 256, 0, st>>>(Q, L, llb, thr, qsel, s.leaf_off.as<int>(), cursor, s.leaf_q.as<int>());
-    k_units<<<(unsigned)ceil_div(L, 256), 256, 0, st>>>(L, P.group, s.leaf_cnt.as<int>(), s.leaf_off.as<int>(),
-                                                         s.unit_off.as<int>(), s.units.as<int4>());
-    SOFA_CUDA(cudaMemcpyAsync(n_units, s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToDevice, st));
-    ix->prof.end(st);
-    ix->prof.begin(3, st);
-    scan_fn<<<nb, 256, scan_smem, st>>>(P, s.units.as<int4>(), n_units, s.leaf_q.as<int>(), qv, thr,
-                                         ix->tenv, ix->words, ix->edge, ix->ch, ix->ch16, f16, inv_f16, qslot,
-                                         s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(), pool_cap,
-                                         pool_n, s.pool_q.as<int>(), s.pool_p.as<uint32_t>(), s.pool_lb.as<float>(),
-                                         s.qpool_cnt.as<int>(), counters);
-    ix->prof.end(st);
+    if (dense) {
+      ix->prof.begin(3, st, 2);
+      DenseArgs A;
+      A.zq = zq;
+      A.Q = (int)Q;
+      A.k = k;
+      A.cap = P.cap;
+      A.pool_cap = pool_cap;
+      A.f_prune = P.f_prune;
+      A.qsel = qsel;
+      A.qslot = qslot;
+      A.thr = thr;
+      A.cand_p = s.cand_p.as<uint32_t>();
+      A.cand_lb = s.cand_lb.as<float>();
+      A.cand_n = s.cand_n.as<int>();
+      A.pool_n = pool_n;
+      A.pool_q = s.pool_q.as<int>();
+      A.pool_p = s.pool_p.as<uint32_t>();
+      A.pool_lb = s.pool_lb.as<float>();
+      A.qpool_cnt = s.qpool_cnt.as<int>();
+      A.dump = nullptr;
+      A.counters = counters;
+      A.status = status;
+      A.qn_buf = &s.qn;
+      TRYQ(launch_dense(ix, A, st));
+      ix->prof.end(st);
+      ix->stats[1] += 1;
+    } else {
+      ix->prof.begin(2, st, 2);
+      k_route_fill<<<rb, 256, 0, st>>>(Q, L, llb, thr, qsel, s.leaf_off.as<int>(), cursor, s.leaf_q.as<int>());
+      k_units<<<(unsigned)ceil_div(L, 256), 256, 0, st>>>(L, P.group, s.leaf_cnt.as<int>(), s.leaf_off.as<int>(),
+                                                           s.unit_off.as<int>(), s.units.as<int4>());
+      SOFA_CUDA(cudaMemcpyAsync(n_units, s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToDevice, st));
+      ix->prof.end(st);
+      ix->prof.begin(3, st);
+      scan_fn<<<nb, 256, scan_smem, st>>>(P, s.units.as<int4>(), n_units, s.leaf_q.as<int>(), qv, thr,
+                                           ix->tenv, ix->words, ix->edge, ix->ch, ix->ch16, f16, inv_f16, qslot,
+                                           s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(),
+                                           pool_cap, pool_n, s.pool_q.as<int>(), s.pool_p.as<uint32_t>(),
+                                           s.pool_lb.as<float>(), s.qpool_cnt.as<int>(), counters);
+      ix->prof.end(st);
+    }
     SOFA_CUDA(cudaGetLastError());
     ix->prof.begin(7, st, 3);
     k_chunk_plan<<<1, 1024, 0, st>>>(slots, P.cap, s.cand_n.as<int>(), s.qpool_cnt.as<int>(), s.qpool_off.as<int>(),
@@ -1468,12 +1628,14 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     ix->prof.end(st);
     ix->prof.begin(4, st, 2);
     const float one_minus_g = std::nextafter((float)(1.0 - (n + 4) * std::ldexp(1.0, -24) / (1.0 - (n + 4) * std::ldexp(1.0, -24))), 0.0f);
+    const float one_minus_gv = std::nextafter((float)(1.0 - (NB + 4) * std::ldexp(1.0, -24) / (1.0 - (NB + 4) * std::ldexp(1.0, -24))), 0.0f);
     refine_fn<<<refine_blocks, 256, nsm, st>>>(P, n_chunks, s.chunk_q.as<int>(), s.choff.as<int>(), qof, zq, ix->Z,
                                              s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(),
                                              s.qpool_cnt.as<int>(), s.qpool_off.as<int>(), s.pool_sp.as<uint32_t>(),
                                              s.pool_slb.as<float>(), thr, s.chunk_d.as<float>(),
                                              s.chunk_p.as<uint32_t>(), s.chunk_n.as<int>(), ix->Z8, ix->s8, ix->e8,
-                                             one_minus_g, counters, status);
+                                             one_minus_g, qv, ix->VC, ix->vsr, ix->vw, one_minus_gv, counters,
+                                             status);
     SOFA_CUDA(cudaGetLastError());
     k_merge<<<(unsigned)Q, 256, 0, st>>>(P, qsel, qslot, s.cand_n.as<int>(), s.qpool_cnt.as<int>(), s.choff.as<int>(),
                                          s.chunk_d.as<float>(), s.chunk_p.as<uint32_t>(), s.chunk_n.as<int>(),
@@ -1484,35 +1646,52 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     if (capturing) break;  // a full pool is detected after the replay
     SOFA_CUDA(cudaMemcpyAsync(h_over, n_overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
     SOFA_CUDA(cudaStreamSynchronize(st));
-    if (*h_over == 0) break;
+    if (*h_over == 0 && deferred.empty()) break;
     ix->stats[5] += 1;
-    if (pass >= 64) {
+    if (pass >= max_passes) {
       rc = fail(SOFA_ERR_TIMEOUT, "candidate overflow passes did not converge");
       break;
     }
-    // Next pass: only the overflowed queries, against their tightened
-    // thresholds, each with an 8x larger candidate buffer (so the passes end:
-    // at the latest when a buffer holds every series).
-    hflag.resize(Q);
+    // Next pass: the queries that overflowed, against their tightened
+    // thresholds, with an 8x larger candidate region (so a query stops
+    // overflowing at the latest when its region holds every series), plus the
+    // queries deferred by an earlier pass.  A pass takes only as many queries
+    // as fit the region budget at the new size; the rest wait, keeping the
+    // kept lists and thresholds they have.
+    hflag.assign(Q, 0);
+    if (*h_over > 0) {
+      SOFA_CUDA(cudaMemcpy(hflag.data(), qflag_out, Q * sizeof(int), cudaMemcpyDeviceToHost));
+      P.cap = (int)std::min<int64_t>((int64_t)P.cap * 8, std::max<int64_t>(ix->N, 1));
+    }
+    for (int i : deferred) hflag[i] = 1;
+    deferred.clear();
+    const int64_t take_max = std::max<int64_t>(1, ix->cand_budget / P.cap);
     hslot.assign(Q, 0);
-    SOFA_CUDA(cudaMemcpy(hflag.data(), qflag_out, Q * sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int> hsel(Q, 0);
     int64_t m = 0;
-    for (int64_t i = 0; i < Q; ++i)
-      if (hflag[i]) hslot[i] = (int)m++;
+    for (int64_t i = 0; i < Q; ++i) {
+      if (!hflag[i]) continue;
+      if (m < take_max) {
+        hsel[i] = 1;
+        hslot[i] = (int)m++;
+      } else {
+        deferred.push_back((int)i);
+      }
+    }
     slots = m;
-    P.cap = (int)std::min<int64_t>((int64_t)P.cap * 8, std::max<int64_t>(ix->N, 1));
     TRYQ(s.qslot.ensure(Q * sizeof(int)));
     SOFA_CUDA(cudaMemcpy(s.qslot.p, hslot.data(), Q * sizeof(int), cudaMemcpyHostToDevice));
     qslot = s.qslot.as<int>();
+    TRYQ(s.qsel.ensure(Q * sizeof(int)));
+    SOFA_CUDA(cudaMemcpy(s.qsel.p, hsel.data(), Q * sizeof(int), cudaMemcpyHostToDevice));
+    qsel = s.qsel.as<int>();
     std::vector<int> hqof((size_t)std::max<int64_t>(m, 1));
     for (int64_t i = 0; i < Q; ++i)
-      if (hflag[i]) hqof[hslot[i]] = (int)i;
+      if (hsel[i]) hqof[hslot[i]] = (int)i;
     TRYQ(s.qof.ensure((size_t)std::max<int64_t>(m, 1) * sizeof(int)));
     SOFA_CUDA(cudaMemcpy(s.qof.p, hqof.data(), hqof.size() * sizeof(int), cudaMemcpyHostToDevice));
     qof = s.qof.as<int>();
-    int* prev = qflag_out;
     qflag_out = (qflag_out == s.qflag.as<int>()) ? s.qflag.as<int>() + Q : s.qflag.as<int>();
-    qsel = prev;
   }
   if (rc) return rc;
   ix->prof.begin(5, st);
@@ -1544,17 +1723,17 @@ static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* i
     SOFA_CUDA(cudaEventCreateWithFlags(&ix->gev[0], cudaEventDisableTiming));
     SOFA_CUDA(cudaEventCreateWithFlags(&ix->gev[1], cudaEventDisableTiming));
   }
-  const int64_t key[12] = {qb, k, ix->bound_precision, ix->refine_filter, ix->seed_mode, ix->group, ix->cand_cap,
-                           ix->seed_count, ix->seed_window, ix->pool_cap, ix->LW, ix->nyq_first};
+  const int64_t key[15] = {qb, k, ix->bound_precision, ix->refine_filter, ix->seed_mode, ix->group, ix->cand_cap,
+                           ix->seed_count, ix->seed_window, ix->pool_cap, ix->LW, ix->nyq_first, ix->approximate, ix->dense_mode, ix->cand_budget};
   Index::GraphEntry* e = nullptr;
   for (auto& g : ix->graphs)
-    if (std::equal(key, key + 12, g.key)) e = &g;
+    if (std::equal(key, key + 15, g.key)) e = &g;
   if (e && !e->failed && e->gen != g_buf_generation) {  // buffers moved since the recording
     cudaGraphExecDestroy(e->exec);
     e->exec = nullptr;
     e = nullptr;
     ix->graphs.erase(std::remove_if(ix->graphs.begin(), ix->graphs.end(),
-                                    [&](const Index::GraphEntry& g) { return std::equal(key, key + 12, g.key); }),
+                                    [&](const Index::GraphEntry& g) { return std::equal(key, key + 15, g.key); }),
                      ix->graphs.end());
   }
   if (e && e->failed) return dispatch_batch(ix, qp, qb, k, ip, dp, st, false);
@@ -1565,7 +1744,7 @@ static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* i
     SOFA_CUDA(cudaStreamSynchronize(st));
     const unsigned long long gen0 = g_buf_generation;
     Index::GraphEntry ne;
-    std::copy(key, key + 12, ne.key);
+    std::copy(key, key + 15, ne.key);
     ne.exec = nullptr;
     ne.failed = true;
     const bool prof_on = ix->prof.on;

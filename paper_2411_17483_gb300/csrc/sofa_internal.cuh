@@ -47,6 +47,7 @@ struct DevBuf {
 struct QueryScratch {
   DevBuf zq;        // Q x n canonical query series
   DevBuf qv;        // Q x NB projected values
+  DevBuf qn;        // Q squared norms of the canonical queries (dense path)
   DevBuf llb;       // Q x L leaf lower bounds (half units)
   DevBuf thr;       // Q prune thresholds (half units, fp32)
   DevBuf list_d;    // Q x KCAP kept squared distances (fp32)
@@ -63,6 +64,7 @@ struct QueryScratch {
   DevBuf cand_n;    // Q candidate counts
   DevBuf qflag;     // 2 x Q per-query flags (overflow), double-buffered
   DevBuf qslot;     // Q candidate-buffer slots of overflowed queries
+  DevBuf qsel;      // Q flags: queries scanned in an overflow pass
   DevBuf pool_q, pool_p, pool_lb;   // shared candidate pool (slot, position, bound)
   DevBuf pool_sp, pool_slb;         // the pool grouped by slot
   DevBuf qpool_cnt, qpool_off, qcursor, choff, chunk_q, qof;
@@ -120,6 +122,10 @@ struct Index {
   int8_t* Z8 = nullptr;        // [N][n] int8 copy (refinement filter), optional
   float* s8 = nullptr;         // [N] its scales
   float* e8 = nullptr;         // [N] its residual norms (rounded up)
+  int8_t* VC = nullptr;        // [N][NB] int8 codes of the selected Fourier values (value filter), optional
+  float2* vsr = nullptr;       // [N] (scale, margin) of the value codes
+  float* vw = nullptr;         // [NB] Eq. (1) weight of each basis column (0 for unused columns)
+  float* xn = nullptr;         // [N] ||x||^2 of each canonical series (dense path)
   uint32_t* perm = nullptr;    // [N] sorted position -> original row
   uint64_t* keys = nullptr;    // [N] sorted layout keys
   uint8_t* keyorder = nullptr; // [64] key bit order (dim << 3 | bit)
@@ -135,8 +141,11 @@ struct Index {
   int64_t pool_cap = 0;        // shared candidate pool entries (0: automatic)
   int refine_filter = 0;       // 1: int8 filter before the FP32 distance
   int use_graph = 0;           // 1: replay recorded CUDA graphs of query batches
+  int64_t cand_budget = (int64_t)1 << 30;  // candidate-region entries of one overflow pass
+  int approximate = 0;         // 1: answers from the seed alone
+  int dense_mode = 0;          // 0: dense contraction when the leaf bound prunes little, 1: never, 2: always
   struct GraphEntry {
-    int64_t key[12];
+    int64_t key[15];
     unsigned long long gen;
     cudaGraphExec_t exec;
     bool failed;
@@ -174,6 +183,37 @@ __device__ inline float znorm_value(float x, double mu, double inv) {
 
 // Launch helpers implemented in the .cu files.
 int build_index(Index* ix, const float* data_dev, const sofa_build_opts& o, cudaStream_t st);
+// Dense path (tensor-core contraction of a whole batch against every series).
+struct DenseArgs {
+  const float* zq;             // Q x n canonical queries of the batch
+  int Q, k, cap;
+  int64_t pool_cap;
+  float f_prune;
+  const int* qsel;             // queries of this pass (nullptr: all)
+  const int* qslot;            // their candidate slots (nullptr: identity)
+  float* thr;                  // per-query thresholds, half units
+  uint32_t* cand_p;
+  float* cand_lb;
+  int* cand_n;
+  unsigned long long* pool_n;
+  int* pool_q;
+  uint32_t* pool_p;
+  float* pool_lb;
+  int* qpool_cnt;
+  float* dump;                 // non-null: write every d~^2 (Q x N) instead of emitting
+  unsigned long long* counters;
+  int* status;
+  DevBuf* qn_buf;
+};
+bool dense_supported(const Index* ix, int k);
+int launch_dense(Index* ix, const DenseArgs& a, cudaStream_t st);
+int launch_row_norms(Index* ix, cudaStream_t st);
+float dense_margin_of(int n);
+
+void destroy_index(Index* ix);
+int mlp_save(const Index* ix, void* file);   // FILE*; 0 or an error code
+int mlp_load(Index* ix, void* file, cudaStream_t st);
+
 int run_query(Index* ix, const float* q_dev, int64_t Q, int k, int64_t* idx_dev, float* dist_dev,
               cudaStream_t st);
 int launch_qprep(Index* ix, const float* q_dev, int64_t Q, float* zq, float* qv, cudaStream_t st);

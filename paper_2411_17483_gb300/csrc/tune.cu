@@ -31,15 +31,15 @@ static std::string tune_key(const Index* ix, int k, int64_t Q) {
   return key;
 }
 
-static bool cache_lookup(const char* path, const std::string& key, sofa_tuning* t) {
+// A cached line holds the timed knobs; the others keep the current values.
+static bool cache_lookup(const char* path, const std::string& key, const sofa_tuning& cur, sofa_tuning* t) {
   if (!path) return false;
   std::ifstream in(path);
   std::string line;
   while (std::getline(in, line)) {
     std::istringstream ls(line);
     std::string k;
-    sofa_tuning c;
-    std::memset(&c, 0, sizeof(c));
+    sofa_tuning c = cur;
     long long pool = 0;
     if (ls >> k >> c.group >> c.cand_cap >> c.seed_count >> c.seed_window >> c.bound_precision >> pool >>
         c.refine_filter) {
@@ -69,6 +69,9 @@ static void apply(Index* ix, const sofa_tuning& t) {
   ix->pool_cap = t.pool_cap;
   ix->refine_filter = t.refine_filter;
   ix->use_graph = t.use_graph;
+  ix->cand_budget = t.cand_budget ? t.cand_budget : ((int64_t)1 << 30);
+  ix->dense_mode = t.dense;
+  ix->approximate = t.approximate;
 }
 
 }  // namespace sofa
@@ -87,15 +90,6 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
   Index* ix = h;
   cudaStream_t st = (cudaStream_t)stream;
   const std::string key = tune_key(ix, k, Q);
-  sofa_tuning best;
-  std::memset(&best, 0, sizeof(best));
-  if (cache_lookup(cache_path, key, &best)) {
-    apply(ix, best);
-    if (chosen) *chosen = best;
-    return 0;
-  }
-  // candidate grid (all exact); the current setting is the first candidate
-  std::vector<sofa_tuning> cands;
   sofa_tuning cur;
   std::memset(&cur, 0, sizeof(cur));
   cur.group = ix->group;
@@ -106,6 +100,17 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
   cur.pool_cap = ix->pool_cap;
   cur.refine_filter = ix->refine_filter;
   cur.use_graph = ix->use_graph;
+  cur.cand_budget = ix->cand_budget;
+  cur.dense = ix->dense_mode;
+  cur.approximate = ix->approximate;
+  sofa_tuning best = cur;
+  if (cache_lookup(cache_path, key, cur, &best)) {
+    apply(ix, best);
+    if (chosen) *chosen = best;
+    return 0;
+  }
+  // candidate grid (all exact); the current setting is the first candidate
+  std::vector<sofa_tuning> cands;
   cands.push_back(cur);
   const int groups[] = {32, 64};
   const int windows[] = {1024, 4096};
@@ -113,7 +118,7 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
   for (int g : groups)
     for (int w : windows)
       for (int c : counts)
-        for (int f = 0; f <= (ix->Z8 ? 1 : 0); ++f) {
+        for (int f = 0; f <= ((ix->Z8 && ix->VC) ? 2 : 0); ++f) {
           sofa_tuning t = cur;
           t.group = g;
           t.seed_window = w;

@@ -45,7 +45,8 @@ class TrainOpts(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("cand_cap", ctypes.c_int32), ("seed_count", ctypes.c_int32),
                 ("seed_window", ctypes.c_int32), ("bound_precision", ctypes.c_int32), ("pool_cap", ctypes.c_int64),
-                ("refine_filter", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("refine_filter", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("cand_budget", ctypes.c_int64),
+                ("dense", ctypes.c_int32), ("approximate", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -53,7 +54,10 @@ class Stats(ctypes.Structure):
                 ("queries", "leaf_pairs", "tile_pairs", "candidates", "refined", "overflow_passes",
                  "n_leaves", "n_tiles", "filtered", "graph_replays", "graphs_recorded")] + [
                     ("seed_dist_sum", ctypes.c_double),
-                                                        ("final_dist_sum", ctypes.c_double)]
+                                                        ("final_dist_sum", ctypes.c_double),
+                                                        ("value_filtered", ctypes.c_int64),
+                                                        ("dense_pairs", ctypes.c_int64),
+                                                        ("dense_passes", ctypes.c_int64)]
 
 
 class Profile(ctypes.Structure):
@@ -106,6 +110,9 @@ def load():
         "sofa_export_perm": (ctypes.c_int, [P, P]),
         "sofa_lower_bounds": (ctypes.c_int, [P, P, i64, P, P]),
         "sofa_lower_bounds_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
+        "sofa_dense_sqdist": (ctypes.c_int, [P, P, i64, P, ctypes.POINTER(ctypes.c_float), P]),
+        "sofa_save": (ctypes.c_int, [P, ctypes.c_char_p]),
+        "sofa_load": (P, [ctypes.c_char_p, P]),
         "sofa_znorm": (ctypes.c_int, [P, i64, i32, P, P]),
         "sofa_free": (None, [P]),
         "sofa_last_error": (ctypes.c_char_p, []),
@@ -165,6 +172,23 @@ class Index:
         self.h = ctypes.c_void_p(h)
         self.N, self.n, self.l, self.alphabet = data.shape[0], data.shape[1], l, alphabet
 
+    def save(self, path: str):
+        """sofa_save: every array of the index (and a trained proposal network) to one file."""
+        _check(load().sofa_save(self.h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Index":
+        """sofa_load: an index recreated on the current device from a file of sofa_save."""
+        lib = load()
+        h = lib.sofa_load(str(path).encode(), _stream(stream))
+        if not h:
+            raise SofaError(-1, lib.sofa_last_error().decode())
+        ix = cls.__new__(cls)
+        ix.h = ctypes.c_void_p(h)
+        inf = ix.info()
+        ix.N, ix.n, ix.l, ix.alphabet = inf["N"], inf["n"], inf["l"], inf["alphabet"]
+        return ix
+
     def close(self):
         if getattr(self, "h", None):
             load().sofa_free(self.h)
@@ -190,8 +214,9 @@ class Index:
         return idx, dist
 
     def set_tuning(self, group=0, cand_cap=0, seed_count=0, seed_window=0, bound_precision=0, pool_cap=0,
-                   refine_filter=0, use_graph=0):
-        t = Tuning(group, cand_cap, seed_count, seed_window, bound_precision, pool_cap, refine_filter, use_graph)
+                   refine_filter=0, use_graph=0, cand_budget=0, dense=0, approximate=0):
+        t = Tuning(group, cand_cap, seed_count, seed_window, bound_precision, pool_cap, refine_filter, use_graph,
+                   cand_budget, dense, approximate)
         _check(load().sofa_set_tuning(self.h, ctypes.byref(t)))
 
     def autotune(self, q: torch.Tensor, k: int = 1, cache_path: str | None = None, stream=None) -> dict:
@@ -257,6 +282,16 @@ class Index:
         out = torch.empty((q.shape[0], self.N), dtype=torch.float32, device=q.device)
         _check(load().sofa_lower_bounds(self.h, _ptr(q), q.shape[0], _ptr(out), _stream(stream)))
         return out
+
+
+def dense_sqdist(index: "Index", q: torch.Tensor, stream=None):
+    """sofa_dense_sqdist: (Q x N approximate squared distances in sorted
+    order, their error bound M)."""
+    q = q.contiguous()
+    out = torch.empty((q.shape[0], index.N), dtype=torch.float32, device=q.device)
+    m = ctypes.c_float(0.0)
+    _check(load().sofa_dense_sqdist(index.h, _ptr(q), q.shape[0], _ptr(out), ctypes.byref(m), _stream(stream)))
+    return out, m.value
 
 
 def lower_bounds_noalloc(index: "Index", q: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:

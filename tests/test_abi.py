@@ -58,3 +58,17 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     assert not lib.sofa_build(buf, 1, 8, 9, 256)            # l > candidate values (7 for n = 8)
     lib.sofa_query.restype = ctypes.c_int
     assert lib.sofa_query(None, None, 1, 1, None, None, None) == -1
+
+
+def test_load_rejects_missing_and_foreign_files(tmp_path):
+    """sofa_load fails cleanly (NULL and a message) without touching a GPU for
+    files that are missing or not index files."""
+    import ctypes
+    from paper_2411_17483_gb300 import sofa
+    lib = sofa.load()
+    assert not lib.sofa_load(str(tmp_path / "absent.sofa").encode(), None)
+    assert b"cannot open" in lib.sofa_last_error()
+    bad = tmp_path / "foreign.bin"
+    bad.write_bytes(b"NOTSOFA!" + b"\0" * 64)
+    assert not lib.sofa_load(str(bad).encode(), None)
+    assert b"not an index file" in lib.sofa_last_error()

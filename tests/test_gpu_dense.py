@@ -1,0 +1,100 @@
+"""Dense tensor-core form of the query: its approximate squared distances
+stay within the derived bound M of the FP64 distances, and the answers it
+leads to are the oracle's."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sofa_oracle as orc
+from paper_2411_17483_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def sofa():
+    from paper_2411_17483_gb300 import sofa as s
+    s.load()
+    return s
+
+
+def oracle_knn(x, q, k):
+    z, _, _ = orc.znorm(x.cpu().numpy())
+    zq, _, _ = orc.znorm(q.cpu().numpy())
+    return orc.knn(z, zq, k)
+
+
+# N not a multiple of the 256-series tile, Q not a multiple of the 128-query
+# block, n not a multiple of the 32-value k-block (zero-filled tails)
+@pytest.mark.parametrize("N,n,Q,gen", [(3000, 256, 200, "rw"), (1000, 100, 130, "sin"), (700, 1024, 64, "sin"),
+                                       (257, 32, 1, "rw")])
+def test_dense_sqdist_within_margin(sofa, N, n, Q, gen):
+    x = datagen.random_walks(N, n, seed=N, device=DEV) if gen == "rw" else \
+        datagen.sinusoid_mix(N, n, seed=N, device=DEV)
+    q = datagen.random_walks(Q, n, seed=N + 1, device=DEV) if gen == "rw" else \
+        datagen.sinusoid_mix(Q, n, seed=N + 1, device=DEV)
+    ix = sofa.Index(x, 8 if n <= 64 else 16, 256)
+    out, margin = sofa.dense_sqdist(ix, q)
+    torch.cuda.synchronize()
+    perm = ix.perm().numpy().astype(np.int64)         # sorted position -> original row
+    z, _, _ = orc.znorm(x.cpu().numpy())
+    zq, _, _ = orc.znorm(q.cpu().numpy())
+    exact = np.stack([orc.sqdist(z, zq[i]) for i in range(Q)])    # Q x N, original order
+    approx = np.empty_like(exact)
+    approx[:, perm] = out.cpu().numpy().astype(np.float64)
+    err = np.abs(approx - exact)
+    assert np.all(np.isfinite(approx))
+    assert err.max() <= margin, (err.max(), margin)
+    # the bound is not vacuous: TF32 errors are a visible part of it
+    assert err.max() > 1e-6 * margin
+    ix.close()
+
+
+@pytest.mark.parametrize("N,n,l,k,Q,gen", [(20000, 128, 16, 1, 64, "rw"), (20000, 256, 16, 5, 48, "mixed"),
+                                           (9000, 96, 16, 16, 16, "sin"), (12000, 1024, 32, 1, 40, "sin"),
+                                           (100, 16, 6, 4, 3, "rw")])
+def test_dense_knn_matches_oracle(sofa, N, n, l, k, Q, gen):
+    if gen == "rw":
+        x = datagen.random_walks(N, n, seed=N + n, device=DEV)
+    elif gen == "mixed":
+        x = datagen.mixed_walks(N, n, seed=N + n, device=DEV)
+    else:
+        x = datagen.sinusoid_mix(N, n, seed=N + n, device=DEV)
+    q = datagen.half_perturbed_queries(x, Q, seed=5)
+    ix = sofa.Index(x, l, 256)
+    ix.set_tuning(dense=2)
+    ix.stats(reset=True)
+    gi, gd = ix.query(q, k)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    st = ix.stats()
+    assert st["dense_passes"] >= 1 and st["dense_pairs"] > 0
+    oi, od = oracle_knn(x, q, k)
+    gi = gi.cpu().numpy()
+    gdv = gd.cpu().numpy().astype(np.float64)
+    assert np.array_equal(gi, oi)
+    assert np.array_equal(gdv.astype(np.float32), od.astype(np.float32))
+    # the scan form gives the same answers
+    ix.set_tuning(dense=1)
+    gi2, gd2 = ix.query(q, k)
+    assert np.array_equal(gi2.cpu().numpy(), gi) and torch.equal(gd2, gd)
+    ix.close()
+
+
+def test_dense_chosen_when_bounds_fail(sofa):
+    """High-frequency data: the SFA bound passes nearly every leaf, so the
+    automatic mode takes the dense form; answers stay exact."""
+    N, n, Q = 40000, 512, 32
+    x = datagen.sinusoid_mix(N, n, seed=77, device=DEV)
+    q = datagen.sinusoid_mix(Q, n, seed=78, device=DEV)
+    ix = sofa.Index(x, 16, 256)
+    ix.stats(reset=True)
+    gi, gd = ix.query(q, 1)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    assert ix.stats()["dense_passes"] >= 1
+    oi, od = oracle_knn(x, q, 1)
+    assert np.array_equal(gi.cpu().numpy(), oi)
+    ix.close()

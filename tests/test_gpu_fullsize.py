@@ -1,0 +1,227 @@
+"""Parity at the full sizes of the benchmark workloads.
+
+Every dataset is rebuilt here from its seeded generator at full size.
+* Sampled queries are compared with the oracle's brute force over every row.
+  The oracle works chunk by chunk, each chunk regenerated from the same seeded
+  stream, so the host never holds a whole dataset.
+* Properties that hold at any size are checked over all queries. The main one
+  is that every precision and seeding mode returns identical answers.
+The 100M x 256 case runs in the launch configuration the benchmark times:
+- an index with the int8 copy;
+- a batch of 10,000 queries, answered as one batch of 8192 and one of 1808;
+- k = 1;
+- the learned seed with the int8 refinement filter, and the plain FP32 form.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sofa_oracle as orc
+from paper_2411_17483_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def sofa():
+    from paper_2411_17483_gb300 import sofa as s
+    s.load()
+    return s
+
+
+def need_bytes(nbytes):
+    free, _ = torch.cuda.mem_get_info()
+    if free < nbytes:
+        pytest.skip(f"needs {nbytes / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
+
+
+def oracle_sample(gen_rows, N, q, k, chunk):
+    """Brute-force k-NN of the rows of q over the N rows gen_rows(row0, rows)
+    yields on the device, one chunk at a time."""
+    zq, _, _ = orc.znorm(q.cpu().numpy())
+
+    def chunks():
+        for r0 in range(0, N, chunk):
+            rows = min(chunk, N - r0)
+            x = gen_rows(r0, rows)
+            z, _, _ = orc.znorm(x.cpu().numpy())
+            del x
+            yield r0, z
+
+    return orc.knn_chunked(chunks(), zq, k)
+
+
+def assert_sample_equal(gi, gd, oi, od):
+    gi = gi.cpu().numpy()
+    gd = gd.cpu().numpy().astype(np.float64)
+    bad = np.nonzero(np.any(gi != oi, axis=1))[0]
+    assert len(bad) == 0, f"{len(bad)} sampled queries differ, first {bad[:5]}: gpu {gi[bad[0]]} oracle {oi[bad[0]]}"
+    rel = np.abs(gd - od) / np.maximum(od, 1e-30)
+    assert rel.max() <= 1e-4
+    assert np.array_equal(gd.astype(np.float32), od.astype(np.float32))
+
+
+def answers_valid(gi, gd, N, k):
+    """k valid, distinct neighbours per query, in ascending distance up to the
+    tie rule (a run within 1e-6 relative is ordered by id instead)."""
+    assert gi.shape[1] == k
+    assert int(gi.min()) >= 0 and int(gi.max()) < N
+    assert bool(torch.all(torch.isfinite(gd)))
+    if k > 1:
+        assert bool(torch.all(gd[:, 1:] >= gd[:, :-1] * (1 - 2e-6)))
+        s, _ = torch.sort(gi, dim=1)
+        assert bool(torch.all(s[:, 1:] != s[:, :-1]))
+
+
+def test_rw100M_benchmark_configuration(sofa):
+    """100M x 256 random walks, 10,000 fresh random-walk queries, exact 1-NN."""
+    N, n, Q = 100_000_000, 256, 10_000
+    torch.cuda.empty_cache()
+    need_bytes(250e9)
+    x = torch.empty((N, n), dtype=torch.float32, device=DEV)
+    datagen.random_walks(N, n, seed=0, device=DEV, out=x)
+    ix = sofa.Index(x, 16, 256, sample_ratio=0.1, precision=1)
+    del x
+    torch.cuda.empty_cache()
+    ix.train_proposal(n_train=262_144, n_classes=4096, epochs=2, batch=4096, seed=2, top_m=4)
+    q = datagen.random_walks(Q, n, seed=1, device=DEV)
+    ix.set_seed_mode(0)
+    ix.set_tuning(refine_filter=0)
+    gi0, gd0 = ix.query(q, 1)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    ix.set_seed_mode(1)
+    ix.set_tuning(refine_filter=1)
+    gi1, gd1 = ix.query(q, 1)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    # every query: both modes give the same answer, and a valid one
+    assert torch.equal(gi0, gi1) and torch.equal(gd0, gd1)
+    answers_valid(gi1, gd1, N, 1)
+    ix.close()
+    # sampled queries from both batches (first, last, and the batch boundary)
+    sample = [0, 1, 4095, 8191, 8192, 9999]
+    oi, od = oracle_sample(lambda r0, rows: datagen.random_walks(rows, n, seed=0, device=DEV, row0=r0),
+                           N, q[sample], 1, chunk=1 << 22)
+    assert_sample_equal(gi1[sample], gd1[sample], oi, od)
+
+
+@pytest.mark.parametrize("k", [1, 10])
+def test_mixed10M_precision_modes(sofa, k):
+    """10M x 256: half random walks, half walks + N(0, 0.5^2) noise; 1,000
+    queries (half perturbed members, half fresh walks); FP32 bounds and
+    refinement vs FP16 bounds and the int8 filter."""
+    N, n, Q = 10_000_000, 256, 1000
+    need_bytes(40e9)
+    x = datagen.mixed_walks(N, n, seed=0, device=DEV)
+    q = datagen.half_perturbed_queries(x, Q, seed=1)
+    ix = sofa.Index(x, 16, 256, sample_ratio=0.1, precision=1)
+    del x
+    torch.cuda.empty_cache()
+    res = []
+    for t in (dict(), dict(refine_filter=1), dict(bound_precision=1, refine_filter=1), dict(bound_precision=1)):
+        ix.set_tuning(**t)
+        gi, gd = ix.query(q, k)
+        torch.cuda.synchronize()
+        assert ix.status() == 0, t
+        res.append((gi, gd))
+    for gi, gd in res[1:]:
+        assert torch.equal(gi, res[0][0]) and torch.equal(gd, res[0][1])
+    answers_valid(res[0][0], res[0][1], N, k)
+    ix.close()
+    sample = list(range(0, Q, 100)) + [499, 500, 999]
+    oi, od = oracle_sample(lambda r0, rows: datagen.mixed_walks(rows, n, seed=0, device=DEV, total=N, row0=r0),
+                           N, q[sample], k, chunk=1 << 22)
+    assert_sample_equal(res[0][0][sample], res[0][1][sample], oi, od)
+
+
+def test_sinusoid10M_n1024_l32(sofa):
+    """High-frequency stress: 10M x 1024 sums of 8 sinusoids plus noise,
+    1,000 queries of the same generator, l = 32, exact 1-NN."""
+    N, n, Q = 10_000_000, 1024, 1000
+    need_bytes(100e9)
+    x = datagen.sinusoid_mix(N, n, seed=0, device=DEV)
+    ix = sofa.Index(x, 32, 256, sample_ratio=0.1)
+    del x
+    torch.cuda.empty_cache()
+    q = datagen.sinusoid_mix(Q, n, seed=1, device=DEV)
+    gi, gd = ix.query(q, 1)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    ix.set_tuning(bound_precision=1)
+    gi2, gd2 = ix.query(q, 1)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    assert torch.equal(gi, gi2) and torch.equal(gd, gd2)
+    answers_valid(gi, gd, N, 1)
+    ix.close()
+    sample = list(range(0, Q, 125)) + [999]
+    oi, od = oracle_sample(lambda r0, rows: datagen.sinusoid_mix(rows, n, seed=0, device=DEV, row0=r0),
+                           N, q[sample], 1, chunk=1 << 20)
+    assert_sample_equal(gi[sample], gd[sample], oi, od)
+
+
+def test_mixed_lengths_four_datasets(sofa):
+    """Four random-walk datasets (25M x 128, 25M x 256, 12M x 512,
+    6M x 1024) answered in one call: 10,000 fresh walks, length uniform over
+    the four, k uniform in {1, 5, 10, 50}."""
+    sets = [(25_000_000, 128), (25_000_000, 256), (12_000_000, 512), (6_000_000, 1024)]
+    torch.cuda.empty_cache()
+    need_bytes(150e9)
+    ixs = []
+    for si, (N, n) in enumerate(sets):
+        x = torch.empty((N, n), dtype=torch.float32, device=DEV)
+        datagen.random_walks(N, n, seed=10 + si, device=DEV, out=x)
+        ixs.append(sofa.Index(x, 16, 256, sample_ratio=0.1))
+        del x
+        torch.cuda.empty_cache()
+    Q = 10_000
+    g = torch.Generator().manual_seed(5)
+    which = torch.randint(0, 4, (Q,), generator=g).tolist()
+    ks = [(1, 5, 10, 50)[int(v)] for v in torch.randint(0, 4, (Q,), generator=g)]
+    per_set = {si: [i for i in range(Q) if which[i] == si] for si in range(4)}
+    qrows = {si: datagen.random_walks(len(per_set[si]), sets[si][1], seed=20 + si, device=DEV) for si in range(4)}
+    pos_in_set = {}
+    for si in range(4):
+        for j, i in enumerate(per_set[si]):
+            pos_in_set[i] = j
+    parts, offs, ql, oo = [], [], [], []
+    pos = out = 0
+    for i in range(Q):
+        si = which[i]
+        n = sets[si][1]
+        parts.append(qrows[si][pos_in_set[i]])
+        offs.append(pos)
+        ql.append(n)
+        oo.append(out)
+        pos += n
+        out += ks[i]
+    packed = torch.cat(parts)
+    idx, dist = sofa.query_multi(ixs, packed, offs, ql, ks, oo, out)
+    torch.cuda.synchronize()
+    for ix in ixs:
+        assert ix.status() == 0
+    # every query gets k valid, distinct neighbours in ascending distance
+    for i in range(0, Q, 97):
+        si, k = which[i], ks[i]
+        gi = idx[oo[i]:oo[i] + k][None, :]
+        gd = dist[oo[i]:oo[i] + k][None, :]
+        answers_valid(gi, gd, sets[si][0], k)
+    for ix in ixs:
+        ix.close()
+    # four sampled queries per dataset against the oracle, in one pass over
+    # the dataset with the largest k of the sample: the k-window of a query is
+    # a prefix of its k_max-window in distance order, and a tie run that starts
+    # inside that prefix ends inside it, so the first k entries of the k_max
+    # answer are the k-NN
+    for si, (N, n) in enumerate(sets):
+        smp = per_set[si][:4]
+        kmax = max(ks[i] for i in smp)
+        oi, od = oracle_sample(lambda r0, rows: datagen.random_walks(rows, n, seed=10 + si, device=DEV, row0=r0),
+                               N, torch.stack([parts[i] for i in smp]), kmax, chunk=max(1 << 18, (1 << 30) // n))
+        for j, i in enumerate(smp):
+            k = ks[i]
+            assert_sample_equal(idx[oo[i]:oo[i] + k][None, :], dist[oo[i]:oo[i] + k][None, :],
+                                oi[j:j + 1, :k], od[j:j + 1, :k])

@@ -157,14 +157,16 @@ def test_knn_matches_oracle(sofa, N, n, l, alpha, k, Q, gen):
     ix.close()
 
 
+@pytest.mark.parametrize("level", [1, 2])
 @pytest.mark.parametrize("N,n,l,alpha,k,Q,gen", [CASES[1], CASES[3], CASES[4], CASES[5]])
-def test_knn_reduced_precision_match_oracle(sofa, N, n, l, alpha, k, Q, gen):
-    """FP16x2 series bounds and the int8 refinement filter, each with its
-    derived margin: the same exact answers."""
+def test_knn_reduced_precision_match_oracle(sofa, N, n, l, alpha, k, Q, gen, level):
+    """FP16x2 series bounds and the refinement filters (int8 rows; value
+    codes then int8 rows), each with its derived margin: the same exact
+    answers."""
     x = make(gen, N, n, seed=N + n + 1)
     q = datagen.half_perturbed_queries(x, Q, seed=4)
     ix = sofa.Index(x, l, alpha, precision=1)
-    ix.set_tuning(bound_precision=1, refine_filter=1)
+    ix.set_tuning(bound_precision=1, refine_filter=level)
     gi, gd = ix.query(q, k)
     oi, od = oracle_knn(x, q, k)
     assert_knn_equal(gi, gd, oi, od)
@@ -192,18 +194,45 @@ def test_duplicates_and_member_queries(sofa):
                                     dict(seed_count=1), dict(seed_count=256), dict(seed_window=4096, seed_count=128),
                                     dict(seed_window=256), dict(bound_precision=1),
                                     dict(bound_precision=1, cand_cap=5, group=7), dict(refine_filter=1),
-                                    dict(refine_filter=1, bound_precision=1, cand_cap=9, pool_cap=40)])
+                                    dict(refine_filter=1, bound_precision=1, cand_cap=9, pool_cap=40),
+                                    dict(refine_filter=2), dict(refine_filter=2, cand_cap=3, pool_cap=5),
+                                    dict(cand_cap=2, pool_cap=3, cand_budget=4),
+                                    dict(refine_filter=2, cand_cap=1, pool_cap=1, cand_budget=1),
+                                    dict(dense=2), dict(dense=2, cand_cap=2, pool_cap=3),
+                                    dict(dense=2, refine_filter=2, cand_cap=3, pool_cap=7, cand_budget=6)])
 def test_tuning_invariance(sofa, tuning):
     N, n = 15000, 128
     x = datagen.mixed_walks(N, n, seed=31, device=DEV)
     q = datagen.half_perturbed_queries(x, 40, seed=2)
     ix = sofa.Index(x, 16, 256, leaf_tiles=4, precision=1)
     gi0, gd0 = ix.query(q, 10)
-    ix.set_tuning(**tuning)
+    t = dict(tuning)
+    if "pool_cap" in t and "dense" not in t:
+        t["dense"] = 1             # the series scan, whose candidates overflow the tiny pool
+    ix.set_tuning(**t)
+    ix.stats(reset=True)
     gi1, gd1 = ix.query(q, 10)
     assert torch.equal(gi0, gi1) and torch.equal(gd0, gd1)
-    if "pool_cap" in tuning:       # a full pool: the queries concerned are scanned again
+    if "pool_cap" in t and t["dense"] == 1:   # a full pool: the queries concerned are scanned again
         assert ix.stats()["overflow_passes"] > 0
+    ix.close()
+
+
+def test_value_code_filter_prunes(sofa):
+    """The value-code bound drops most candidates before any int8 row is read,
+    and the answers stay those of the oracle."""
+    N, n = 60000, 256
+    x = datagen.random_walks(N, n, seed=41, device=DEV)
+    q = datagen.random_walks(64, n, seed=42, device=DEV)
+    ix = sofa.Index(x, 16, 256, precision=1)
+    ix.set_tuning(refine_filter=2, dense=1)   # the series scan's candidates (the dense form's are near-exact)
+    ix.stats(reset=True)
+    gi, gd = ix.query(q, 3)
+    st = ix.stats()
+    assert ix.status() == 0
+    assert st["value_filtered"] > 0
+    oi, od = oracle_knn(x, q, 3)
+    assert_knn_equal(gi, gd, oi, od)
     ix.close()
 
 
@@ -285,3 +314,56 @@ def test_graph_replay_matches_eager(sofa, extra):
     st = ix.stats()
     assert st["graphs_recorded"] >= 1 and st["graph_replays"] >= 4
     ix.close()
+
+
+def test_approximate_mode(sofa):
+    """The approximate search alone (no pruning scan): every answer is a real
+    distance of the returned series, never better than the exact k-th, and
+    most perturbed-member queries find their source row."""
+    N, n, k = 50000, 128, 5
+    x = datagen.random_walks(N, n, seed=81, device=DEV)
+    q = datagen.half_perturbed_queries(x, 64, seed=82)
+    ix = sofa.Index(x, 16, 256)
+    ge, gde = ix.query(q, k)
+    ix.set_tuning(approximate=1)
+    ga, gda = ix.query(q, k)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    z, _, _ = orc.znorm(x.cpu().numpy())
+    zq, _, _ = orc.znorm(q.cpu().numpy())
+    ga_n, gda_n = ga.cpu().numpy(), gda.cpu().numpy()
+    for i in range(q.shape[0]):
+        d = np.sqrt(orc.sqdist(z[ga_n[i]], zq[i]))
+        assert np.array_equal(d.astype(np.float32), gda_n[i])
+    assert bool(torch.all(gda[:, -1] >= gde[:, -1] * (1 - 1e-6)))
+    # half the queries are perturbed members: their 1-NN is usually the key window's
+    hit = np.mean([ge[i, 0].item() in set(ga_n[i]) for i in range(32)])
+    assert hit >= 0.5
+    ix.set_tuning()
+    gi, gd = ix.query(q, k)                  # back to exact
+    assert torch.equal(gi, ge) and torch.equal(gd, gde)
+    ix.close()
+
+
+def test_save_load_roundtrip(sofa, tmp_path):
+    """An index written by sofa_save and read by sofa_load answers exactly as
+    the original, in every precision and seed mode."""
+    N, n = 30000, 128
+    x = datagen.random_walks(N, n, seed=91, device=DEV)
+    q = datagen.half_perturbed_queries(x, 40, seed=92)
+    ix = sofa.Index(x, 16, 256, precision=1)
+    ix.train_proposal(n_train=8192, n_classes=64, epochs=1, batch=2048, seed=2, top_m=4)
+    path = str(tmp_path / "index.sofa")
+    ix.save(path)
+    iy = sofa.Index.load(path)
+    assert iy.info()["N"] == N and iy.info()["proposal_classes"] == 64
+    assert torch.equal(iy.perm(), ix.perm()) and torch.equal(iy.words(), ix.words())
+    for tuning, seed_mode in ((dict(), 0), (dict(refine_filter=2), 1), (dict(approximate=1), 1), (dict(dense=2), 0)):
+        for h in (ix, iy):
+            h.set_seed_mode(seed_mode)
+            h.set_tuning(**tuning)
+        a = ix.query(q, 4)
+        b = iy.query(q, 4)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), tuning
+    ix.close()
+    iy.close()
