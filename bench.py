@@ -60,7 +60,7 @@ def parse():
 # 1808-query batch) from one ncu capture of the default workload, chosen mode;
 # summary and command in profiles/k_scan_dram_rw100M_q10k.md.  Reported only
 # while the kernel's source is the one that was captured.
-SCAN_TRAFFIC = {"bytes_per_launch": 6093278592, "source_sha": "dcf394f6580b02b9",
+SCAN_TRAFFIC = {"bytes_per_launch": 6204032896, "source_sha": "1aa0a20e54f09dc2",
                 "workload": (100_000_000, 256, 10_000, 1, 16)}
 
 

@@ -189,41 +189,61 @@ __device__ __forceinline__ float topk_kth(const float* top, int k) {
   return v;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised CTA of 6 warps: warp 0 issues the TMA loads, warp 1 the
+// MMAs (and owns the tensor memory: two 256-column accumulators, so the
+// epilogue of one series tile overlaps the MMAs of the next), warps 2-5 run
+// the epilogue, each on its quarter of the TMEM lanes (lane quadrant = warp
+// index mod 4).  Barriers: full / empty per pipeline stage (TMA -> MMA ->
+// TMA), tfull / tempty per accumulator (MMA -> epilogue -> MMA).  Every wait
+// is bounded; a timed-out wait stops all roles and sets the status.
+constexpr int DWARPS = 6;
+constexpr int DTHREADS = 32 * DWARPS;
+constexpr int DACC = 2;
+
 template <int KD>
-__global__ void __launch_bounds__(DM, 1) k_dense(const __grid_constant__ CUtensorMap tmQ,
-                                                 const __grid_constant__ CUtensorMap tmX, DenseParams D,
-                                                 const float* __restrict__ qn, const float* __restrict__ xn,
-                                                 const int* __restrict__ qsel, const int* __restrict__ qslot,
-                                                 float* __restrict__ thr, uint32_t* __restrict__ cand_p,
-                                                 float* __restrict__ cand_lb, int* __restrict__ cand_n,
-                                                 unsigned long long* __restrict__ pool_n, int* __restrict__ pool_q,
-                                                 uint32_t* __restrict__ pool_p, float* __restrict__ pool_lb,
-                                                 int* __restrict__ qpool_cnt, float* __restrict__ dump,
-                                                 unsigned long long* __restrict__ counters, int* __restrict__ status) {
+__global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ CUtensorMap tmQ,
+                                                       const __grid_constant__ CUtensorMap tmX, DenseParams D,
+                                                       const float* __restrict__ qn, const float* __restrict__ xn,
+                                                       const int* __restrict__ qsel, const int* __restrict__ qslot,
+                                                       float* __restrict__ thr, uint32_t* __restrict__ cand_p,
+                                                       float* __restrict__ cand_lb, int* __restrict__ cand_n,
+                                                       int* __restrict__ pool_n,
+                                                       int* __restrict__ pool_q, uint32_t* __restrict__ pool_p,
+                                                       float* __restrict__ pool_lb, int* __restrict__ qpool_cnt,
+                                                       float* __restrict__ dump,
+                                                       unsigned long long* __restrict__ counters,
+                                                       int* __restrict__ status) {
   extern __shared__ uint8_t dsm_raw[];
-  __shared__ __align__(8) uint64_t full[DSTAGES], empty[DSTAGES], accf;
+  __shared__ __align__(8) uint64_t full[DSTAGES], empty[DSTAGES], tfull[DACC], tempty[DACC];
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
-  __shared__ float sxn[DN];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t n_tiles = (D.N + DN - 1) / DN;
   const int64_t t_begin = (int64_t)blockIdx.y * D.tiles_per_cta;
   const int64_t t_end = t_begin + D.tiles_per_cta < n_tiles ? t_begin + D.tiles_per_cta : n_tiles;
   if (t_begin >= t_end) return;  // the whole CTA, before any barrier or allocation
-  // stage buffers on a 1024-byte boundary (the 128-byte swizzle atom)
   const uint32_t raw = smem_u32(dsm_raw);
-  uint8_t* stages = dsm_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* stages = dsm_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte swizzle atoms
   const int q0 = blockIdx.x * DM;
   const int kblocks = (D.n + DK - 1) / DK;
-  const int64_t total = (t_end - t_begin) * kblocks;
+  const int64_t ntiles = t_end - t_begin;
+  const int64_t total = ntiles * kblocks;
+  volatile int* vfail = &s_fail;
 
-  if (warp == 0) tmem_alloc(&s_tmem, DN);
+  if (warp == 1) tmem_alloc(&s_tmem, DN * DACC);
   if (tid == 0) {
     for (int s = 0; s < DSTAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&accf, 1);
+    for (int a = 0; a < DACC; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4 * 32);  // every epilogue thread
+    }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -232,133 +252,143 @@ __global__ void __launch_bounds__(DM, 1) k_dense(const __grid_constant__ CUtenso
   tc_fence_after();
   const uint32_t tmem = s_tmem;
 
-  // this thread's query (its TMEM lane)
-  const int q = q0 + tid;
-  const bool qa = q < D.Q && (!qsel || qsel[q]);
-  const int nq_active = __syncthreads_count(qa);  // for the pair counter
-  const int qs = qa ? (qslot ? qslot[q] : q) : 0;
-  const float qnr = qa ? qn[q] : 0.f;
-  volatile float* vthr = thr;
-  float T = qa ? vthr[q] : -1.f;  // emission threshold, half units
-  float top[KD];
-#pragma unroll
-  for (int i = 0; i < KD; ++i) top[i] = INFINITY;
-  unsigned long long emitted = 0;
+  // epilogue threads: one query each (its TMEM lane)
+  const bool epi = warp >= 2;
+  const int er = 32 * (warp & 3) + lane;
+  const int q = q0 + er;
+  const bool qa = epi && q < D.Q && (!qsel || qsel[q]);
+  const int nq_active = __syncthreads_count(qa);
 
-  // thread 0 drives TMA and the MMAs: loads run DSTAGES - 1 k-blocks ahead
-  int64_t issued = 0;
-  auto issue = [&](int64_t idx) -> bool {
-    const int s = (int)(idx % DSTAGES);
-    if (idx >= DSTAGES && !mbar_wait(&empty[s], (uint32_t)((idx / DSTAGES - 1) & 1))) return false;
-    const int64_t tile = t_begin + idx / kblocks;
-    const int kb = (int)(idx % kblocks);
-    uint8_t* a = stages + s * STAGE_BYTES;
-    mbar_expect_tx(&full[s], STAGE_BYTES);
-    tma_load_2d(a, &tmQ, kb * DK, q0, &full[s]);
-    tma_load_2d(a + A_BYTES, &tmX, kb * DK, (int)(tile * DN), &full[s]);
-    return true;
-  };
-  if (tid == 0)
-    while (issued < total && issued < DSTAGES - 1) {
-      if (!issue(issued)) {
-        s_fail = 1;
-        break;
-      }
-      ++issued;
-    }
-
-  int64_t ti = 0;
-  for (int64_t t = t_begin; t < t_end; ++t, ++ti) {
-    if (tid == 0 && !s_fail) {
-      bool ok = true;
-      for (int kb = 0; kb < kblocks && ok; ++kb) {
-        const int64_t idx = ti * kblocks + kb;
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      for (int64_t idx = 0; idx < total; ++idx) {
         const int s = (int)(idx % DSTAGES);
-        if (!mbar_wait(&full[s], (uint32_t)((idx / DSTAGES) & 1))) {
-          ok = false;
+        if (idx >= DSTAGES && !mbar_wait(&empty[s], (uint32_t)((idx / DSTAGES - 1) & 1))) {
+          *vfail = 1;
+          break;
+        }
+        if (*vfail) break;
+        const int64_t tile = t_begin + idx / kblocks;
+        const int kb = (int)(idx % kblocks);
+        uint8_t* a = stages + s * STAGE_BYTES;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_2d(a, &tmQ, kb * DK, q0, &full[s]);
+        tma_load_2d(a + A_BYTES, &tmX, kb * DK, (int)(tile * DN), &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      for (int64_t ti = 0; ti < ntiles && !*vfail; ++ti) {
+        const int acc = (int)(ti & 1);
+        if (ti >= DACC && !mbar_wait(&tempty[acc], (uint32_t)((ti / DACC - 1) & 1))) {
+          *vfail = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t a = smem_u32(stages + s * STAGE_BYTES);
-        const uint64_t ad = sw128_desc(a), bd = sw128_desc(a + A_BYTES);
+        const uint32_t dcol = tmem + (uint32_t)(acc * DN);
+        bool ok = true;
+        for (int kb = 0; kb < kblocks; ++kb) {
+          const int64_t idx = ti * kblocks + kb;
+          const int s = (int)(idx % DSTAGES);
+          if (!mbar_wait(&full[s], (uint32_t)((idx / DSTAGES) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+          const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < DK / 8; ++kk)  // K = 8 tf32 values (32 bytes) per MMA
-          mma_tf32(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0 ? 1u : 0u);
-        mma_commit(&empty[s]);
-        if (issued < total) {
-          if (!issue(issued)) ok = false;
-          ++issued;
+          for (int kk = 0; kk < DK / 8; ++kk)  // K = 8 tf32 values (32 bytes) per MMA
+            mma_tf32(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0 ? 1u : 0u);
+          mma_commit(&empty[s]);
         }
+        if (!ok) {
+          *vfail = 1;
+          break;
+        }
+        mma_commit(&tfull[acc]);
       }
-      if (ok) mma_commit(&accf);
-      else s_fail = 1;
     }
-    // every thread: the accumulator of this tile
-    if (!mbar_wait(&accf, (uint32_t)(ti & 1))) atomicExch(&s_fail, 1);
-    tc_fence_after();
-    const int64_t s0 = t * DN;
-    for (int j = tid; j < DN; j += DM) sxn[j] = s0 + j < D.N ? xn[s0 + j] : 0.f;
-    __syncthreads();
-    if (s_fail) break;  // the same value for every thread after the barrier
-    if (qa) T = fminf(T, vthr[q]);
-    const float T_in = T;
-#pragma unroll 1
-    for (int c0 = 0; c0 < DN; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);  // warp-collective
-      if (!qa) continue;
+  } else {
+    // epilogue
+    const int qs = qa ? (qslot ? qslot[q] : q) : 0;
+    const float qnr = qa ? qn[q] : 0.f;
+    volatile float* vthr = thr;
+    float T = qa ? vthr[q] : -1.f;  // emission threshold, half units
+    float top[KD];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int64_t sidx = s0 + c0 + i;
-        if (sidx >= D.N) break;
-        const float d2 = fmaf(-2.f, v[i], qnr + sxn[c0 + i]);
-        if (dump) {
-          dump[(int64_t)q * D.N + sidx] = d2;
-          continue;
-        }
-        const float lb = __fmul_rd(__fsub_rd(d2, D.margin), 0.5f);  // lower bound, half units
-        if (lb > T) continue;
-        // a candidate: into the query's region, its excess into the pool
-        ++emitted;
-        const int slot = atomicAdd(cand_n + qs, 1);
-        if (slot < D.cap) {
-          cand_p[(int64_t)qs * D.cap + slot] = (uint32_t)sidx;
-          cand_lb[(int64_t)qs * D.cap + slot] = fmaxf(lb, 0.f);
-        } else {
-          const unsigned long long pb = atomicAdd(pool_n, 1ull);
-          if ((int64_t)pb < D.pool_cap) {
-            pool_q[pb] = qs;
-            pool_p[pb] = (uint32_t)sidx;
-            pool_lb[pb] = fmaxf(lb, 0.f);
-            atomicAdd(qpool_cnt + qs, 1);
+    for (int i = 0; i < KD; ++i) top[i] = INFINITY;
+    unsigned long long emitted = 0;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    for (int64_t ti = 0; ti < ntiles; ++ti) {
+      const int acc = (int)(ti & 1);
+      // warp-uniform: the TMEM loads below are warp-collective
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(&tfull[acc], (uint32_t)((ti / DACC) & 1)))) {
+        *vfail = 1;
+        break;
+      }
+      tc_fence_after();
+      const int64_t s0 = (t_begin + ti) * DN;
+      if (qa) T = fminf(T, vthr[q]);
+      const float T_in = T;
+#pragma unroll 1
+      for (int c0 = 0; c0 < DN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(acc * DN + c0), v);  // warp-collective
+        const float xv = s0 + c0 + lane < D.N ? __ldg(xn + s0 + c0 + lane) : 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float xi = __shfl_sync(0xFFFFFFFFu, xv, i);  // every lane takes part
+          const int64_t sidx = s0 + c0 + i;
+          if (!qa || sidx >= D.N) continue;
+          const float d2 = fmaf(-2.f, v[i], qnr + xi);
+          if (dump) {
+            dump[(int64_t)q * D.N + sidx] = d2;
+            continue;
+          }
+          const float lb = __fmul_rd(__fsub_rd(d2, D.margin), 0.5f);  // lower bound, half units
+          if (lb > T) continue;
+          ++emitted;
+          const int slot = atomicAdd(cand_n + qs, 1);
+          if (slot < D.cap) {
+            cand_p[(int64_t)qs * D.cap + slot] = (uint32_t)sidx;
+            cand_lb[(int64_t)qs * D.cap + slot] = fmaxf(lb, 0.f);
+          } else {
+            // the pool counter grows only while the pool has room (it cannot wrap)
+            const int pb = *reinterpret_cast<volatile int*>(pool_n) < D.pool_cap ? atomicAdd(pool_n, 1)
+                                                                                  : (int)D.pool_cap;
+            if (pb < D.pool_cap) {
+              pool_q[pb] = qs;
+              pool_p[pb] = (uint32_t)sidx;
+              pool_lb[pb] = fmaxf(lb, 0.f);
+              atomicAdd(qpool_cnt + qs, 1);
+            }
+          }
+          if (d2 < top[KD - 1]) {
+            topk_insert<KD>(top, d2);
+            const float kth = topk_kth<KD>(top, D.k);
+            // k series with d^2 <= d~^2 + M each: a valid threshold
+            if (kth < INFINITY) T = fminf(T, __fmul_ru(__fadd_ru(kth, D.margin), D.f_half));
           }
         }
-        if (d2 < top[KD - 1]) {
-          topk_insert<KD>(top, d2);
-          const float kth = topk_kth<KD>(top, D.k);
-          // k series with d^2 <= d~^2 + M each: a valid threshold
-          if (kth < INFINITY) T = fminf(T, __fmul_ru(__fadd_ru(kth, D.margin), D.f_half));
-        }
       }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);  // the accumulator is free for the MMA warp
+      if (qa && T < T_in) atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(T));  // T >= 0
+      if (__any_sync(0xFFFFFFFFu, *vfail != 0)) break;
     }
-    if (qa && T < T_in) atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(T));  // T >= 0
-    tc_fence_before();
-    __syncthreads();  // the accumulator and sxn are free for the next tile
+    if (emitted) atomicAdd(counters + 2, emitted);
   }
-  if (s_fail && tid == 0) atomicExch(status, SOFA_ERR_TIMEOUT);
-  if (emitted) atomicAdd(counters + 2, emitted);
+  __syncthreads();
   if (tid == 0) {
+    if (*vfail) atomicExch(status, SOFA_ERR_TIMEOUT);
     const int64_t s_hi = t_end * DN < D.N ? t_end * DN : D.N;
     atomicAdd(counters + 11, (unsigned long long)nq_active * (unsigned long long)(s_hi - t_begin * DN));
   }
-  // loads still in flight after a failure: wait for them (bounded) before the
-  // shared memory goes away
-  if (tid == 0 && s_fail)
-    for (int64_t idx = ti * kblocks; idx < issued; ++idx) mbar_wait(&full[idx % DSTAGES], (uint32_t)((idx / DSTAGES) & 1));
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, DN);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, DN * DACC);
+  }
 }
 
 // ------------------------------------------------------------------------
@@ -472,12 +502,12 @@ int launch_dense(Index* ix, const DenseArgs& A, cudaStream_t st) {
   const dim3 grid((unsigned)gx, (unsigned)ceil_div(n_tiles, D.tiles_per_cta));
   if (A.k == 1) {
     SOFA_CUDA(cudaFuncSetAttribute(k_dense<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, DENSE_SMEM));
-    k_dense<1><<<grid, DM, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p, A.cand_lb,
+    k_dense<1><<<grid, DTHREADS, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p, A.cand_lb,
                                              A.cand_n, A.pool_n, A.pool_q, A.pool_p, A.pool_lb, A.qpool_cnt, A.dump,
                                              A.counters, A.status);
   } else {
     SOFA_CUDA(cudaFuncSetAttribute(k_dense<DKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, DENSE_SMEM));
-    k_dense<DKMAX><<<grid, DM, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p,
+    k_dense<DKMAX><<<grid, DTHREADS, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p,
                                                  A.cand_lb, A.cand_n, A.pool_n, A.pool_q, A.pool_p, A.pool_lb,
                                                  A.qpool_cnt, A.dump, A.counters, A.status);
   }

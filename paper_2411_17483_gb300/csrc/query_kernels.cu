@@ -514,8 +514,7 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
                                               const __half2* __restrict__ ch16, float f16, float inv_f16,
                                               const int* __restrict__ qslot, uint32_t* __restrict__ cand_p,
                                               float* __restrict__ cand_lb, int* __restrict__ cand_n,
-                                              int64_t pool_cap, unsigned long long* __restrict__ pool_n,
-                                              int* __restrict__ pool_q,
+                                              int64_t pool_cap, int* __restrict__ pool_n, int* __restrict__ pool_q,
                                               uint32_t* __restrict__ pool_p, float* __restrict__ pool_lb,
                                               int* __restrict__ qpool_cnt, unsigned long long* __restrict__ counters) {
   extern __shared__ float2 tabs[];
@@ -684,16 +683,18 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
         if (hit) {
           const int qs = sslot[g];
           const int npop = __popc(hit);
-          int base = 0;
-          unsigned long long pbase = 0;  // 64-bit: appends are counted even after the pool is full
+          int base = 0, pbase = 0;
           if (lane == 0) base = atomicAdd(cand_n + qs, npop);
           base = __shfl_sync(0xFFFFFFFFu, base, 0);
           // slots beyond the query's region go to the shared pool
           const int over0 = base > P.cap ? base : P.cap;
           const int nover = base + npop - over0;
           if (lane == 0 && nover > 0) {
-            pbase = atomicAdd(pool_n, (unsigned long long)nover);
-            const int64_t room = pool_cap - (int64_t)pbase;
+            // the counter grows only while the pool has room, so however
+            // many candidates are refused it stays below pool_cap + 32 x
+            // (warps in flight) and cannot wrap
+            pbase = *reinterpret_cast<volatile int*>(pool_n) < pool_cap ? atomicAdd(pool_n, nover) : (int)pool_cap;
+            const int64_t room = pool_cap - pbase;
             const int written = room <= 0 ? 0 : (room < nover ? (int)room : nover);
             if (written > 0) atomicAdd(qpool_cnt + qs, written);
           }
@@ -768,12 +769,11 @@ __global__ void __launch_bounds__(1024) k_chunk_plan(int64_t slots, int cap, con
 }
 
 // Counting-sort scatter of the pool into per-slot segments (grid-stride).
-__global__ void k_pool_scatter(const unsigned long long* __restrict__ pool_n, int64_t pool_cap,
-                               const int* __restrict__ pool_q,
+__global__ void k_pool_scatter(const int* __restrict__ pool_n, int64_t pool_cap, const int* __restrict__ pool_q,
                                const uint32_t* __restrict__ pool_p, const float* __restrict__ pool_lb,
                                const int* __restrict__ qpool_off, int* __restrict__ qcursor,
                                uint32_t* __restrict__ sp, float* __restrict__ slb) {
-  const int64_t n = *pool_n < (unsigned long long)pool_cap ? (int64_t)*pool_n : pool_cap;
+  const int64_t n = *pool_n < pool_cap ? *pool_n : pool_cap;
   const int lane = threadIdx.x & 31;
   // the scan wrote each query's entries in runs: lanes with the same query
   // share one atomic (warp-uniform loop bounds keep every lane in the vote)
@@ -1510,7 +1510,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   TRYQ(s.pool_lb.ensure((size_t)pool_cap * sizeof(float)));
   TRYQ(s.pool_sp.ensure((size_t)pool_cap * sizeof(uint32_t)));
   TRYQ(s.pool_slb.ensure((size_t)pool_cap * sizeof(float)));
-  unsigned long long* pool_n = counters + 14;  // attempted pool appends (64-bit)
+  int* pool_n = status + 3;  // pool appends (stops growing once the pool is full)
   int* n_chunks = status + 4;
   // persistent refinement grid: resident CTAs of the instantiation that runs
   // (with the value-code stage the static and dynamic shared memory may pass
@@ -1539,7 +1539,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     TRYQ(s.chunk_p.ensure((size_t)max_chunks * KCAP * sizeof(uint32_t)));
     TRYQ(s.chunk_n.ensure((size_t)max_chunks * sizeof(int)));
     SOFA_CUDA(cudaMemsetAsync(s.qpool_cnt.p, 0, (slots + 1) * sizeof(int), st));
-    SOFA_CUDA(cudaMemsetAsync(pool_n, 0, sizeof(unsigned long long), st));
+    SOFA_CUDA(cudaMemsetAsync(pool_n, 0, sizeof(int), st));
     SOFA_CUDA(cudaMemsetAsync(s.leaf_cnt.p, 0, (L + 1) * sizeof(int), st));
     SOFA_CUDA(cudaMemsetAsync(s.cand_n.p, 0, Q * sizeof(int), st));
     SOFA_CUDA(cudaMemsetAsync(qflag_out, 0, Q * sizeof(int), st));

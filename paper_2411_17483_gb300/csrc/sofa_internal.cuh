@@ -195,7 +195,7 @@ struct DenseArgs {
   uint32_t* cand_p;
   float* cand_lb;
   int* cand_n;
-  unsigned long long* pool_n;
+  int* pool_n;
   int* pool_q;
   uint32_t* pool_p;
   float* pool_lb;

@@ -367,3 +367,23 @@ def test_save_load_roundtrip(sofa, tmp_path):
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), tuning
     ix.close()
     iy.close()
+
+
+def test_unprunable_data_on_the_scan_path(sofa):
+    """High-frequency data where the bound prunes nothing, forced through the
+    series scan with a tiny pool and region budget: the pool counter stops at
+    its capacity, overflow passes regrow the regions (a few queries at a time),
+    and the answers are the oracle's."""
+    N, n, Q, k = 20000, 256, 24, 3
+    x = datagen.sinusoid_mix(N, n, seed=95, device=DEV)
+    q = datagen.sinusoid_mix(Q, n, seed=96, device=DEV)
+    ix = sofa.Index(x, 16, 256)
+    ix.set_tuning(dense=1, cand_cap=16, pool_cap=500, cand_budget=4096)
+    ix.stats(reset=True)
+    gi, gd = ix.query(q, k)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    assert ix.stats()["overflow_passes"] >= 3
+    oi, od = oracle_knn(x, q, k)
+    assert_knn_equal(gi, gd, oi, od)
+    ix.close()
