@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--classes", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="chosen mode with the default tuning instead of the autotuner's choice")
     ap.add_argument("--gen", default="rw", choices=["rw", "mixed", "sin"],
                     help="rw: random walks (default); mixed: half walks + noisy walks with half perturbed-member "
                          "queries; sin: 8-sinusoid mixtures (high-frequency stress, bounds prune little)")
@@ -60,7 +62,7 @@ def parse():
 # 1808-query batch) from one ncu capture of the default workload, chosen mode;
 # summary and command in profiles/k_scan_dram_rw100M_q10k.md.  Reported only
 # while the kernel's source is the one that was captured.
-SCAN_TRAFFIC = {"bytes_per_launch": 6204032896, "source_sha": "1aa0a20e54f09dc2",
+SCAN_TRAFFIC = {"bytes_per_launch": 6428695552, "source_sha": "4f45bbb3e24bb959",
                 "workload": (100_000_000, 256, 10_000, 1, 16)}
 
 
@@ -285,12 +287,26 @@ def run_sofa(a, ws, rank, local):
                  "heldout_top1": inf2["proposal_top1"], "heldout_top4": inf2["proposal_topm"]}
         modes["learned"] = 1
         chosen = "learned"
+    # the chosen mode's run-time tuning: the autotuner's pick on 2048 queries
+    # of a separate stream (seed 100 + rank), never on the timed queries
+    chosen_tuning = dict(refine_filter=2)
+    if not a.no_autotune:
+        qt = make_rows(a, 2048, 100 + rank, dev)
+        ix.set_seed_mode(modes[chosen])
+        ix.set_tuning(refine_filter=2)
+        t = ix.autotune(qt, a.k)
+        chosen_tuning = {k: v for k, v in t.items() if v}
+        del qt
     results = {}
     for mode_name, mode in modes.items():
-        # plain: FP32 bounds and refinement, key-window seed; chosen: learned
-        # seed and the two refinement filters: value codes, then int8 rows (all exact)
+        # plain: FP32 bounds and refinement, key-window seed, default tuning;
+        # chosen: learned seed, the refinement filters (value codes, then int8
+        # rows) and the autotuned knobs (all exact)
         ix.set_seed_mode(mode)
-        ix.set_tuning(refine_filter=2 if mode_name != "plain" else 0)
+        if mode_name == chosen:
+            ix.set_tuning(**chosen_tuning)
+        else:
+            ix.set_tuning()
         for _ in range(a.warmup):
             ix.query(q, a.k, idx, dist)
         torch.cuda.synchronize()
@@ -420,7 +436,7 @@ def run_sofa(a, ws, rank, local):
         ld = torch.empty((64, a.k), dtype=torch.float32, device=dev)
         lat = {}
         for use_graph in (0, 1):
-            ix.set_tuning(refine_filter=2, use_graph=use_graph)
+            ix.set_tuning(**{**chosen_tuning, "use_graph": use_graph})
             for _ in range(3):
                 ix.query(qs, a.k, li, ld)
             torch.cuda.synchronize()
@@ -429,7 +445,7 @@ def run_sofa(a, ws, rank, local):
                 ix.query(qs, a.k, li, ld)
             torch.cuda.synchronize()
             lat["graph_ms" if use_graph else "eager_ms"] = (time.perf_counter() - w0) / 20 * 1e3
-        ix.set_tuning(refine_filter=2)
+        ix.set_tuning(**chosen_tuning)
         latency = {"queries": 64, **lat, "graph_replays": ix.stats()["graph_replays"]}
 
     # the approximate search alone (same seed mode): throughput and recall@k
@@ -438,7 +454,7 @@ def run_sofa(a, ws, rank, local):
     if not a.no_e2e:
         ix.query(q, a.k, idx, dist)                     # exact answers of the chosen mode
         exact = idx.clone()
-        ix.set_tuning(refine_filter=2, approximate=1)
+        ix.set_tuning(**{**chosen_tuning, "approximate": 1})
         ai = torch.empty_like(idx)
         ad = torch.empty_like(dist)
         for _ in range(2):
@@ -455,7 +471,7 @@ def run_sofa(a, ws, rank, local):
         A, E = ai.cpu().numpy(), exact.cpu().numpy()
         hits = sum(len(set(A[i]) & set(E[i])) for i in range(a.Q))
         approx = {"queries_per_s": a.Q / (ms / 1e3), "ms_per_step": ms, "recall_at_k": hits / (a.Q * a.k)}
-        ix.set_tuning(refine_filter=2)
+        ix.set_tuning(**chosen_tuning)
 
     cpu = None
     if cpu_rows is not None:
@@ -473,7 +489,7 @@ def run_sofa(a, ws, rank, local):
             "warmup": a.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "N": a.N, "n": a.n, "Q_per_gpu": a.Q, "k": a.k, "l": a.l,
-                       "alphabet": a.alphabet, "seed_mode": chosen, "precision": "chosen: fp32 bounds (packed f32x2), int8 value-code and int8 row filters (derived margins), fp32 refine, fp64 final re-score",
+                       "alphabet": a.alphabet, "seed_mode": chosen, "tuning": chosen_tuning, "precision": "chosen: fp32 bounds (packed f32x2), int8 value-code and int8 row filters (derived margins), fp32 refine, fp64 final re-score",
                        "l2": "flushed between timed steps (256 MB write)", "build_s": round(t2 - t1, 3),
                        "gen_s": round(t1 - t0, 3), "parallelism": f"replicas x{ws}"},
             "roofline": roof,

@@ -520,6 +520,10 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
   extern __shared__ float2 tabs[];
   float2* sch = tabs;                                                   // LW x 256 (tile checks, FP32 bounds)
   __half2* sch16 = reinterpret_cast<__half2*>(tabs + LW * MAX_ALPHA);   // LW x 256 (FP16 bounds)
+  // per-tile lists of the unit's queries that passed the tile envelope
+  // (leaf_tiles x MAX_GROUP bytes after the tables)
+  uint8_t* sql = reinterpret_cast<uint8_t*>(tabs + LW * MAX_ALPHA) + (H16 ? LW * MAX_ALPHA * sizeof(__half2) : 0);
+  __shared__ uint16_t s_off[MAX_LEAF_TILES + 1];
   __shared__ __align__(16) float sq[MAX_GROUP][LW];
   __shared__ __align__(16) __half2 sq16[MAX_GROUP][LW / 2];
   __shared__ float sT[MAX_GROUP];
@@ -579,11 +583,39 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
     }
     n_checks += (tid == 0) ? (unsigned long long)nt : 0ull;
     __syncthreads();
-    for (int t = 0; t < nt; ++t) {
+    // compact each tile's mask into a list of query indices once per unit, so
+    // the threads walk the list instead of each scanning the mask bits
+    if (tid < 32) {  // exclusive scan of the per-tile counts by one warp
+      int run = 0;
+      for (int base = 0; base < nt; base += 32) {
+        const int t = base + lane;
+        const int c = t < nt ? __popcll(smask[t]) : 0;
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (t < nt) s_off[t] = (uint16_t)(run + x - c);
+        run += __shfl_sync(0xFFFFFFFFu, x, 31);
+      }
+      if (lane == 0) s_off[nt] = (uint16_t)run;
+    }
+    __syncthreads();
+    for (int t = tid; t < nt; t += blockDim.x) {
       unsigned long long m = smask[t];
-      if (!m) continue;
+      int o = s_off[t];
+      while (m) {
+        sql[o++] = (uint8_t)(__ffsll((long long)m) - 1);
+        m &= m - 1;
+      }
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+      const int o0 = s_off[t], o1 = s_off[t + 1];
+      if (o0 == o1) continue;
       if (tid == 0) {
-        n_tile_pairs += __popcll(m);
+        n_tile_pairs += (unsigned long long)(o1 - o0);
         n_loads += 1;
       }
       const int64_t p = (t0 + t) * TILE + tid;
@@ -621,9 +653,8 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
 #pragma unroll
         for (int j = 0; j < LW; ++j) h[j] = __fmul_ru(h[j], a);  // h a, rounded up
       }
-      while (m) {
-        const int g = __ffsll((long long)m) - 1;
-        m &= m - 1;
+      for (int oi = o0; oi < o1; ++oi) {
+        const int g = sql[oi];
         const float T = H16 ? sT[g] * f16 : sTs[g];
         bool live = valid;
         float acc;
@@ -657,12 +688,16 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
           // u = sat(|q - c| a - h a) (one FADD, one FFMA.SAT), two partial sums
           // (even / odd values); the warp votes after 4, 8, 16 (and 32) values
           float a0 = 0.f, a1 = 0.f;
+          bool warp_dead = false;
 #pragma unroll
           for (int stage = 0; stage < 8; ++stage) {
             const int j0 = stage == 0 ? 0 : (4 << (stage - 1));
             const int j1 = 4 << stage;
             if (j0 >= LW) break;
-            if (!__any_sync(0xFFFFFFFFu, live)) break;
+            if (!__any_sync(0xFFFFFFFFu, live)) {
+              warp_dead = true;
+              break;
+            }
 #pragma unroll
             for (int j = j0; j < j1 && j < LW; j += 4) {
               const float4 q4 = qg4[j >> 2];
@@ -678,6 +713,7 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
             live = live && (a0 + a1) <= T;
           }
           acc = __fmul_rd(a0 + a1, s_inva2);  // back to half units, rounded down
+          if (warp_dead) continue;  // warp-uniform: no lane left for this query
         }
         const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
         if (hit) {
@@ -1472,12 +1508,13 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   const bool h16 = ix->bound_precision == 1;
   const float f16 = std::nextafter((float)(1.0 + (LW / 2 + 5) * std::ldexp(1.0, -11)), 2.0f);
   const float inv_f16 = std::nextafter(1.0f / f16, 0.0f);
-  static int scan_blocks[2][2] = {{0, 0}, {0, 0}};
   auto scan_fn = h16 ? k_scan<LW, NYQ, true> : k_scan<LW, NYQ, false>;
-  const size_t scan_smem = (size_t)LW * MAX_ALPHA * (sizeof(float2) + (h16 ? sizeof(__half2) : 0));
+  // symbol tables, then the per-tile query lists (leaf_tiles x MAX_GROUP bytes)
+  const size_t scan_smem = (size_t)LW * MAX_ALPHA * (sizeof(float2) + (h16 ? sizeof(__half2) : 0)) +
+                           (size_t)ix->leaf_tiles * MAX_GROUP;
   SOFA_CUDA(cudaFuncSetAttribute(scan_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem));
-  int& nb = scan_blocks[LW == 32][h16];
-  if (nb == 0) {
+  int nb = 0;  // persistent grid: resident CTAs
+  {
     int per_sm = 0, sms = 0, dev = 0;
     SOFA_CUDA(cudaGetDevice(&dev));
     SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
