@@ -225,3 +225,23 @@ def test_mixed_lengths_four_datasets(sofa):
             k = ks[i]
             assert_sample_equal(idx[oo[i]:oo[i] + k][None, :], dist[oo[i]:oo[i] + k][None, :],
                                 oi[j:j + 1, :k], od[j:j + 1, :k])
+
+
+@pytest.mark.parametrize("mode", ["plain", "filters", "dense"])
+def test_small_configuration_all_queries(sofa, mode):
+    """100,000 random walks of length 256 (seed 0), l = 16, alphabet 256,
+    equi-depth bins on a 10 % sample; 100 fresh random-walk queries (seed 1);
+    exact 1-NN: every query against the oracle's brute force."""
+    N, n, Q = 100_000, 256, 100
+    x = datagen.random_walks(N, n, seed=0, device=DEV)
+    q = datagen.random_walks(Q, n, seed=1, device=DEV)
+    ix = sofa.Index(x, 16, 256, sample_ratio=0.1, precision=1)
+    ix.set_tuning(**{"plain": dict(dense=1), "filters": dict(refine_filter=2, dense=1), "dense": dict(dense=2)}[mode])
+    gi, gd = ix.query(q, 1)
+    torch.cuda.synchronize()
+    assert ix.status() == 0
+    z, _, _ = orc.znorm(x.cpu().numpy())
+    zq, _, _ = orc.znorm(q.cpu().numpy())
+    oi, od = orc.knn(z, zq, 1)
+    assert_sample_equal(gi, gd, oi, od)
+    ix.close()
