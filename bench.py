@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--classes", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, default=1, choices=[1, 2],
+                    help="index copies: 1 int8 copies for the refinement filters; 2 also an FP16 copy for "
+                         "the dense tensor-core form")
     ap.add_argument("--no-autotune", action="store_true",
                     help="chosen mode with the default tuning instead of the autotuner's choice")
     ap.add_argument("--gen", default="rw", choices=["rw", "mixed", "sin"],
@@ -75,6 +78,16 @@ def kernel_source_sha(name="k_scan"):
     a = s.rindex("template <", 0, i)
     b = s.index("\n}\n", i) + 3
     return hashlib.sha256(s[a:b].encode()).hexdigest()[:16]
+
+
+def precision_text(a, stats) -> str:
+    """Arithmetic of the chosen mode, stage by stage."""
+    if stats.get("dense_pairs", 0) > 0:
+        bound = "tcgen05 " + ("fp16" if a.precision == 2 else "tf32") + " contraction (derived margin)"
+    else:
+        bound = "fp32 SFA bounds"
+    return (f"{bound}, int8 value-code and int8 row filters (derived margins), fp32 refine, "
+            "fp64 final re-score")
 
 
 def workload_name(a):
@@ -261,7 +274,7 @@ def run_sofa(a, ws, rank, local):
         cpu_rows = x[: min(a.N, 2_000_000)].cpu().numpy()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    ix = sofa.Index(x, a.l, a.alphabet, sample_ratio=0.1, precision=1)
+    ix = sofa.Index(x, a.l, a.alphabet, sample_ratio=0.1, precision=a.precision)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     # each rank answers its own batch: rank r uses query stream seed 1 + r
@@ -366,16 +379,20 @@ def run_sofa(a, ws, rank, local):
     roof = hbm
     dense_pairs = stats.get("dense_pairs", 0)
     if phase == "scan" and dense_pairs > 0:
-        # dense batches: the bound phase is the tcgen05 TF32 contraction;
-        # tensor roofline against the measured bf16 burst peak times the
-        # nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)
+        # dense batches: the bound phase is the tcgen05 contraction, TF32
+        # operands, or FP16 when the index holds an FP16 copy.  Tensor
+        # roofline: the measured bf16 burst peak, times the nominal
+        # TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s) for TF32; FP16 runs at the
+        # BF16 rate
+        f16 = a.precision == 2 and a.n % 8 == 0
+        ratio, rname = (1.0, "fp16 = bf16 rate") if f16 else (1.1 / 2.25, "x 1.1/2.25 (nominal tf32/bf16)")
         try:
             with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
                 bf16 = float(json.load(f)["bf16_tflops"])
-            pk_kind = "measured bf16 x 1.1/2.25 (nominal tf32/bf16)"
+            pk_kind = f"measured bf16 {rname}"
         except (OSError, KeyError, ValueError):
-            bf16, pk_kind = 1900.0, "fallback bf16 x 1.1/2.25 (nominal tf32/bf16)"
-        peak_t = bf16 * 1.1 / 2.25
+            bf16, pk_kind = 1900.0, f"fallback bf16 {rname}"
+        peak_t = bf16 * ratio
         npad = (a.n + 31) // 32 * 32
         flops = 2.0 * dense_pairs * npad / launches
         ach_t = flops / per_launch_s / 1e12
@@ -489,7 +506,7 @@ def run_sofa(a, ws, rank, local):
             "warmup": a.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "N": a.N, "n": a.n, "Q_per_gpu": a.Q, "k": a.k, "l": a.l,
-                       "alphabet": a.alphabet, "seed_mode": chosen, "tuning": chosen_tuning, "precision": "chosen: fp32 bounds (packed f32x2), int8 value-code and int8 row filters (derived margins), fp32 refine, fp64 final re-score",
+                       "alphabet": a.alphabet, "seed_mode": chosen, "tuning": chosen_tuning, "precision": precision_text(a, stats),
                        "l2": "flushed between timed steps (256 MB write)", "build_s": round(t2 - t1, 3),
                        "gen_s": round(t1 - t0, 3), "parallelism": f"replicas x{ws}"},
             "roofline": roof,

@@ -64,7 +64,13 @@ typedef struct {
   int32_t leaf_tiles;   /* tiles of 256 series per leaf block (<= 256); 0 -> 64 */
   int32_t precision;    /* 0: FP32 series only; 1: also an int8 copy of every
                            canonical series with its scale and quantisation
-                           error norm, used by the refinement filter            */
+                           error norm, and int8 codes of its selected Fourier
+                           values (the refinement filters); 2: as 1, plus an
+                           FP16 copy of every canonical series, which the
+                           dense tensor-core contraction then reads (FP16
+                           operands instead of TF32).  When n % 8 != 0 the
+                           FP16 rows could not be TMA-addressed, so no FP16
+                           copy is made and 2 acts as 1 (TF32 operands)     */
   /* Optional user-supplied summarisation (host pointers), replacing Alg. 1:
      user_sel: value ids in the candidate order (k ascending, real before
      imaginary, Nyquist imaginary part excluded), word values first;

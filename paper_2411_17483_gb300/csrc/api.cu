@@ -101,10 +101,10 @@ static int num_candidates_host(int n, int pool) {
 void destroy_index(Index* ix) {
   if (!ix) return;
   void* ptrs[] = {ix->sel, ix->sel_k, ix->sel_part, ix->var, ix->basis, ix->beta, ix->edge, ix->ch, ix->ch16,
-                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->VC, ix->vsr, ix->vw, ix->xn, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
+                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->VC, ix->vsr, ix->vw, ix->xn, ix->Zh, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  DevBuf* bufs[] = {&ix->qs.zq, &ix->qs.qv, &ix->qs.qn, &ix->qs.llb, &ix->qs.thr, &ix->qs.list_d, &ix->qs.list_p,
+  DevBuf* bufs[] = {&ix->qs.zq, &ix->qs.qv, &ix->qs.qn, &ix->qs.zqh, &ix->qs.llb, &ix->qs.thr, &ix->qs.list_d, &ix->qs.list_p,
                     &ix->qs.list_n, &ix->qs.leaf_cnt, &ix->qs.leaf_off, &ix->qs.leaf_q, &ix->qs.leaf_cursor,
                     &ix->qs.unit_off, &ix->qs.units, &ix->qs.cand_p, &ix->qs.cand_lb, &ix->qs.cand_n,
                     &ix->qs.qflag, &ix->qs.qslot, &ix->qs.qsel, &ix->qs.chunk_d, &ix->qs.chunk_p, &ix->qs.chunk_n, &ix->qs.pool_q, &ix->qs.pool_p, &ix->qs.pool_lb,
@@ -150,7 +150,7 @@ sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, in
   if (o.sample_ratio < 0.f || o.sample_ratio > 1.f) return bad("sample_ratio must lie in [0, 1]");
   if (o.binning < 0 || o.binning > 1) return bad("binning must be 0 or 1");
   if (o.select < 0 || o.select > 1) return bad("select must be 0 or 1");
-  if (o.precision < 0 || o.precision > 1) return bad("precision must be 0 or 1");
+  if (o.precision < 0 || o.precision > 2) return bad("precision must be 0, 1 or 2");
   if (o.leaf_tiles < 0 || o.leaf_tiles > 256) return bad("leaf_tiles must lie in [0, 256]");
   if (o.user_sel) {
     if (o.user_nsel < l || o.user_nsel > 2 * l) return bad("user_nsel must lie in [l, 2l]");

@@ -541,6 +541,12 @@ __global__ void k_quantv(const float* __restrict__ Z, int64_t N, int n, const fl
   vsr[row] = make_float2(sc, __double2float_ru(sqrt(e2) * (1.0 + 1e-6) + (double)dmargin + 1e-30));
 }
 
+// FP16 copy (round to nearest) of count fp32 values, 4 per thread.
+__global__ void k_to_half(const float* __restrict__ src, int64_t count, __half* __restrict__ dst) {
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  for (int64_t i = i0; i < i0 + 4 && i < count; ++i) dst[i] = __float2half_rn(src[i]);
+}
+
 // Symbol envelope (per word value min and max symbol) of each tile of 256
 // consecutive key-sorted series, using byte-wise SIMD min / max.
 template <int LW>
@@ -824,7 +830,7 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
   }
 
   // ---- int8 copy for the refinement filter (optional)
-  if (o.precision == 1) {
+  if (o.precision >= 1) {
     TRY(dalloc(&ix->Z8, N * n, acct));
     TRY(dalloc(&ix->s8, N, acct));
     TRY(dalloc(&ix->e8, N, acct));
@@ -849,6 +855,14 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
       k_quantv<64><<<(unsigned)ceil_div(N, ROWS), ROWS, vsmem, st>>>(ix->Z, N, n, ix->basis, ix->vw, dmargin,
                                                                      ix->VC, ix->vsr);
     }
+    SOFA_CUDA(cudaGetLastError());
+  }
+
+  // ---- FP16 copy of the canonical series (dense path with FP16 operands);
+  // its rows are TMA-addressed, so their stride must be a multiple of 16 bytes
+  if (o.precision == 2 && n % 8 == 0) {
+    TRY(dalloc(&ix->Zh, N * n, acct));
+    k_to_half<<<(unsigned)ceil_div(N * n, 1024), 256, 0, st>>>(ix->Z, N * n, ix->Zh);
     SOFA_CUDA(cudaGetLastError());
   }
 

@@ -29,7 +29,7 @@ namespace sofa {
 
 constexpr int DM = 128;                  // queries per CTA: MMA M, TMEM lanes
 constexpr int DN = 256;                  // series per tile: MMA N, TMEM columns
-constexpr int DK = 32;                   // fp32 values per k-block: one 128-byte swizzled row
+constexpr int DK = 32;                   // fp32 values per k-block: one 128-byte swizzled row (64 for fp16)
 constexpr int DSTAGES = 4;               // TMA pipeline depth
 constexpr int A_BYTES = DM * DK * 4;     // 16 KB
 constexpr int B_BYTES = DN * DK * 4;     // 32 KB
@@ -38,11 +38,14 @@ constexpr int DENSE_SMEM = DSTAGES * STAGE_BYTES + 1024;  // + alignment slack
 constexpr int DKMAX = 16;                // largest k of the dense path
 constexpr unsigned long long WAIT_NS = 2000000000ull;     // bounded waits: 2 s
 
-// Instruction descriptor of tcgen05.mma kind::tf32: D fp32 (bits 4-5 = 1),
-// A and B tf32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t DENSE_IDESC =
-    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(DN >> 3) << 17) | ((uint32_t)(DM >> 4) << 24);
+// Instruction descriptor of tcgen05.mma kind::tf32 / kind::f16: D fp32
+// (bits 4-5 = 1), A and B tf32 (bits 7-9, 10-12 = 2) or f16 (= 0), both
+// K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+template <bool F16>
+__host__ __device__ constexpr uint32_t dense_idesc() {
+  return (1u << 4) | ((F16 ? 0u : 2u) << 7) | ((F16 ? 0u : 2u) << 10) | ((uint32_t)(DN >> 3) << 17) |
+         ((uint32_t)(DM >> 4) << 24);
+}
 
 struct DenseParams {
   int64_t N;           // series
@@ -112,12 +115,21 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(DENSE_IDESC), "r"(accumulate));
+// One MMA of K = 32 bytes of each operand row (8 tf32 or 16 f16 values).
+template <bool F16>
+__device__ __forceinline__ void mma_dense(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  if constexpr (F16)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(dense_idesc<true>()), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(dense_idesc<false>()), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -204,7 +216,7 @@ constexpr int DWARPS = 6;
 constexpr int DTHREADS = 32 * DWARPS;
 constexpr int DACC = 2;
 
-template <int KD>
+template <int KD, bool F16>
 __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ CUtensorMap tmQ,
                                                        const __grid_constant__ CUtensorMap tmX, DenseParams D,
                                                        const float* __restrict__ qn, const float* __restrict__ xn,
@@ -229,7 +241,8 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
   const uint32_t raw = smem_u32(dsm_raw);
   uint8_t* stages = dsm_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte swizzle atoms
   const int q0 = blockIdx.x * DM;
-  const int kblocks = (D.n + DK - 1) / DK;
+  constexpr int DKE = F16 ? 2 * DK : DK;  // values per k-block (one 128-byte row)
+  const int kblocks = (D.n + DKE - 1) / DKE;
   const int64_t ntiles = t_end - t_begin;
   const int64_t total = ntiles * kblocks;
   volatile int* vfail = &s_fail;
@@ -272,8 +285,8 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
         const int kb = (int)(idx % kblocks);
         uint8_t* a = stages + s * STAGE_BYTES;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_2d(a, &tmQ, kb * DK, q0, &full[s]);
-        tma_load_2d(a + A_BYTES, &tmX, kb * DK, (int)(tile * DN), &full[s]);
+        tma_load_2d(a, &tmQ, kb * DKE, q0, &full[s]);
+        tma_load_2d(a + A_BYTES, &tmX, kb * DKE, (int)(tile * DN), &full[s]);
       }
     }
   } else if (warp == 1) {
@@ -298,8 +311,8 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
           const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
           const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < DK / 8; ++kk)  // K = 8 tf32 values (32 bytes) per MMA
-            mma_tf32(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per MMA: 8 tf32 or 16 f16 values
+            mma_dense<F16>(dcol, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (kb | kk) != 0 ? 1u : 0u);
           mma_commit(&empty[s]);
         }
         if (!ok) {
@@ -418,40 +431,60 @@ static EncodeTiled encode_fn() {
   return fn;
 }
 
-// 2-d map of a row-major fp32 matrix (rows x n), boxes of DK x box_rows,
-// 128-byte swizzle; elements outside the matrix read as zero.
-static int make_map(CUtensorMap* m, const float* base, int64_t rows, int n, int box_rows) {
+// 2-d map of a row-major matrix (rows x n) of fp32 or fp16 values, boxes of
+// one 128-byte row (32 fp32 or 64 fp16 values) x box_rows, 128-byte swizzle;
+// elements outside the matrix read as zero.
+static int make_map(CUtensorMap* m, const void* base, int64_t rows, int n, int box_rows, bool f16) {
   EncodeTiled fn = encode_fn();
   if (!fn) return fail(SOFA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const size_t es_bytes = f16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)DK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)n * es_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es_bytes), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(SOFA_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return 0;
 }
 
+// FP16 operands when the index holds the FP16 copy of its series.
+static bool dense_f16(const Index* ix) { return ix->Zh != nullptr; }
+
 bool dense_supported(const Index* ix, int k) {
-  return ix->xn && ix->n % 4 == 0 && k <= DKMAX && ix->N < ((int64_t)1 << 31) - 2 * DN && encode_fn() != nullptr;
+  // row strides must be multiples of 16 bytes
+  return ix->xn && ix->n % (dense_f16(ix) ? 8 : 4) == 0 && k <= DKMAX && ix->N < ((int64_t)1 << 31) - 2 * DN &&
+         encode_fn() != nullptr;
 }
 
-// |d~^2 - d^2| for canonical series (||x||^2 <= n (1 + 4u)) with TF32
-// operands (relative error < 2^-10 each, truncated or rounded) and an FP32
-// accumulation whose additions may lose up to 2 bits against IEEE:
-//   |q.x~ - q.x| <= n' (2^-9 + 2^-20 + n 2^-22 (1 + 2^-9)),  n' = n (1 + 4u),
-// twice that for -2 q.x, plus the fp32 roundings of ||x||^2 and ||q||^2 and
-// of the two fp32 operations forming d~^2 (8.2 u n'); 1 % on top.
-static float dense_margin(int n) {
+// |d~^2 - d^2| for canonical series (||x||^2 <= n (1 + 4u)), n' = n (1 + 4u):
+// * TF32 operands: relative error < 2^-10 each (truncated or rounded), so
+//   |q.x~ - q.x| <= n' (2^-9 + 2^-20 + n 2^-22 (1 + 2^-9));
+// * FP16 operands (round to nearest): relative error <= 2^-11 each plus at
+//   most 2^-25 absolute for subnormals, so
+//   |q.x~ - q.x| <= n' (2^-10 + 2^-22 + 2^-24 + n 2^-22 (1 + 2^-10));
+// where n 2^-22 covers an FP32 accumulation whose additions may lose up to 2
+// bits against IEEE.  Twice that for -2 q.x, plus the fp32 roundings of
+// ||x||^2 and ||q||^2 and of the two fp32 operations forming d~^2 (8.2 u n');
+// 1 % on top.
+static float dense_margin(int n, bool f16) {
   const double u = std::ldexp(1.0, -24);
   const double np = n * (1.0 + 4 * u);
-  const double dot = np * (std::ldexp(1.0, -9) + std::ldexp(1.0, -20) + n * std::ldexp(1.0, -22) * (1.0 + std::ldexp(1.0, -9)));
+  const double dot =
+      f16 ? np * (std::ldexp(1.0, -10) + std::ldexp(1.0, -22) + std::ldexp(1.0, -24) +
+                  n * std::ldexp(1.0, -22) * (1.0 + std::ldexp(1.0, -10)))
+          : np * (std::ldexp(1.0, -9) + std::ldexp(1.0, -20) + n * std::ldexp(1.0, -22) * (1.0 + std::ldexp(1.0, -9)));
   return std::nextafter((float)((2.0 * dot + 8.2 * u * np) * 1.01), INFINITY);
 }
 
-float dense_margin_of(int n) { return dense_margin(n); }
+float dense_margin_of(const Index* ix) { return dense_margin(ix->n, dense_f16(ix)); }
+
+// FP16 copy (round to nearest) of the batch's canonical queries.
+__global__ void k_queries_half(const float* __restrict__ zq, int64_t count, __half* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = __float2half_rn(zq[i]);
+}
 
 // ||q||^2 of each canonical query (FP64 sum rounded to fp32).
 __global__ void k_qnorms(const float* __restrict__ zq, int Q, int n, float* __restrict__ out) {
@@ -473,10 +506,31 @@ int launch_row_norms(Index* ix, cudaStream_t st) {
   return 0;
 }
 
+template <int KD, bool F16>
+static int launch_dense_t(const CUtensorMap& tq, const CUtensorMap& tx, const DenseParams& D, dim3 grid,
+                          const float* qn, const Index* ix, const DenseArgs& A, cudaStream_t st) {
+  SOFA_CUDA(cudaFuncSetAttribute(k_dense<KD, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, DENSE_SMEM));
+  k_dense<KD, F16><<<grid, DTHREADS, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p,
+                                                      A.cand_lb, A.cand_n, A.pool_n, A.pool_q, A.pool_p, A.pool_lb,
+                                                      A.qpool_cnt, A.dump, A.counters, A.status);
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
 int launch_dense(Index* ix, const DenseArgs& A, cudaStream_t st) {
+  const bool f16 = dense_f16(ix);
   CUtensorMap tq, tx;
-  TRYD(make_map(&tq, A.zq, A.Q, ix->n, DM));
-  TRYD(make_map(&tx, ix->Z, ix->N, ix->n, DN));
+  if (f16) {
+    TRYD(ix->qs.zqh.ensure((size_t)A.Q * ix->n * sizeof(__half)));
+    const int64_t cnt = (int64_t)A.Q * ix->n;
+    k_queries_half<<<(unsigned)ceil_div(cnt, 256), 256, 0, st>>>(A.zq, cnt, ix->qs.zqh.as<__half>());
+    SOFA_CUDA(cudaGetLastError());
+    TRYD(make_map(&tq, ix->qs.zqh.p, A.Q, ix->n, DM, true));
+    TRYD(make_map(&tx, ix->Zh, ix->N, ix->n, DN, true));
+  } else {
+    TRYD(make_map(&tq, A.zq, A.Q, ix->n, DM, false));
+    TRYD(make_map(&tx, ix->Z, ix->N, ix->n, DN, false));
+  }
   TRYD(A.qn_buf->ensure((size_t)A.Q * sizeof(float)));
   float* qn = A.qn_buf->as<float>();
   k_qnorms<<<(unsigned)ceil_div((int64_t)A.Q * 32, 256), 256, 0, st>>>(A.zq, A.Q, ix->n, qn);
@@ -497,22 +551,13 @@ int launch_dense(Index* ix, const DenseArgs& A, cudaStream_t st) {
   D.cap = A.cap;
   D.pool_cap = A.pool_cap;
   D.tiles_per_cta = ceil_div(n_tiles, chunks);
-  D.margin = dense_margin(ix->n);
+  D.margin = dense_margin(ix->n, f16);
   D.f_half = std::nextafter(A.f_prune * 0.5f, INFINITY);
   const dim3 grid((unsigned)gx, (unsigned)ceil_div(n_tiles, D.tiles_per_cta));
-  if (A.k == 1) {
-    SOFA_CUDA(cudaFuncSetAttribute(k_dense<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, DENSE_SMEM));
-    k_dense<1><<<grid, DTHREADS, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p, A.cand_lb,
-                                             A.cand_n, A.pool_n, A.pool_q, A.pool_p, A.pool_lb, A.qpool_cnt, A.dump,
-                                             A.counters, A.status);
-  } else {
-    SOFA_CUDA(cudaFuncSetAttribute(k_dense<DKMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, DENSE_SMEM));
-    k_dense<DKMAX><<<grid, DTHREADS, DENSE_SMEM, st>>>(tq, tx, D, qn, ix->xn, A.qsel, A.qslot, A.thr, A.cand_p,
-                                                 A.cand_lb, A.cand_n, A.pool_n, A.pool_q, A.pool_p, A.pool_lb,
-                                                 A.qpool_cnt, A.dump, A.counters, A.status);
-  }
-  SOFA_CUDA(cudaGetLastError());
-  return 0;
+  if (A.k == 1) return f16 ? launch_dense_t<1, true>(tq, tx, D, grid, qn, ix, A, st)
+                           : launch_dense_t<1, false>(tq, tx, D, grid, qn, ix, A, st);
+  return f16 ? launch_dense_t<DKMAX, true>(tq, tx, D, grid, qn, ix, A, st)
+             : launch_dense_t<DKMAX, false>(tq, tx, D, grid, qn, ix, A, st);
 }
 
 }  // namespace sofa
@@ -524,7 +569,8 @@ extern "C" int sofa_dense_sqdist(sofa_handle h, const float* queries, int64_t Q,
   if (!h || !queries || !out) return fail(SOFA_ERR_INVALID_ARG, "null argument");
   if (Q < 1 || Q > 8192) return fail(SOFA_ERR_INVALID_ARG, "Q must lie in [1, 8192]");
   if (Q * h->N > ((int64_t)1 << 31)) return fail(SOFA_ERR_INVALID_ARG, "Q * N must be <= 2^31");
-  if (!dense_supported(h, 1)) return fail(SOFA_ERR_INVALID_ARG, "the dense contraction needs n % 4 == 0");
+  if (!dense_supported(h, 1))
+    return fail(SOFA_ERR_INVALID_ARG, "the dense contraction needs n % 4 == 0 (n % 8 == 0 with FP16 operands)");
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, queries) != cudaSuccess || a.type != cudaMemoryTypeDevice ||
       cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
@@ -552,6 +598,6 @@ extern "C" int sofa_dense_sqdist(sofa_handle h, const float* queries, int64_t Q,
   A.status = reinterpret_cast<int*>(s.counters.as<unsigned long long>() + 8);
   A.qn_buf = &s.qn;
   TRYD(launch_dense(h, A, st));
-  if (margin) *margin = dense_margin(h->n);
+  if (margin) *margin = dense_margin(h->n, dense_f16(h));
   return 0;
 }

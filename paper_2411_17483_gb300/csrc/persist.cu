@@ -2,7 +2,7 @@
 // trained proposal network) to one file; sofa_load recreates the handle on the
 // current device from it, without the raw data or any of the build's work.
 //
-// File: the 8-byte magic "SOFAIDX1", a fixed header of 64-bit fields, then one
+// File: the 8-byte magic "SOFAIDX2", a fixed header of 64-bit fields, then one
 // section per array -- a 64-bit byte count followed by the bytes, in a fixed
 // order (optional arrays have count 0 when absent) -- then the proposal
 // network.  Arrays move between device and file through a pinned staging
@@ -20,7 +20,7 @@ void set_error(const std::string& msg);
 
 namespace {
 
-constexpr char MAGIC[8] = {'S', 'O', 'F', 'A', 'I', 'D', 'X', '1'};
+constexpr char MAGIC[8] = {'S', 'O', 'F', 'A', 'I', 'D', 'X', '2'};
 constexpr size_t PIECE = (size_t)64 << 20;
 
 struct Header {
@@ -79,7 +79,7 @@ int read_array(FILE* f, Staging& sg, T** dev, size_t bytes, bool optional, int64
 }
 
 struct Sizes {
-  size_t nsel_i, nsel_d, basis, beta, tab, words, Z, N4, N8, keyorder, tenv, lenv, Z8, VC, vsr, vw;
+  size_t nsel_i, nsel_d, basis, beta, tab, words, Z, N4, N8, keyorder, tenv, lenv, Z8, VC, vsr, vw, Zh;
 };
 
 Sizes sizes_of(const Index* ix) {
@@ -101,6 +101,7 @@ Sizes sizes_of(const Index* ix) {
   z.VC = N * ix->NB;
   z.vsr = N * sizeof(float2);
   z.vw = (size_t)ix->NB * sizeof(float);
+  z.Zh = N * ix->n * sizeof(__half);
   return z;
 }
 
@@ -138,7 +139,7 @@ int save_index(const Index* ix, FILE* f) {
                 {ix->ch16, z.tab / 2},  {ix->words, z.words},  {ix->Z, z.Z},              {ix->perm, z.N4},
                 {ix->keys, z.N8},       {ix->keyorder, z.keyorder}, {ix->tenv, z.tenv},   {ix->lenv, z.lenv},
                 {ix->xn, z.N4},         {ix->Z8, z.Z8},        {ix->s8, z.N4},            {ix->e8, z.N4},
-                {ix->VC, z.VC},         {ix->vsr, z.vsr},      {ix->vw, z.vw}};
+                {ix->VC, z.VC},         {ix->vsr, z.vsr},      {ix->vw, z.vw},            {ix->Zh, z.Zh}};
   for (const auto& a : arrays)
     if (int rc = write_array(f, sg, a.p, a.b)) return rc;
   if (ix->mlp)
@@ -202,6 +203,7 @@ int load_index(Index* ix, FILE* f, cudaStream_t st) {
   rc = rc ? rc : read_array(f, sg, &ix->VC, z.VC, true, acct);
   rc = rc ? rc : read_array(f, sg, &ix->vsr, z.vsr, true, acct);
   rc = rc ? rc : read_array(f, sg, &ix->vw, z.vw, true, acct);
+  rc = rc ? rc : read_array(f, sg, &ix->Zh, z.Zh, true, acct);
   if (rc) return rc;
   if (!ix->Z8 != !ix->VC) return fail(SOFA_ERR_INVALID_ARG, "index file holds only part of the precision copies");
   if (h.has_mlp)

@@ -48,6 +48,7 @@ struct QueryScratch {
   DevBuf zq;        // Q x n canonical query series
   DevBuf qv;        // Q x NB projected values
   DevBuf qn;        // Q squared norms of the canonical queries (dense path)
+  DevBuf zqh;       // Q x n FP16 canonical queries (dense path with FP16 operands)
   DevBuf llb;       // Q x L leaf lower bounds (half units)
   DevBuf thr;       // Q prune thresholds (half units, fp32)
   DevBuf list_d;    // Q x KCAP kept squared distances (fp32)
@@ -126,6 +127,7 @@ struct Index {
   float2* vsr = nullptr;       // [N] (scale, margin) of the value codes
   float* vw = nullptr;         // [NB] Eq. (1) weight of each basis column (0 for unused columns)
   float* xn = nullptr;         // [N] ||x||^2 of each canonical series (dense path)
+  __half* Zh = nullptr;        // [N][n] FP16 copy of the canonical series (dense path, precision 2)
   uint32_t* perm = nullptr;    // [N] sorted position -> original row
   uint64_t* keys = nullptr;    // [N] sorted layout keys
   uint8_t* keyorder = nullptr; // [64] key bit order (dim << 3 | bit)
@@ -208,7 +210,7 @@ struct DenseArgs {
 bool dense_supported(const Index* ix, int k);
 int launch_dense(Index* ix, const DenseArgs& a, cudaStream_t st);
 int launch_row_norms(Index* ix, cudaStream_t st);
-float dense_margin_of(int n);
+float dense_margin_of(const Index* ix);
 
 void destroy_index(Index* ix);
 int mlp_save(const Index* ix, void* file);   // FILE*; 0 or an error code

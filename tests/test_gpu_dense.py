@@ -26,17 +26,32 @@ def oracle_knn(x, q, k):
     return orc.knn(z, zq, k)
 
 
+def tf32_margin(n):
+    """The margin the library states for the dense contraction with TF32
+    operands; a smaller returned margin shows that FP16 operands were used."""
+    u = 2.0 ** -24
+    n1 = n * (1 + 4 * u)
+    dot = n1 * (2.0 ** -9 + 2.0 ** -20 + n * 2.0 ** -22 * (1 + 2.0 ** -9))
+    return (2 * dot + 8.2 * u * n1) * 1.01
+
+
 # N not a multiple of the 256-series tile, Q not a multiple of the 128-query
 # block, n not a multiple of the 32-value k-block (zero-filled tails)
-@pytest.mark.parametrize("N,n,Q,gen", [(3000, 256, 200, "rw"), (1000, 100, 130, "sin"), (700, 1024, 64, "sin"),
-                                       (257, 32, 1, "rw")])
-def test_dense_sqdist_within_margin(sofa, N, n, Q, gen):
+@pytest.mark.parametrize("N,n,Q,gen,precision", [(3000, 256, 200, "rw", 0), (1000, 100, 130, "sin", 0),
+                                                 (700, 1024, 64, "sin", 0), (257, 32, 1, "rw", 0),
+                                                 (3000, 256, 200, "rw", 2), (700, 1024, 64, "sin", 2),
+                                                 (257, 32, 1, "rw", 2), (1500, 96, 129, "sin", 2),
+                                                 (900, 100, 70, "sin", 2)])     # n % 8 != 0: TF32
+def test_dense_sqdist_within_margin(sofa, N, n, Q, gen, precision):
+    """TF32 operands (precision 0) or FP16 operands (precision 2)."""
     x = datagen.random_walks(N, n, seed=N, device=DEV) if gen == "rw" else \
         datagen.sinusoid_mix(N, n, seed=N, device=DEV)
     q = datagen.random_walks(Q, n, seed=N + 1, device=DEV) if gen == "rw" else \
         datagen.sinusoid_mix(Q, n, seed=N + 1, device=DEV)
-    ix = sofa.Index(x, 8 if n <= 64 else 16, 256)
+    ix = sofa.Index(x, 8 if n <= 64 else 16, 256, precision=precision)
     out, margin = sofa.dense_sqdist(ix, q)
+    f16 = precision == 2 and n % 8 == 0
+    assert (margin < 0.9 * tf32_margin(n)) == f16         # the FP16 bound is the tighter one
     torch.cuda.synchronize()
     perm = ix.perm().numpy().astype(np.int64)         # sorted position -> original row
     z, _, _ = orc.znorm(x.cpu().numpy())
@@ -52,10 +67,11 @@ def test_dense_sqdist_within_margin(sofa, N, n, Q, gen):
     ix.close()
 
 
+@pytest.mark.parametrize("precision", [0, 2])
 @pytest.mark.parametrize("N,n,l,k,Q,gen", [(20000, 128, 16, 1, 64, "rw"), (20000, 256, 16, 5, 48, "mixed"),
                                            (9000, 96, 16, 16, 16, "sin"), (12000, 1024, 32, 1, 40, "sin"),
                                            (100, 16, 6, 4, 3, "rw")])
-def test_dense_knn_matches_oracle(sofa, N, n, l, k, Q, gen):
+def test_dense_knn_matches_oracle(sofa, N, n, l, k, Q, gen, precision):
     if gen == "rw":
         x = datagen.random_walks(N, n, seed=N + n, device=DEV)
     elif gen == "mixed":
@@ -63,7 +79,7 @@ def test_dense_knn_matches_oracle(sofa, N, n, l, k, Q, gen):
     else:
         x = datagen.sinusoid_mix(N, n, seed=N + n, device=DEV)
     q = datagen.half_perturbed_queries(x, Q, seed=5)
-    ix = sofa.Index(x, l, 256)
+    ix = sofa.Index(x, l, 256, precision=precision)
     ix.set_tuning(dense=2)
     ix.stats(reset=True)
     gi, gd = ix.query(q, k)

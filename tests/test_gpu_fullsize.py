@@ -143,7 +143,7 @@ def test_sinusoid10M_n1024_l32(sofa):
     N, n, Q = 10_000_000, 1024, 1000
     need_bytes(100e9)
     x = datagen.sinusoid_mix(N, n, seed=0, device=DEV)
-    ix = sofa.Index(x, 32, 256, sample_ratio=0.1)
+    ix = sofa.Index(x, 32, 256, sample_ratio=0.1, precision=2)   # FP16 operands for the dense form
     del x
     torch.cuda.empty_cache()
     q = datagen.sinusoid_mix(Q, n, seed=1, device=DEV)

@@ -351,7 +351,7 @@ def test_save_load_roundtrip(sofa, tmp_path):
     N, n = 30000, 128
     x = datagen.random_walks(N, n, seed=91, device=DEV)
     q = datagen.half_perturbed_queries(x, 40, seed=92)
-    ix = sofa.Index(x, 16, 256, precision=1)
+    ix = sofa.Index(x, 16, 256, precision=2)      # every optional copy, FP16 included
     ix.train_proposal(n_train=8192, n_classes=64, epochs=1, batch=2048, seed=2, top_m=4)
     path = str(tmp_path / "index.sofa")
     ix.save(path)
