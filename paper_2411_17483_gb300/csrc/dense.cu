@@ -140,18 +140,20 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive fp32 columns of this thread's TMEM lane.
+// 32 consecutive fp32 columns of this thread's TMEM lane (load and wait in
+// one statement: no use of the outputs can be scheduled before the wait).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      : "r"(taddr)
+      : "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -231,6 +233,8 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
                                                        int* __restrict__ status) {
   extern __shared__ uint8_t dsm_raw[];
   __shared__ __align__(8) uint64_t full[DSTAGES], empty[DSTAGES], tfull[DACC], tempty[DACC];
+  __shared__ __align__(16) float s_x[4][DN];  // per epilogue warp: ||x||^2 of the tile's series
+  __shared__ float s_v[4][32][32];             // per epilogue warp: 32 accumulator columns x 32 lanes
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -323,9 +327,14 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
       }
     }
   } else {
-    // epilogue
+    // epilogue.  Per 32 columns: d~^2 = ||q||^2 + ||x||^2 - 2 q.x of each
+    // (one FADD, one FFMA) and their minimum; the lower bound is monotone in
+    // d~^2, so the columns are visited one by one only when the minimum
+    // passes the threshold (rare once the threshold is tight).
+    float* xs = s_x[warp - 2];      // this warp's copy of the tile's ||x||^2 (+inf past N)
+    float* vs = &s_v[warp - 2][0][0];  // [column][lane] spill of the accumulator for the slow path
     const int qs = qa ? (qslot ? qslot[q] : q) : 0;
-    const float qnr = qa ? qn[q] : 0.f;
+    const float qnr = qa ? qn[q] : INFINITY;  // inactive lanes: every d~^2 is +inf
     volatile float* vthr = thr;
     float T = qa ? vthr[q] : -1.f;  // emission threshold, half units
     float top[KD];
@@ -333,8 +342,15 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
     for (int i = 0; i < KD; ++i) top[i] = INFINITY;
     unsigned long long emitted = 0;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    float xr[DN / 32];  // ||x||^2 of the next tile, prefetched a tile ahead
+#pragma unroll
+    for (int j = 0; j < DN / 32; ++j) {
+      const int64_t sx = t_begin * DN + lane + 32 * j;
+      xr[j] = sx < D.N ? __ldg(xn + sx) : INFINITY;
+    }
     for (int64_t ti = 0; ti < ntiles; ++ti) {
       const int acc = (int)(ti & 1);
+      const float Tg = qa ? vthr[q] : -1.f;  // in flight during the wait below
       // warp-uniform: the TMEM loads below are warp-collective
       if (!__all_sync(0xFFFFFFFFu, mbar_wait(&tfull[acc], (uint32_t)((ti / DACC) & 1)))) {
         *vfail = 1;
@@ -342,48 +358,82 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
       }
       tc_fence_after();
       const int64_t s0 = (t_begin + ti) * DN;
-      if (qa) T = fminf(T, vthr[q]);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < DN / 32; ++j) xs[lane + 32 * j] = xr[j];
+      __syncwarp();
+      if (ti + 1 < ntiles) {
+#pragma unroll
+        for (int j = 0; j < DN / 32; ++j) {
+          const int64_t sx = s0 + DN + lane + 32 * j;
+          xr[j] = sx < D.N ? __ldg(xn + sx) : INFINITY;
+        }
+      }
+      if (qa) T = fminf(T, Tg);
       const float T_in = T;
 #pragma unroll 1
       for (int c0 = 0; c0 < DN; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + lane_base + (uint32_t)(acc * DN + c0), v);  // warp-collective
-        const float xv = s0 + c0 + lane < D.N ? __ldg(xn + s0 + c0 + lane) : 0.f;
+        const float4* x4 = reinterpret_cast<const float4*>(xs + c0);
+        if (dump) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float xi = __shfl_sync(0xFFFFFFFFu, xv, i);  // every lane takes part
-          const int64_t sidx = s0 + c0 + i;
-          if (!qa || sidx >= D.N) continue;
-          const float d2 = fmaf(-2.f, v[i], qnr + xi);
-          if (dump) {
-            dump[(int64_t)q * D.N + sidx] = d2;
-            continue;
-          }
-          const float lb = __fmul_rd(__fsub_rd(d2, D.margin), 0.5f);  // lower bound, half units
-          if (lb > T) continue;
-          ++emitted;
-          const int slot = atomicAdd(cand_n + qs, 1);
-          if (slot < D.cap) {
-            cand_p[(int64_t)qs * D.cap + slot] = (uint32_t)sidx;
-            cand_lb[(int64_t)qs * D.cap + slot] = fmaxf(lb, 0.f);
-          } else {
-            // the pool counter grows only while the pool has room (it cannot wrap)
-            const int pb = *reinterpret_cast<volatile int*>(pool_n) < D.pool_cap ? atomicAdd(pool_n, 1)
-                                                                                  : (int)D.pool_cap;
-            if (pb < D.pool_cap) {
-              pool_q[pb] = qs;
-              pool_p[pb] = (uint32_t)sidx;
-              pool_lb[pb] = fmaxf(lb, 0.f);
-              atomicAdd(qpool_cnt + qs, 1);
+          for (int i = 0; i < 32; i += 4) {
+            const float4 xv = x4[i >> 2];
+            const float xq[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int64_t sidx = s0 + c0 + i + e;
+              if (qa && sidx < D.N) dump[(int64_t)q * D.N + sidx] = fmaf(-2.f, v[i + e], qnr + xq[e]);
             }
           }
-          if (d2 < top[KD - 1]) {
-            topk_insert<KD>(top, d2);
-            const float kth = topk_kth<KD>(top, D.k);
-            // k series with d^2 <= d~^2 + M each: a valid threshold
-            if (kth < INFINITY) T = fminf(T, __fmul_ru(__fadd_ru(kth, D.margin), D.f_half));
+          continue;
+        }
+        float m = INFINITY;
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) {
+          const float4 xv = x4[i >> 2];
+          m = fminf(m, fminf(fminf(fmaf(-2.f, v[i], qnr + xv.x), fmaf(-2.f, v[i + 1], qnr + xv.y)),
+                             fminf(fmaf(-2.f, v[i + 2], qnr + xv.z), fmaf(-2.f, v[i + 3], qnr + xv.w))));
+        }
+        const bool pass = __fmul_rd(__fsub_rd(m, D.margin), 0.5f) <= T;
+        if (!__any_sync(0xFFFFFFFFu, pass)) continue;
+        // slow path: the accumulator columns through shared memory, one by one
+#pragma unroll
+        for (int i = 0; i < 32; ++i) vs[i * 32 + lane] = v[i];
+        __syncwarp();
+        if (pass) {
+#pragma unroll 1
+          for (int i = 0; i < 32; ++i) {
+            const float d2 = fmaf(-2.f, vs[i * 32 + lane], qnr + xs[c0 + i]);  // the value the minimum took
+            const float lb = __fmul_rd(__fsub_rd(d2, D.margin), 0.5f);       // lower bound, half units
+            if (lb > T) continue;
+            const int64_t sidx = s0 + c0 + i;  // < N: columns past N carry +inf
+            ++emitted;
+            const int slot = atomicAdd(cand_n + qs, 1);
+            if (slot < D.cap) {
+              cand_p[(int64_t)qs * D.cap + slot] = (uint32_t)sidx;
+              cand_lb[(int64_t)qs * D.cap + slot] = fmaxf(lb, 0.f);
+            } else {
+              // the pool counter grows only while the pool has room (it cannot wrap)
+              const int pb = *reinterpret_cast<volatile int*>(pool_n) < D.pool_cap ? atomicAdd(pool_n, 1)
+                                                                                    : (int)D.pool_cap;
+              if (pb < D.pool_cap) {
+                pool_q[pb] = qs;
+                pool_p[pb] = (uint32_t)sidx;
+                pool_lb[pb] = fmaxf(lb, 0.f);
+                atomicAdd(qpool_cnt + qs, 1);
+              }
+            }
+            if (d2 < top[KD - 1]) {
+              topk_insert<KD>(top, d2);
+              const float kth = topk_kth<KD>(top, D.k);
+              // k series with d^2 <= d~^2 + M each: a valid threshold
+              if (kth < INFINITY) T = fminf(T, __fmul_ru(__fadd_ru(kth, D.margin), D.f_half));
+            }
           }
         }
+        __syncwarp();
       }
       tc_fence_before();
       mbar_arrive(&tempty[acc]);  // the accumulator is free for the MMA warp
