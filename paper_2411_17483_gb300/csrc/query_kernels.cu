@@ -620,6 +620,7 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
       }
       const int64_t p = (t0 + t) * TILE + tid;
       const bool valid = p < P.N;
+      [[maybe_unused]] const float acc0 = valid ? 0.f : __int_as_float(0x7f800000);  // +inf: never live
       float c[H16 ? 1 : LW], h[H16 ? 1 : LW];
       __half2 c2[H16 ? LW / 2 : 1], nh2[H16 ? LW / 2 : 1];
       if constexpr (H16) {
@@ -685,18 +686,20 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
         } else {
           const float4* qg4 = reinterpret_cast<const float4*>(sq[g]);
           const float a = s_a;
-          // u = sat(|q - c| a - h a) (one FADD, one FFMA.SAT), two partial sums
-          // (even / odd values); the warp votes after every 4 of the first 16
-          // values (about 10 of 16 are evaluated on average at 100M x 256),
-          // then after 24 and 32
-          float a0 = 0.f, a1 = 0.f;
+          // u = sat(|q - c| a - h a) (one FADD, one FFMA.SAT), one running sum
+          // s.  Every term is >= 0, so s never decreases and "s <= T" is the
+          // lane's whole liveness (lanes past N start at +inf): the warp votes
+          // on it after every 4 of the first 16 values (about 10 of 16 are
+          // evaluated on average at 100M x 256), then after 24 and 32, and a
+          // warp with no live lane goes straight to the next query.
+          float s = acc0;
           bool warp_dead = false;
 #pragma unroll
           for (int stage = 0; stage < 6; ++stage) {
             const int j0 = stage < 4 ? 4 * stage : 16 + 8 * (stage - 4);
             const int j1 = stage < 4 ? j0 + 4 : j0 + 8;
             if (j0 >= LW) break;
-            if (!__any_sync(0xFFFFFFFFu, live)) {
+            if (stage > 0 && !__any_sync(0xFFFFFFFFu, s <= T)) {
               warp_dead = true;
               break;
             }
@@ -707,15 +710,15 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
               const float u1 = __saturatef(fmaf(fabsf(q4.y - c[j + 1]), a, -h[j + 1]));
               const float u2 = __saturatef(fmaf(fabsf(q4.z - c[j + 2]), a, -h[j + 2]));
               const float u3 = __saturatef(fmaf(fabsf(q4.w - c[j + 3]), a, -h[j + 3]));
-              a0 = fmaf((NYQ && j == 0) ? 0.5f * u0 : u0, u0, a0);
-              a1 = fmaf(u1, u1, a1);
-              a0 = fmaf(u2, u2, a0);
-              a1 = fmaf(u3, u3, a1);
+              s = fmaf((NYQ && j == 0) ? 0.5f * u0 : u0, u0, s);
+              s = fmaf(u1, u1, s);
+              s = fmaf(u2, u2, s);
+              s = fmaf(u3, u3, s);
             }
-            live = live && (a0 + a1) <= T;
           }
-          acc = __fmul_rd(a0 + a1, s_inva2);  // back to half units, rounded down
           if (warp_dead) continue;  // warp-uniform: no lane left for this query
+          live = s <= T;
+          acc = __fmul_rd(s, s_inva2);  // back to half units, rounded down
         }
         const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
         if (hit) {
