@@ -65,7 +65,7 @@ def parse():
 # 1808-query batch) from one ncu capture of the default workload, chosen mode;
 # summary and command in profiles/k_scan_dram_rw100M_q10k.md.  Reported only
 # while the kernel's source is the one that was captured.
-SCAN_TRAFFIC = {"bytes_per_launch": 6462902656, "source_sha": "1ebb9c5dbaeb52d5",
+SCAN_TRAFFIC = {"bytes_per_launch": 6636247808, "source_sha": "17bd9db7b490eaa9",
                 "workload": (100_000_000, 256, 10_000, 1, 16)}
 
 
