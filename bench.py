@@ -54,9 +54,12 @@ def parse():
                          "the dense tensor-core form")
     ap.add_argument("--no-autotune", action="store_true",
                     help="chosen mode with the default tuning instead of the autotuner's choice")
-    ap.add_argument("--gen", default="rw", choices=["rw", "mixed", "sin"],
+    ap.add_argument("--gen", default="rw", choices=["rw", "mixed", "sin", "multi"],
                     help="rw: random walks (default); mixed: half walks + noisy walks with half perturbed-member "
-                         "queries; sin: 8-sinusoid mixtures (high-frequency stress, bounds prune little)")
+                         "queries; sin: 8-sinusoid mixtures (high-frequency stress, bounds prune little); multi: "
+                         "four random-walk datasets (25M x 128, 25M x 256, 12M x 512, 6M x 1024) in one index set, "
+                         "--Q mixed-length queries with k uniform in {1, 5, 10, 50}, one sofa_query_multi call "
+                         "per step (--N, --n and --k are ignored)")
     return ap.parse_args()
 
 
@@ -90,7 +93,15 @@ def precision_text(a, stats) -> str:
             "fp64 final re-score")
 
 
+MULTI_SETS = [(25_000_000, 128), (25_000_000, 256), (12_000_000, 512), (6_000_000, 1024)]
+MULTI_KS = (1, 5, 10, 50)
+
+
 def workload_name(a):
+    if a.gen == "multi":
+        sets = ", ".join(f"{N // 1_000_000}Mx{n}" for N, n in MULTI_SETS)
+        return (f"random walks in four datasets ({sets}) fp32, {a.Q} fresh random-walk queries, length uniform "
+                f"over the four, exact k-NN with k uniform in {{1, 5, 10, 50}}, l={a.l}, alphabet {a.alphabet}")
     data = {"rw": "random walks", "mixed": "random walks + noisy random walks",
             "sin": "8-sinusoid mixtures + N(0,0.3^2) noise"}[a.gen]
     queries = {"rw": "fresh random-walk queries", "mixed": "queries (half perturbed members, half fresh walks)",
@@ -226,6 +237,28 @@ def run_reference(a, ws, rank):
         return
     from paper_2411_17483_gb300 import datagen
     dev = "cuda:0" if torch.cuda.is_available() else "cpu"
+    if a.gen == "multi":
+        rows_per_set = [datagen.random_walks(min(N, 500_000), n, seed=10 + si, device=dev).cpu().numpy()
+                        for si, (N, n) in enumerate(MULTI_SETS)]
+        packed, qo, _, _, _, _, which = multi_queries(a, 0, dev)
+        per_step = max(4.0, 60.0 / max(1, a.steps + a.warmup))
+        multi_oracle_rate(a, rows_per_set, packed, qo, which, min(per_step, 8.0))   # warm-up
+        rates, secs = [], 0.0
+        for _ in range(a.steps):
+            rate, cores, sample, el = multi_oracle_rate(a, rows_per_set, packed, qo, which, per_step)
+            rates.append(rate)
+            secs += el
+        value = statistics.mean(rates)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / max(1, a.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "oracle": "CPU FP64 brute force (oracle/)"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }), flush=True)
+        return
     rows = min(a.N, 2_000_000)
     xs = make_rows(a, rows, 0, dev).cpu().numpy()
     q = make_queries(a, make_rows(a, rows, 0, dev), 1, dev).cpu().numpy()
@@ -252,6 +285,201 @@ def run_reference(a, ws, rank):
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+# ---------------------------------------------------------------- mixed workload
+def multi_queries(a, rank, dev):
+    """The mixed workload's queries: dataset (hence length) uniform over the
+    four, k uniform over MULTI_KS, each row a fresh random walk of its
+    dataset's length (stream seed 1000 (1 + rank) + dataset).  Returns the
+    packed rows and per-query offsets, lengths, k's and output offsets, and
+    the total output length."""
+    from paper_2411_17483_gb300 import datagen
+    g = torch.Generator().manual_seed(1 + rank)
+    which = torch.randint(0, len(MULTI_SETS), (a.Q,), generator=g)
+    ks = torch.tensor(MULTI_KS, dtype=torch.int32)[torch.randint(0, len(MULTI_KS), (a.Q,), generator=g)]
+    lens = torch.tensor([n for _, n in MULTI_SETS], dtype=torch.int64)[which]
+    rows = [datagen.random_walks(int((which == si).sum()), n, seed=1000 * (1 + rank) + si, device=dev)
+            for si, (_, n) in enumerate(MULTI_SETS)]
+    cursor = [0] * len(MULTI_SETS)
+    parts = []
+    for si in which.tolist():
+        parts.append(rows[si][cursor[si]])
+        cursor[si] += 1
+    packed = torch.cat(parts).contiguous()
+    q_off = torch.cumsum(lens, 0) - lens
+    o_off = torch.cumsum(ks.to(torch.int64), 0) - ks.to(torch.int64)
+    return packed, q_off, lens.to(torch.int32), ks, o_off, int(ks.sum()), which
+
+
+def multi_oracle_rate(a, rows_per_set, packed, qo, which, seconds):
+    """The oracle's brute force on the mixed workload: per dataset, up to
+    50 of its queries over the sample rows_per_set[si] (the dataset's first
+    rows), the rate scaled to the dataset's size; the rates are combined by
+    the query mix (seconds per query = sum of share / rate)."""
+    from oracle import sofa_oracle as orc
+    per_query_s, done_all, el_all, cores = 0.0, 0, 0.0, 1
+    for si, (N, n) in enumerate(MULTI_SETS):
+        zs, _, _ = orc.znorm(rows_per_set[si])
+        sel = (which == si).nonzero().flatten()[:50].tolist()
+        zq, _, _ = orc.znorm(torch.stack([packed[int(qo[i]):int(qo[i]) + n] for i in sel]).cpu().numpy())
+        rate, done, el, cores = cpu_oracle_rate(zs, zq, 10, N, seconds / len(MULTI_SETS))
+        per_query_s += float((which == si).sum()) / which.numel() / rate
+        done_all += done
+        el_all += el
+    rows = rows_per_set[0].shape[0]
+    sample = (f"{done_all} queries brute-forced (FP64, k=10) over the first {rows} series of each dataset in "
+              f"{el_all:.1f} s, each dataset's rate scaled by {rows}/N and combined by the query mix")
+    return 1.0 / per_query_s, cores, sample, el_all
+
+
+def run_sofa_multi(a, ws, rank, local):
+    """Four random-walk indexes answered together by sofa_query_multi: plain
+    FP32 refinement vs the refinement filters (both exact, same answers)."""
+    from paper_2411_17483_gb300 import datagen, sofa
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    hbm_peak, peak_kind = peaks()
+    ixs, cpu_rows, gen_s, build_s = [], [], 0.0, 0.0
+    for si, (N, n) in enumerate(MULTI_SETS):
+        ta = time.perf_counter()
+        x = torch.empty((N, n), dtype=torch.float32, device=dev)
+        datagen.random_walks(N, n, seed=10 + si, device=dev, out=x)
+        if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+            cpu_rows.append(x[: min(N, 500_000)].cpu().numpy())
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        ixs.append(sofa.Index(x, a.l, a.alphabet, sample_ratio=0.1, precision=1))
+        torch.cuda.synchronize()
+        gen_s += tb - ta
+        build_s += time.perf_counter() - tb
+        del x
+        torch.cuda.empty_cache()
+    packed, qo, ql, qk, oo, total, which = multi_queries(a, rank, dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    modes = {"plain": {}, "filters": dict(refine_filter=2)}
+    chosen = "filters"
+    results, answers = {}, {}
+    for name, tun in modes.items():
+        for ix in ixs:
+            ix.set_seed_mode(0)
+            ix.set_tuning(**tun)
+        for _ in range(a.warmup):
+            sofa.query_multi(ixs, packed, qo, ql, qk, oo, total)
+        torch.cuda.synchronize()
+        for ix in ixs:
+            ix.stats(reset=True)
+            ix.profile(reset=True)
+            ix.set_profiling(True)
+        clk = Clocks(local)
+        barrier(ws)
+        torch.cuda.synchronize()
+        clk.start()
+        tot_ms = 0.0
+        st = torch.cuda.current_stream()
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            idx, dist = sofa.query_multi(ixs, packed, qo, ql, qk, oo, total)
+            e1.record(st)
+            e1.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        for ix in ixs:
+            if ix.status() != 0:
+                raise RuntimeError(f"query status {ix.status()} in mode {name}: answers not valid")
+            ix.set_profiling(False)
+        barrier(ws)
+        profs = [ix.profile(reset=True) for ix in ixs]
+        stats = [ix.stats(reset=True) for ix in ixs]
+        prof = {"ms": {k: sum(p["ms"][k] for p in profs) for k in profs[0]["ms"]},
+                "launches": {k: sum(p["launches"][k] for p in profs) for k in profs[0]["launches"]},
+                "scan_tile_loads": sum(p["scan_tile_loads"] for p in profs),
+                "scan_tile_checks": sum(p["scan_tile_checks"] for p in profs)}
+        results[name] = dict(ms=max_over_ranks(tot_ms / a.steps, ws, dev), prof=prof, stats=stats, clocks=clocks)
+        answers[name] = idx.clone()
+    if not torch.equal(answers["plain"], answers["filters"]):
+        raise RuntimeError("the two modes gave different answers")
+    r = results[chosen]
+    value = ws * a.Q / (r["ms"] / 1e3)
+    prof = r["prof"]
+    phase = max(prof["ms"], key=lambda k: prof["ms"][k])
+    launches = max(1, prof["launches"][phase])
+    per_launch_s = prof["ms"][phase] / 1e3 / launches
+    LW = ixs[0].info()["word_bytes"]
+    roof = {"kernel": phase, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+    if phase == "scan":
+        clk = (r["clocks"].get("sm_mhz") or 1920.0) * 1e6
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_b = sms * 128 * clk / (3 * LW) / 1e9
+        bounds = sum(s_["tile_pairs"] for s_ in r["stats"]) * 256 / launches
+        ach_b = bounds / per_launch_s / 1e9
+        roof = {"kernel": "scan", "bound": "alu", "achieved": ach_b, "peak": peak_b,
+                "unit": "G (query, series) bounds/s", "frac": ach_b / peak_b, "traffic": None,
+                "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz / (3 x {LW})"}
+    step_bytes = 0.0
+    for (N, n), s_ in zip(MULTI_SETS, r["stats"]):
+        vf, f8, rf = s_.get("value_filtered", 0), s_.get("filtered", 0), s_["refined"]
+        value_checked = vf + f8 + rf if vf else 0
+        int8_rows = f8 + rf if (vf or f8) else 0
+        step_bytes += (s_["tile_pairs"] * 256 * LW + value_checked * (2 * LW + 8) + int8_rows * n + rf * n * 4)
+    step_bytes /= a.steps
+    step_roof = step_bytes / (r["ms"] / 1e3) / 1e9
+
+    e2e = None
+    if not a.no_e2e:
+        ph = packed.cpu().pin_memory()
+        qo_h, ql_h, qk_h, oo_h = qo.cpu(), ql.cpu(), qk.cpu(), oo.cpu()
+        ih, _ = sofa.query_multi(ixs, ph, qo_h, ql_h, qk_h, oo_h, total)
+        barrier(ws)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(a.steps):
+            ih, dh = sofa.query_multi(ixs, ph, qo_h, ql_h, qk_h, oo_h, total)
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - w0, ws, dev)
+        e2e = {"value": ws * a.Q * a.steps / el, "unit": "queries/s",
+               "h2d_bytes_per_step": packed.numel() * 4 + a.Q * (8 + 4 + 4 + 8), "d2h_bytes_per_step": total * 12}
+        assert torch.equal(ih, answers[chosen].cpu())
+
+    cpu = None
+    if cpu_rows:
+        rate, cores, sample, _ = multi_oracle_rate(a, cpu_rows, packed, qo, which, a.cpu_seconds)
+        cpu = {"value": rate, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "datasets": [f"{N}x{n}" for N, n in MULTI_SETS],
+                       "Q_per_gpu": a.Q, "k": "uniform in {1, 5, 10, 50}", "l": a.l, "alphabet": a.alphabet,
+                       "seed_mode": "plain", "tuning": modes[chosen],
+                       "precision": "fp32 SFA bounds, int8 value-code and int8 row filters (derived margins), "
+                                    "fp32 refine, fp64 final re-score",
+                       "l2": "flushed between timed steps (256 MB write)", "build_s": round(build_s, 3),
+                       "gen_s": round(gen_s, 3), "parallelism": f"replicas x{ws}"},
+            "roofline": roof,
+            "step_roofline": {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_roof,
+                              "frac": step_roof / hbm_peak, "peak": hbm_peak},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": r["clocks"],
+            "gpu_launches": int(sum(prof["launches"].values())),
+            "modes": {m: {"queries_per_s": ws * a.Q / (results[m]["ms"] / 1e3), "ms_per_step": results[m]["ms"],
+                          "phases_ms_per_step": {k: v / a.steps for k, v in results[m]["prof"]["ms"].items()},
+                          "pruning": {k: sum(s_[k] for s_ in results[m]["stats"]) / a.steps
+                                      for k in ("tile_pairs", "candidates", "refined", "filtered",
+                                                "value_filtered", "overflow_passes", "dense_passes")}}
+                      for m in results},
+        }
+        print(json.dumps(out), flush=True)
+    for ix in ixs:
+        ix.close()
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -537,6 +765,8 @@ def main():
     ws, rank, local = dist_init()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.gen == "multi":
+        run_sofa_multi(a, ws, rank, local)
     else:
         run_sofa(a, ws, rank, local)
     if ws > 1:

@@ -68,6 +68,66 @@ __global__ void k_rows_project(const float* __restrict__ x, int64_t R, int n, in
   }
 }
 
+// Query transform (Alg. 2 on queries, keeping the values) for a batch of
+// ROWS query rows per CTA of 256 threads.  Lane r of warp 0 takes row r's
+// canonical FP64 statistics (the same left-to-right sums as every
+// z-normalisation here, all 32 lanes busy on the FP64 pipe); all threads then
+// write the z-values; for the projection, warp w takes rows w, w+8, w+16,
+// w+24 and lane c the basis columns c and c+32, each a sequence of one FMA
+// per t in ascending t (the thread-per-row kernel's sequence, so the values
+// are the same bit for bit) while the basis loads are shared by four rows.
+static_assert(ROWS == 32, "k_qprep maps the rows of a CTA onto the lanes of one warp");
+__global__ void __launch_bounds__(256) k_qprep(const float* __restrict__ x, int64_t R, int n,
+                                               const float* __restrict__ basis, int NB, float* __restrict__ z,
+                                               float* __restrict__ v) {
+  extern __shared__ float sm[];  // ROWS x (n + 1): the rows, then their z-values in place
+  __shared__ double s_mu[ROWS], s_inv[ROWS];
+  const int64_t first = (int64_t)blockIdx.x * ROWS;
+  const int nr = (int)(R - first < ROWS ? R - first : ROWS);
+  for (int e = threadIdx.x; e < ROWS * n; e += blockDim.x) {
+    const int r = e / n, t = e - r * n;
+    sm[r * (n + 1) + t] = r < nr ? x[(first + r) * n + t] : 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    double mu, inv;
+    znorm_stats_seq(sm + threadIdx.x * (n + 1), n, 1, mu, inv);
+    s_mu[threadIdx.x] = mu;
+    s_inv[threadIdx.x] = inv;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+    const int r = e / n, t = e - r * n;
+    const float zt = znorm_value(sm[r * (n + 1) + t], s_mu[r], s_inv[r]);
+    sm[r * (n + 1) + t] = zt;
+    z[(first + r) * n + t] = zt;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = lane, c1 = lane + 32;
+  float acc[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.f;
+  for (int t = 0; t < n; ++t) {
+    const float b0 = c0 < NB ? __ldg(basis + (int64_t)t * NB + c0) : 0.f;
+    const float b1 = c1 < NB ? __ldg(basis + (int64_t)t * NB + c1) : 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float zt = sm[(warp + 8 * i) * (n + 1) + t];
+      acc[i][0] = fmaf(zt, b0, acc[i][0]);
+      acc[i][1] = fmaf(zt, b1, acc[i][1]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = warp + 8 * i;
+    if (r < nr) {
+      if (c0 < NB) v[(first + r) * NB + c0] = acc[i][0];
+      if (c1 < NB) v[(first + r) * NB + c1] = acc[i][1];
+    }
+  }
+}
+
 // ------------------------------------------------------------------------
 // SFA words of every series (Alg. 2): z-normalise, project on the l word
 // columns in FP32, quantise by counting breakpoints <= value (half-open bins
@@ -661,10 +721,9 @@ int launch_znorm(const float* x, int64_t R, int n, float* z, cudaStream_t st) {
 
 int launch_qprep(Index* ix, const float* q, int64_t Q, float* zq, float* qv, cudaStream_t st) {
   if (Q <= 0) return 0;
-  size_t smem = (size_t)ROWS * (ix->n + 1) * sizeof(float);
-  SOFA_CUDA(cudaFuncSetAttribute(k_rows_project<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_rows_project<true><<<(unsigned)ceil_div(Q, ROWS), ROWS, smem, st>>>(q, Q, ix->n, 1, ix->basis, ix->NB, ix->NB,
-                                                                         zq, qv, 0, nullptr);
+  const size_t smem = (size_t)ROWS * (ix->n + 1) * sizeof(float);
+  SOFA_CUDA(cudaFuncSetAttribute(k_qprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_qprep<<<(unsigned)ceil_div(Q, ROWS), 256, smem, st>>>(q, Q, ix->n, ix->basis, ix->NB, zq, qv);
   SOFA_CUDA(cudaGetLastError());
   return 0;
 }

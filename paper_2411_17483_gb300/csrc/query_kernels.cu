@@ -773,6 +773,7 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
 // scans give each slot its pool segment and its first chunk, and the chunk
 // total goes to the device (the refinement is persistent and reads it).
 constexpr int RSORT = 4096;
+constexpr uint16_t VDROP = 0xFFFFu;  // ordered slot of a candidate the value codes dropped (RSORT <= 0xFFFF)
 __global__ void __launch_bounds__(1024) k_chunk_plan(int64_t slots, int cap, const int* __restrict__ cand_n,
                                                      const int* __restrict__ qpool_cnt, int* __restrict__ qpool_off,
                                                      int* __restrict__ qcursor, int* __restrict__ choff,
@@ -1001,6 +1002,46 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
       atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(t));  // t >= 0: int order = float order
     }
   };
+  if constexpr (FILTER == 2) {
+    // value-code pass over the whole chunk before the rounds (many candidates
+    // per thread, so their gathers overlap instead of one per round and
+    // barrier): Eq. (1) on the selected values from their int8 codes,
+    // ||q~ - s c||_w - r <= ||q - v||_w <= d(q, x), against the threshold at
+    // this point (any threshold at or above the final one is valid); a
+    // dropped candidate's ordered slot is marked VDROP
+    const float Tv = vthr[q];
+#pragma unroll 2
+    for (int j = tid; j < nlive; j += blockDim.x) {
+      const int i = ord[j];
+      const unsigned long long kk = skey[i];
+      if (__uint_as_float((uint32_t)(kk >> 32)) > Tv) continue;  // left to the rounds' own check
+      const uint32_t p = (uint32_t)kk;
+      const float2 sr = __ldg(vsr + p);
+      const uint4* cp = reinterpret_cast<const uint4*>(VC + (int64_t)p * P.NB);
+      float a0 = 0.f, a1 = 0.f;
+      for (int u = 0; u < P.NB / 16; ++u) {
+        const uint4 w4 = __ldg(cp + u);
+        const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int e = 0; e < 4; e += 2) {
+            const int t0 = 16 * u + 4 * b + e;
+            const float c0 = (float)((int)(ws[b] << (24 - 8 * e)) >> 24);
+            const float c1 = (float)((int)(ws[b] << (16 - 8 * e)) >> 24);
+            const float d0 = fmaf(-sr.x, c0, sqv[t0]), d1 = fmaf(-sr.x, c1, sqv[t0 + 1]);
+            a0 = fmaf(d0 * sw[t0], d0, a0);          // weight 0, 1 or 2: exact products
+            a1 = fmaf(d1 * sw[t0 + 1], d1, a1);
+          }
+      }
+      const float lbv = __fsub_rd(__fsqrt_rd(__fmul_rd(a0 + a1, one_minus_gv)), sr.y);
+      if (lbv > 0.f && __fmul_rd(lbv, lbv) > 2.0f * Tv) {
+        ++vfiltered;
+        ord[j] = VDROP;
+      }
+    }
+    __syncthreads();
+  }
   if constexpr (FILTER != 0) {
     // rounds of 256 candidates, one per thread: the int8 bound
     // d(q, x) >= d(q, s v) - e (2 T is the squared distance bound, T in half
@@ -1021,34 +1062,11 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
       // survivors (compacted into s1), or the round's ordered candidates
       int n1 = nlive - base < 256 ? nlive - base : 256;
       if constexpr (FILTER == 2) {
-        // Eq. (1) on the selected values from their int8 codes, one candidate
-        // per thread: ||q~ - s c||_w - r <= ||q - v||_w <= d(q, x)
+        // the round's candidates that the value-code pass kept
         const int j = base + tid;
-        const int i = j < nlive ? ord[j] : 0;
-        if (j < nlive && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T) {
-          const uint32_t p = (uint32_t)skey[i];
-          const float2 sr = __ldg(vsr + p);
-          const uint4* cp = reinterpret_cast<const uint4*>(VC + (int64_t)p * P.NB);
-          float a0 = 0.f, a1 = 0.f;
-          for (int u = 0; u < P.NB / 16; ++u) {
-            const uint4 w4 = __ldg(cp + u);
-            const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-              for (int e = 0; e < 4; e += 2) {
-                const int t0 = 16 * u + 4 * b + e;
-                const float c0 = (float)((int)(ws[b] << (24 - 8 * e)) >> 24);
-                const float c1 = (float)((int)(ws[b] << (16 - 8 * e)) >> 24);
-                const float d0 = fmaf(-sr.x, c0, sqv[t0]), d1 = fmaf(-sr.x, c1, sqv[t0 + 1]);
-                a0 = fmaf(d0 * sw[t0], d0, a0);          // weight 0, 1 or 2: exact products
-                a1 = fmaf(d1 * sw[t0 + 1], d1, a1);
-              }
-          }
-          const float lbv = __fsub_rd(__fsqrt_rd(__fmul_rd(a0 + a1, one_minus_gv)), sr.y);
-          if (lbv > 0.f && __fmul_rd(lbv, lbv) > 2.0f * T) ++vfiltered;
-          else s1[atomicAdd(&s_n1, 1)] = p;
-        }
+        const int i = j < nlive ? ord[j] : VDROP;
+        if (i != VDROP && __uint_as_float((uint32_t)(skey[i] >> 32)) <= T)
+          s1[atomicAdd(&s_n1, 1)] = (uint32_t)skey[i];
         __syncthreads();
         n1 = s_n1;
       }
