@@ -16,7 +16,7 @@ Plain, slow FP64 restatements of the paper, each function citing its passage:
 * GEMINI filter-and-refine ...... Sec. II-A
 * proposal MLP (fwd / bwd) ...... not in the paper: a learned seed for the best-so-far
 
-Readings where the paper is silent or ambiguous (each restated in the design doc):
+Readings where the paper is silent or ambiguous:
 population sigma; Z rounded to fp32 after an FP64 multiply by 1/sigma; an
 orthonormal DFT with weight 2 for 0<k<n/2 and 1 for the Nyquist value; strided
 sampling; equi-depth breakpoint a = sorted[floor(a*S/alpha)]; breakpoints
