@@ -68,23 +68,27 @@ __global__ void k_rows_project(const float* __restrict__ x, int64_t R, int n, in
   }
 }
 
-// Query transform (Alg. 2 on queries, keeping the values) for a batch of
-// ROWS query rows per CTA of 256 threads.  Lane r of warp 0 takes row r's
+// Query transform (Alg. 2 on queries, keeping the values), RQ query rows per
+// CTA of 256 threads (RQ a power of two <= 32, chosen per batch so that
+// there are at least two CTAs per SM).  Lane r of warp 0 takes row r's
 // canonical FP64 statistics (the same left-to-right sums as every
-// z-normalisation here, all 32 lanes busy on the FP64 pipe); all threads then
-// write the z-values; for the projection, warp w takes rows w, w+8, w+16,
-// w+24 and lane c the basis columns c and c+32, each a sequence of one FMA
-// per t in ascending t (the thread-per-row kernel's sequence, so the values
-// are the same bit for bit) while the basis loads are shared by four rows.
-static_assert(ROWS == 32, "k_qprep maps the rows of a CTA onto the lanes of one warp");
+// z-normalisation here: a dependent chain of about 2n FP64 additions, on all
+// RQ lanes at once); all threads then write the z-values; for the projection
+// warp w takes rows w, w+8, w+16, w+24 (those below RQ) and lane c the basis
+// columns c and c+32, each a sequence of one FMA per t in ascending t (the
+// thread-per-row kernel's sequence, so the values are the same bit for bit),
+// the basis loads shared by the warp's rows.
+template <int RQ>
 __global__ void __launch_bounds__(256) k_qprep(const float* __restrict__ x, int64_t R, int n,
                                                const float* __restrict__ basis, int NB, float* __restrict__ z,
                                                float* __restrict__ v) {
-  extern __shared__ float sm[];  // ROWS x (n + 1): the rows, then their z-values in place
-  __shared__ double s_mu[ROWS], s_inv[ROWS];
-  const int64_t first = (int64_t)blockIdx.x * ROWS;
-  const int nr = (int)(R - first < ROWS ? R - first : ROWS);
-  for (int e = threadIdx.x; e < ROWS * n; e += blockDim.x) {
+  static_assert(RQ >= 1 && RQ <= 32 && (RQ & (RQ - 1)) == 0, "RQ: a power of two <= 32 (one warp's lanes)");
+  constexpr int RPW = (RQ + 7) / 8;  // rows per warp in the projection
+  extern __shared__ float sm[];      // RQ x (n + 1): the rows, then their z-values in place
+  __shared__ double s_mu[RQ], s_inv[RQ];
+  const int64_t first = (int64_t)blockIdx.x * RQ;
+  const int nr = (int)(R - first < RQ ? R - first : RQ);
+  for (int e = threadIdx.x; e < RQ * n; e += blockDim.x) {
     const int r = e / n, t = e - r * n;
     sm[r * (n + 1) + t] = r < nr ? x[(first + r) * n + t] : 0.f;
   }
@@ -104,28 +108,38 @@ __global__ void __launch_bounds__(256) k_qprep(const float* __restrict__ x, int6
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp >= RQ) return;  // no rows for this warp (RQ < 8); no barrier follows
   const int c0 = lane, c1 = lane + 32;
-  float acc[4][2];
+  float acc[RPW][2];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.f;
+  for (int i = 0; i < RPW; ++i) acc[i][0] = acc[i][1] = 0.f;
   for (int t = 0; t < n; ++t) {
     const float b0 = c0 < NB ? __ldg(basis + (int64_t)t * NB + c0) : 0.f;
     const float b1 = c1 < NB ? __ldg(basis + (int64_t)t * NB + c1) : 0.f;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RPW; ++i) {
       const float zt = sm[(warp + 8 * i) * (n + 1) + t];
       acc[i][0] = fmaf(zt, b0, acc[i][0]);
       acc[i][1] = fmaf(zt, b1, acc[i][1]);
     }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RPW; ++i) {
     const int r = warp + 8 * i;
     if (r < nr) {
       if (c0 < NB) v[(first + r) * NB + c0] = acc[i][0];
       if (c1 < NB) v[(first + r) * NB + c1] = acc[i][1];
     }
   }
+}
+
+template <int RQ>
+static int launch_qprep_rq(Index* ix, const float* q, int64_t Q, float* zq, float* qv, cudaStream_t st) {
+  const size_t smem = (size_t)RQ * (ix->n + 1) * sizeof(float);
+  SOFA_CUDA(cudaFuncSetAttribute(k_qprep<RQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_qprep<RQ><<<(unsigned)ceil_div(Q, RQ), 256, smem, st>>>(q, Q, ix->n, ix->basis, ix->NB, zq, qv);
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
 }
 
 // ------------------------------------------------------------------------
@@ -721,11 +735,18 @@ int launch_znorm(const float* x, int64_t R, int n, float* z, cudaStream_t st) {
 
 int launch_qprep(Index* ix, const float* q, int64_t Q, float* zq, float* qv, cudaStream_t st) {
   if (Q <= 0) return 0;
-  const size_t smem = (size_t)ROWS * (ix->n + 1) * sizeof(float);
-  SOFA_CUDA(cudaFuncSetAttribute(k_qprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_qprep<<<(unsigned)ceil_div(Q, ROWS), 256, smem, st>>>(q, Q, ix->n, ix->basis, ix->NB, zq, qv);
-  SOFA_CUDA(cudaGetLastError());
-  return 0;
+  // rows per CTA: the largest power of two <= 32 that still gives two CTAs
+  // per SM (the FP64 chain of a row is the floor; more CTAs spread the rest)
+  int dev = 0, sms = 0;
+  SOFA_CUDA(cudaGetDevice(&dev));
+  SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t per = Q / (2 * (int64_t)(sms > 0 ? sms : 1));
+  if (per >= 32) return launch_qprep_rq<32>(ix, q, Q, zq, qv, st);
+  if (per >= 16) return launch_qprep_rq<16>(ix, q, Q, zq, qv, st);
+  if (per >= 8) return launch_qprep_rq<8>(ix, q, Q, zq, qv, st);
+  if (per >= 4) return launch_qprep_rq<4>(ix, q, Q, zq, qv, st);
+  if (per >= 2) return launch_qprep_rq<2>(ix, q, Q, zq, qv, st);
+  return launch_qprep_rq<1>(ix, q, Q, zq, qv, st);
 }
 
 int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_t st) {
