@@ -242,3 +242,18 @@ def test_lb_le_dftlb_le_ed(gen, alpha, binning):
         assert np.all(lb <= dl * (1 + 1e-12) + 1e-12)
         assert np.all(dl <= ed2 * (1 + 1e-9) + 1e-9)
         assert lb[qi] == 0.0
+
+
+def test_lb2_tiny_closed_form():
+    """Eq. dist_i with Eq. (1)'s weights on a hand-worked case: two values,
+    the first a Nyquist value (weight 1), the second weight 2; bins
+    [-inf, 0, 1, inf) and [-inf, -1, 2, inf); query values (3, 0.5).
+    Word (1, 0): intervals [0, 1) and [-inf, -1) -> 1*(3-1)^2 + 2*(0.5+1)^2 = 8.5.
+    Word (0, 2): [-inf, 0) and [2, inf) -> 1*(3-0)^2 + 2*(2-0.5)^2 = 13.5.
+    Word (2, 1): [1, inf) and [-1, 2) hold both values -> 0."""
+    inf = np.inf
+    summ = {"l": 2, "w": np.array([1.0, 2.0]),
+            "beta": np.array([[-inf, 0.0, 1.0, inf], [-inf, -1.0, 2.0, inf]], np.float32)}
+    wds = np.array([[1, 0], [0, 2], [2, 1]], np.uint8)
+    lb = orc.lb2(np.array([3.0, 0.5]), wds, summ)
+    assert list(lb) == [8.5, 13.5, 0.0]
