@@ -298,7 +298,8 @@ sofa_handle sofa_load(const char* path, sofa_stream stream);
  * and inspection aid; the paper has no counterpart).  For every query q (raw,
  * z-normalised here) and every series at sorted position p (see
  * sofa_export_perm): out[q * N + p] = ||q||^2 + ||x_p||^2 - 2 q.x_p from TF32
- * operands with FP32 accumulation on the tensor cores.  *margin (may be NULL)
+ * operands (FP16 when the index holds an FP16 copy, precision 2) with FP32
+ * accumulation on the tensor cores.  *margin (may be NULL)
  * receives the bound M >= |out - d^2| that the query path's dense form relies
  * on.  queries (Q x n) and out (Q x N) are device memory; 1 <= Q <= 8192,
  * Q * N <= 2^31, n % 4 == 0.  Returns 0 or a negative SOFA_ERR_* code. */
