@@ -360,15 +360,35 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
         }
         __syncthreads();
         const int nt2 = s_nt;
-        for (int j = 0; j < nt2; ++j) {
-          const int64_t p = (tb + s_tl[j]) * TILE + tid;
-          if (p < lo || p >= hi) continue;
-          float c[LW], h[LW];
-          load_word_bounds<LW>(words, p, true, ch, c, h);
-          const float a = word_bound<LW, NYQ>(c, h, sq);
-          if (a < tau) {
-            const int slot = atomicAdd(&s_nl2, 1);
-            if (slot < LEARN_CAP) skey[cnt + slot] = pack_key(a, (uint32_t)p);
+        // surviving tiles four at a time: the words of all four are loaded
+        // before any bound, so their global-memory latencies overlap
+        for (int j0 = 0; j0 < nt2; j0 += 4) {
+          uint4 wv[4][LW / 16];
+          int64_t pp[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            pp[u] = j0 + u < nt2 ? (tb + s_tl[j0 + u]) * TILE + tid : -1;
+            const bool ok = pp[u] >= lo && pp[u] < hi;
+            const uint4* wp = reinterpret_cast<const uint4*>(words + (ok ? pp[u] : 0) * LW);
+#pragma unroll
+            for (int i4 = 0; i4 < LW / 16; ++i4) wv[u][i4] = ok ? __ldg(wp + i4) : make_uint4(0u, 0u, 0u, 0u);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (!(pp[u] >= lo && pp[u] < hi)) continue;
+            const uint32_t* w32 = reinterpret_cast<const uint32_t*>(wv[u]);
+            float c[LW], h[LW];
+#pragma unroll
+            for (int j = 0; j < LW; ++j) {
+              const float2 v = ch[j * MAX_ALPHA + ((w32[j >> 2] >> (8 * (j & 3))) & 0xFFu)];
+              c[j] = v.x;
+              h[j] = v.y;
+            }
+            const float a = word_bound<LW, NYQ>(c, h, sq);
+            if (a < tau) {
+              const int slot = atomicAdd(&s_nl2, 1);
+              if (slot < LEARN_CAP) skey[cnt + slot] = pack_key(a, (uint32_t)pp[u]);
+            }
           }
         }
         __syncthreads();
