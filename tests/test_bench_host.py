@@ -32,3 +32,25 @@ def test_workload_names():
     assert "25Mx128" in bench.workload_name(a) and "6Mx1024" in bench.workload_name(a)
     b = types.SimpleNamespace(gen="rw", N=100_000_000, n=256, Q=10_000, k=1, l=16, alphabet=256)
     assert bench.workload_name(b).startswith("random walks 100000000x256")
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints the
+    contract's line; a tiny workload keeps it to a few seconds."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--N", "20000",
+                          "--Q", "2", "--steps", "1", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "queries/s"
+    assert d["metric"] == bench.METRIC and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["config"]["workload"].startswith("random walks 20000x256")
