@@ -113,3 +113,21 @@ def test_gemini_equals_bruteforce(n, alpha, k):
     assert np.array_equal(gi, bi)
     assert np.array_equal(gd, bd)
     assert refined.min() >= k
+
+
+def test_window_keeps_a_near_tie_beyond_the_kth():
+    """Row 10 at distance 1 and row 3 at distance 1 + 4.77e-7 (one fp32 step
+    count away): one tie run, so the 1-NN is row 3 (lowest index), although
+    row 10 alone is the nearest.  The restricted forms must widen their window
+    by the 1e-6 tie window to see row 3."""
+    n = 4
+    Z = np.full((20, n), 2.0, np.float32)           # every other row at distance 4
+    Z[10] = [1.0, 0.0, 0.0, 0.0]
+    Z[3] = [np.float32(1.0 + 5e-7), 0.0, 0.0, 0.0]
+    q = np.zeros((1, n), np.float32)
+    d3 = float(np.float32(1.0 + 5e-7))
+    assert 1.0 < d3 < 1.0 + 1e-6                     # within the tie window of row 10
+    for fn in (orc.knn_full, orc.knn,
+               lambda Z_, q_, k: orc.knn_chunked(((r, Z_[r:r + 7]) for r in range(0, 20, 7)), q_, k, keep=2)):
+        idx, dist = fn(Z, q, 1)
+        assert idx[0, 0] == 3 and dist[0, 0] == d3

@@ -16,7 +16,7 @@ import test_oracle_sfa as ps
 from oracle import sofa_oracle as orc
 
 ORIG = {name: getattr(orc, name) for name in
-        ("znorm", "dft", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
+        ("znorm", "dft", "knn", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
          "sample_stride", "tie_order", "sqdist", "gelu", "softmax_xent", "mlp_loss_grad", "adam_step")}
 
 
@@ -155,6 +155,18 @@ def sqdist_drops_last_value(Z, zq):
     return ORIG["sqdist"](np.ascontiguousarray(np.asarray(Z)[:, :-1]), np.ascontiguousarray(np.asarray(zq)[:-1]))
 
 
+def knn_window_not_widened(Z, Zq, k):
+    idx = np.empty((Zq.shape[0], k), np.int64)
+    dist = np.empty((Zq.shape[0], k), np.float64)
+    for q in range(Zq.shape[0]):
+        d2 = orc.sqdist(Z, Zq[q])
+        d = np.sqrt(d2)
+        keep = np.nonzero(d <= np.partition(d, k - 1)[k - 1])[0]
+        oi, od = orc.tie_order(d2[keep], keep.astype(np.int64))
+        idx[q], dist[q] = oi[:k], od[:k]
+    return idx, dist
+
+
 def gelu_tanh(x):
     return 0.5 * x * (1.0 + np.tanh(math.sqrt(2.0 / math.pi) * (x + 0.044715 * x ** 3)))
 
@@ -214,6 +226,8 @@ CASES = [
      [pk.test_tie_window_is_one_millionth_relative, pk.test_run_is_anchored_at_first_element]),
     ("tie window 1e-5 instead of 1e-6", {"tie_order": tie_order_wide_window},
      [pk.test_tie_window_is_one_millionth_relative]),
+    ("k-NN window not widened by the tie window", {"knn": knn_window_not_widened},
+     [pk.test_window_keeps_a_near_tie_beyond_the_kth]),
     ("squared distance drops the last value", {"sqdist": sqdist_drops_last_value}, [pk.test_sqdist_matches_numpy]),
     ("GELU by the tanh approximation", {"gelu": gelu_tanh}, [pm.test_gelu_closed_values]),
     ("cross-entropy gradient not averaged over the batch", {"softmax_xent": softmax_grad_not_mean},
