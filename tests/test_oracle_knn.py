@@ -1,4 +1,6 @@
 """Pins of the oracle's exact k-NN, tie rule and GEMINI search."""
+import math
+
 import numpy as np
 import pytest
 
@@ -131,3 +133,34 @@ def test_window_keeps_a_near_tie_beyond_the_kth():
                lambda Z_, q_, k: orc.knn_chunked(((r, Z_[r:r + 7]) for r in range(0, 20, 7)), q_, k, keep=2)):
         idx, dist = fn(Z, q, 1)
         assert idx[0, 0] == 3 and dist[0, 0] == d3
+
+
+def test_gemini_refines_a_near_tie_beyond_the_kth():
+    """GEMINI's stopping rule must keep the 1e-6 tie window: row 10 is at
+    distance exactly 1 with bound 0; row 3 is at distance 2b = 1 + 4.77e-7
+    and its bound is 2*beta^2 with beta the bin edge just below its value, so
+    1 < bound <= its distance^2.  Stopping at bound > (the best distance)^2
+    would never refine row 3, whose lower index puts it first in the tie run.
+    n = 8; the selected value is Re X_2 (weight 2); every other row is far
+    (6 cos) but shares row 3's bin, hence its bound."""
+    n = 8
+    cos2 = np.array([1, 0, -1, 0, 1, 0, -1, 0], np.float32)   # cos(2 pi 2 t / 8)
+    sin2 = np.array([0, 1, 0, -1, 0, 1, 0, -1], np.float32)   # sin(2 pi 2 t / 8)
+    b = np.float32(0.5 * (1 + 5e-7))
+    Z = np.tile(3.0 * cos2, (20, 1)).astype(np.float32)
+    Z[10] = 0.5 * sin2                                         # distance^2 = 4 * 0.25 = 1, Re X_2 = 0
+    Z[3] = b * cos2                                            # distance^2 = 4 b^2, Re X_2 = b sqrt(2)
+    q = np.zeros((1, n), np.float32)
+    vb = float(b) * math.sqrt(2.0)
+    edge = np.float32(vb)
+    if float(edge) > vb:                                       # the bin edge at or just below row 3's value
+        edge = np.nextafter(edge, np.float32(0))
+    summ = {"l": 1, "ks": np.array([2]), "parts": np.array([0]), "w": np.array([2.0]),
+            "beta": np.array([[-np.inf, 0.35, float(edge), np.inf]], np.float32)}
+    assert 1.0 < 2 * float(edge) ** 2 <= 4 * float(b) ** 2 < (1 + 1e-6) ** 2
+    W = orc.words(Z, summ)
+    assert W[3, 0] == 2 and W[10, 0] == 0
+    bi, bd = orc.knn_full(Z, q, 1)
+    assert bi[0, 0] == 3
+    gi, gd, _ = orc.gemini_knn(Z, W, q, summ, 1)
+    assert gi[0, 0] == 3 and gd[0, 0] == bd[0, 0]

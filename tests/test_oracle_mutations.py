@@ -16,7 +16,7 @@ import test_oracle_sfa as ps
 from oracle import sofa_oracle as orc
 
 ORIG = {name: getattr(orc, name) for name in
-        ("znorm", "dft", "knn", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
+        ("znorm", "dft", "knn", "gemini_knn", "learn_summary", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
          "sample_stride", "tie_order", "sqdist", "gelu", "softmax_xent", "mlp_loss_grad", "adam_step")}
 
 
@@ -167,6 +167,33 @@ def knn_window_not_widened(Z, Zq, k):
     return idx, dist
 
 
+def gemini_stop_without_tie_window(Z, W, Zq, summ, k):
+    idx = np.empty((Zq.shape[0], k), np.int64)
+    dist = np.empty((Zq.shape[0], k), np.float64)
+    refined = np.zeros(Zq.shape[0], np.int64)
+    qv_all = orc.selected_values(Zq, summ)
+    for q in range(Zq.shape[0]):
+        lb = orc.lb2(qv_all[q][: summ["l"]], W, summ)
+        best_d2, best_i = [], []
+        for i in np.argsort(lb, kind="stable"):
+            if len(best_d2) >= k and math.sqrt(max(lb[i], 0.0)) > math.sqrt(sorted(best_d2)[k - 1]):
+                break
+            best_d2.append(float(orc.sqdist(Z[i:i + 1], Zq[q])[0]))
+            best_i.append(int(i))
+            refined[q] += 1
+        oi, od = orc.tie_order(np.array(best_d2), np.array(best_i, np.int64))
+        idx[q], dist[q] = oi[:k], od[:k]
+    return idx, dist, refined
+
+
+def summary_from_every_row(x, l, alpha, ratio=0.1, binning="equi-depth", select="variance", pool=0):
+    return ORIG["learn_summary"](x, l, alpha, 1.0, binning, select, pool)
+
+
+def summary_sample_shifted(x, l, alpha, ratio=0.1, binning="equi-depth", select="variance", pool=0):
+    return ORIG["learn_summary"](x[1:], l, alpha, ratio, binning, select, pool)
+
+
 def gelu_tanh(x):
     return 0.5 * x * (1.0 + np.tanh(math.sqrt(2.0 / math.pi) * (x + 0.044715 * x ** 3)))
 
@@ -228,6 +255,12 @@ CASES = [
      [pk.test_tie_window_is_one_millionth_relative]),
     ("k-NN window not widened by the tie window", {"knn": knn_window_not_widened},
      [pk.test_window_keeps_a_near_tie_beyond_the_kth]),
+    ("GEMINI stops without the tie window", {"gemini_knn": gemini_stop_without_tie_window},
+     [pk.test_gemini_refines_a_near_tie_beyond_the_kth]),
+    ("summary learned from every row instead of the sample", {"learn_summary": summary_from_every_row},
+     [ps.test_learn_summary_uses_the_strided_sample]),
+    ("summary sample shifted by one row", {"learn_summary": summary_sample_shifted},
+     [ps.test_learn_summary_uses_the_strided_sample]),
     ("squared distance drops the last value", {"sqdist": sqdist_drops_last_value}, [pk.test_sqdist_matches_numpy]),
     ("GELU by the tanh approximation", {"gelu": gelu_tanh}, [pm.test_gelu_closed_values]),
     ("cross-entropy gradient not averaged over the batch", {"softmax_xent": softmax_grad_not_mean},

@@ -257,3 +257,22 @@ def test_lb2_tiny_closed_form():
     wds = np.array([[1, 0], [0, 2], [2, 1]], np.uint8)
     lb = orc.lb2(np.array([3.0, 0.5]), wds, summ)
     assert list(lb) == [8.5, 13.5, 0.0]
+
+
+def test_learn_summary_uses_the_strided_sample():
+    """Alg. 1 learns from sample(X, r): with r = 0.1 the rows 0, 10, 20, ...
+    Those rows are cosines at k = 9 (random amplitude and sign), every other
+    row a cosine at k = 3, so only the strided sample ranks Re X_9 first; the
+    whole collection, or a sample shifted by one row, ranks Re X_3 first."""
+    rng = np.random.default_rng(21)
+    N, n = 1000, 64
+    t = np.arange(n)
+    amp = rng.standard_normal((N, 1)) * 3
+    f = np.where(np.arange(N)[:, None] % 10 == 0, 9, 3)
+    x = (amp * np.cos(2 * np.pi * f * t / n) + 0.01 * rng.standard_normal((N, n))).astype(np.float32)
+    summ = orc.learn_summary(x, l=1, alpha=16, ratio=0.1)
+    assert (int(summ["ks"][0]), int(summ["parts"][0])) == (9, 0)
+    # the bins come from the same sample: the k = 9 values of rows 0, 10, ...
+    z, _, _ = orc.znorm(x[::10])
+    v = orc.dft_values(z)[:, orc.value_table(n).index((9, 0))]
+    assert np.array_equal(summ["beta"][0], orc.learn_bins(v, 16, "equi-depth"))
