@@ -16,7 +16,7 @@ import test_oracle_sfa as ps
 from oracle import sofa_oracle as orc
 
 ORIG = {name: getattr(orc, name) for name in
-        ("znorm", "dft", "knn", "gemini_knn", "learn_summary", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
+        ("znorm", "dft", "knn", "gemini_knn", "learn_summary", "dft_values", "selected_values", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
          "sample_stride", "tie_order", "sqdist", "gelu", "softmax_xent", "mlp_loss_grad", "adam_step")}
 
 
@@ -194,6 +194,27 @@ def summary_sample_shifted(x, l, alpha, ratio=0.1, binning="equi-depth", select=
     return ORIG["learn_summary"](x[1:], l, alpha, ratio, binning, select, pool)
 
 
+def dft_values_parts_swapped(z, pool=0):
+    re, im = orc.dft(z)
+    tab = orc.value_table(np.asarray(z).shape[1], pool)
+    return np.stack([im[:, k] if p == 0 else re[:, k] for k, p in tab], axis=1)
+
+
+def selected_values_parts_swapped(z, summ):
+    re, im = orc.dft(z)
+    return np.stack([im[:, k] if p == 0 else re[:, k] for k, p in zip(summ["ks"], summ["parts"])], axis=1)
+
+
+def lb2_interval_one_bin_down(qv, wds, summ):
+    beta = summ["beta"].astype(np.float64)
+    out = np.zeros(wds.shape[0], np.float64)
+    for j in range(summ["l"]):
+        s = wds[:, j].astype(np.int64)
+        m = orc.mind(qv[j], beta[j][np.maximum(s - 1, 0)], beta[j][s])
+        out += summ["w"][j] * m * m
+    return out
+
+
 def gelu_tanh(x):
     return 0.5 * x * (1.0 + np.tanh(math.sqrt(2.0 / math.pi) * (x + 0.044715 * x ** 3)))
 
@@ -241,6 +262,12 @@ CASES = [
     ("a value on a breakpoint goes down", {"symbols": symbols_breakpoint_goes_down},
      [ps.test_symbols_bruteforce]),
     ("below the bin measured to its upper edge", {"mind": mind_below_to_upper_edge}, [ps.test_mind_three_cases]),
+    ("real and imaginary candidate values swapped", {"dft_values": dft_values_parts_swapped},
+     [ps.test_full_pool_dft_lb_equals_ed, ps.test_selection_finds_planted_frequencies]),
+    ("selected values read from the wrong part", {"selected_values": selected_values_parts_swapped},
+     [ps.test_selected_values_closed_form, pk.test_gemini_refines_a_near_tie_beyond_the_kth]),
+    ("bound taken against the bin below the symbol's", {"lb2": lb2_interval_one_bin_down},
+     [ps.test_lb2_tiny_closed_form, lambda: ps.test_lb_le_dftlb_le_ed("rw", 256, "equi-depth")]),
     ("Eq. (1) weight dropped from the SFA bound", {"lb2": lb2_without_weights}, [ps.test_lb2_tiny_closed_form]),
     ("variance ties broken by descending id", {"select_values": select_ties_by_descending_id},
      [ps.test_selection_ties_and_nyquist_first]),

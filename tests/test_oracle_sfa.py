@@ -276,3 +276,16 @@ def test_learn_summary_uses_the_strided_sample():
     z, _, _ = orc.znorm(x[::10])
     v = orc.dft_values(z)[:, orc.value_table(n).index((9, 0))]
     assert np.array_equal(summ["beta"][0], orc.learn_bins(v, 16, "equi-depth"))
+
+
+def test_selected_values_closed_form():
+    """A selected value is the real or imaginary part its (k, part) names:
+    for x_t = 2 cos(2 pi 5 t/n) + 3 sin(2 pi 7 t/n), n = 32, the orthonormal
+    DFT gives Re X_5 = sqrt(n), Im X_7 = -1.5 sqrt(n), Im X_5 = Re X_7 = 0."""
+    n = 32
+    t = np.arange(n)
+    x = (2 * np.cos(2 * np.pi * 5 * t / n) + 3 * np.sin(2 * np.pi * 7 * t / n)).astype(np.float32)[None, :]
+    summ = {"ks": np.array([5, 7, 5, 7]), "parts": np.array([0, 1, 1, 0])}
+    v = orc.selected_values(x, summ)[0]
+    expect = [math.sqrt(n), -1.5 * math.sqrt(n), 0.0, 0.0]
+    assert np.allclose(v, expect, rtol=0, atol=1e-5)
