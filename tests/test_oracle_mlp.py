@@ -63,3 +63,17 @@ def test_adam_first_step_is_lr_sign():
     v = {"w": np.zeros(3)}
     out = orc.adam_step(p, g, m, v, 1, lr=0.01)
     assert np.allclose(out["w"] - p["w"], -0.01 * np.sign(g["w"]), atol=1e-7)
+
+
+def test_forward_orientation_closed_form():
+    """x @ W with W stored [d_in, d_out]: a tiny network with a non-symmetric
+    middle layer.  x = (1, 2), W1 = I, W2 = [[0, 1], [0, 0]], W3 = I, zero
+    biases: a1 = (1, 2), h1 = (Phi(1), 2 Phi(2)), a2 = (0, h1[0]),
+    logits = h2 = (0, h1[0] Phi(h1[0])), with Phi the standard normal CDF."""
+    Phi = lambda v: 0.5 * (1.0 + math.erf(v / math.sqrt(2.0)))
+    p = {"W1": np.eye(2), "b1": np.zeros(2), "W2": np.array([[0.0, 1.0], [0.0, 0.0]]), "b2": np.zeros(2),
+         "W3": np.eye(2), "b3": np.zeros(2)}
+    logits, _ = orc.mlp_forward(p, np.array([[1.0, 2.0]]))
+    h10 = Phi(1.0)
+    assert abs(logits[0, 0]) < 1e-15
+    assert abs(logits[0, 1] - h10 * Phi(h10)) < 1e-12

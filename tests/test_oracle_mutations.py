@@ -16,7 +16,7 @@ import test_oracle_sfa as ps
 from oracle import sofa_oracle as orc
 
 ORIG = {name: getattr(orc, name) for name in
-        ("znorm", "dft", "knn", "gemini_knn", "learn_summary", "dft_values", "selected_values", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
+        ("znorm", "dft", "knn", "gemini_knn", "learn_summary", "dft_values", "selected_values", "mlp_forward", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
          "sample_stride", "tie_order", "sqdist", "gelu", "softmax_xent", "mlp_loss_grad", "adam_step")}
 
 
@@ -215,6 +215,12 @@ def lb2_interval_one_bin_down(qv, wds, summ):
     return out
 
 
+def forward_w2_transposed(params, x):
+    p = dict(params)
+    p["W2"] = params["W2"].T
+    return ORIG["mlp_forward"](p, x)
+
+
 def gelu_tanh(x):
     return 0.5 * x * (1.0 + np.tanh(math.sqrt(2.0 / math.pi) * (x + 0.044715 * x ** 3)))
 
@@ -289,6 +295,8 @@ CASES = [
     ("summary sample shifted by one row", {"learn_summary": summary_sample_shifted},
      [ps.test_learn_summary_uses_the_strided_sample]),
     ("squared distance drops the last value", {"sqdist": sqdist_drops_last_value}, [pk.test_sqdist_matches_numpy]),
+    ("middle layer applied transposed", {"mlp_forward": forward_w2_transposed},
+     [pm.test_forward_orientation_closed_form, pm.test_finite_differences]),
     ("GELU by the tanh approximation", {"gelu": gelu_tanh}, [pm.test_gelu_closed_values]),
     ("cross-entropy gradient not averaged over the batch", {"softmax_xent": softmax_grad_not_mean},
      [pm.test_zero_weights_uniform_softmax, pm.test_finite_differences]),
