@@ -16,8 +16,9 @@ import test_oracle_sfa as ps
 from oracle import sofa_oracle as orc
 
 ORIG = {name: getattr(orc, name) for name in
-        ("znorm", "dft", "knn", "gemini_knn", "learn_summary", "dft_values", "selected_values", "mlp_forward", "weight", "value_table", "learn_bins", "symbols", "mind", "lb2", "select_values",
-         "sample_stride", "tie_order", "sqdist", "gelu", "softmax_xent", "mlp_loss_grad", "adam_step")}
+        ("znorm", "dft", "dft_values", "selected_values", "weight", "value_table", "sample_stride",
+         "select_values", "learn_bins", "learn_summary", "symbols", "mind", "lb2", "sqdist", "tie_order", "knn",
+         "gemini_knn", "mlp_forward", "gelu", "softmax_xent", "mlp_loss_grad", "adam_step")}
 
 
 # ------------------------------------------------------------------ the mistakes
