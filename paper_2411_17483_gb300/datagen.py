@@ -10,6 +10,8 @@ paper's 17 datasets are not available, so these stand in for them:
                             series, phase U(0, 2pi), amplitude LogNormal(0, 1),
                             plus N(0, 0.3^2) noise (high-frequency stress)
 * perturbed members ....... a uniformly chosen dataset row plus N(0, 0.1^2)
+* alternating walks ....... a random walk plus A (-1)^t with A ~ N(0, amp^2)
+                            per series (energy at the Nyquist frequency)
 
 Every generator is deterministic for (seed, device): rows are produced in
 fixed chunks, each chunk drawing from its own torch.Generator seeded with
@@ -100,6 +102,26 @@ def sinusoid_mix(N: int, n: int, seed: int = 0, device="cpu", n_waves: int = 8,
                 noise[lo - s0:hi - s0] = slab[lo - b:hi - b]
         x += noise_sigma * noise
         out[done:done + rows] = x.to(torch.float32)
+        done += rows
+    return out
+
+
+def alternating_walks(N: int, n: int, amp: float, seed: int = 0, device="cpu", row0: int = 0) -> torch.Tensor:
+    """Random walks plus A (-1)^t, one amplitude A ~ N(0, amp^2) per series
+    (stream seed + 211); rows row0..row0+N-1 of the seeded stream."""
+    device = torch.device(device)
+    out = random_walks(N, n, seed=seed, device=device, row0=row0)
+    sign = torch.ones(n, dtype=torch.float64, device=device)
+    sign[1::2] = -1.0
+    done = 0
+    while done < N:
+        r = row0 + done
+        c = r // CHUNK
+        s0 = r - c * CHUNK
+        rows = min(CHUNK - s0, N - done)
+        g = _gen(seed + 211, c, device)
+        a = torch.randn((CHUNK, 1), generator=g, dtype=torch.float64, device=device)[s0:s0 + rows] * amp
+        out[done:done + rows] = (out[done:done + rows].to(torch.float64) + a * sign[None, :]).to(torch.float32)
         done += rows
     return out
 

@@ -45,7 +45,7 @@ def test_mlp_gradients_match_oracle(sofa, din, hidden, classes, B):
         g = grads[off:off + sz].reshape(shp)
         off += sz
         err = np.linalg.norm(g - og[name]) / max(np.linalg.norm(og[name]), 1e-30)
-        assert err < 3e-2, (name, err)       # BF16 operands, FP32 accumulation
+        assert err < 2e-2, (name, err)       # BF16 operands, FP32 accumulation
 
 
 def test_seed_mode_requires_training(sofa):
@@ -78,6 +78,11 @@ def test_learned_seed_keeps_answers_exact(sofa):
     zq, _, _ = orc.znorm(q[::10].cpu().numpy())
     oi, _ = orc.knn(z, zq, 5)
     assert np.array_equal(gi1[::10].cpu().numpy(), oi)
-    # the learned seed is never worse than the plain seed it extends
+    # the learned seed extends the plain one, so it is never worse; trained on
+    # this data it is strictly better: a lower seed distance for the batch, and
+    # so fewer (query, tile) pairs pass the tighter starting threshold
     assert s1["seed_dist_sum"] <= s0["seed_dist_sum"] * (1 + 1e-6)
+    gain = 1.0 - s1["seed_dist_sum"] / s0["seed_dist_sum"]
+    assert gain > 1e-3, (s0["seed_dist_sum"], s1["seed_dist_sum"])
+    assert s1["tile_pairs"] < s0["tile_pairs"], (s0["tile_pairs"], s1["tile_pairs"])
     ix.close()
