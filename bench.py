@@ -54,6 +54,8 @@ def parse():
                          "the dense tensor-core form")
     ap.add_argument("--no-autotune", action="store_true",
                     help="chosen mode with the default tuning instead of the autotuner's choice")
+    ap.add_argument("--modes", default="",
+                    help="comma-separated subset of the modes to time (plain, plain_seed, learned); default all")
     ap.add_argument("--gen", default="rw", choices=["rw", "mixed", "sin", "multi"],
                     help="rw: random walks (default); mixed: half walks + noisy walks with half perturbed-member "
                          "queries; sin: 8-sinusoid mixtures (high-frequency stress, bounds prune little); multi: "
@@ -63,24 +65,35 @@ def parse():
     return ap.parse_args()
 
 
-# DRAM traffic of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum
-# per launch, averaged over the two launches of one step: the 8192- and the
-# 1808-query batch) from one ncu capture of the default workload, chosen mode;
-# summary and command in profiles/k_scan_dram_rw100M_q10k.md.  Reported only
-# while the kernel's source is the one that was captured.
-SCAN_TRAFFIC = {"bytes_per_launch": 6636247808, "source_sha": "17bd9db7b490eaa9",
-                "workload": (100_000_000, 256, 10_000, 1, 16)}
+# DRAM traffic of the series-bound scan from one ncu capture of a small case
+# of the same kernel (random walks 4M x 256, 2000 queries, k = 1, learned
+# seed + filters; one launch, --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum), with the units that launch processed.  A full-size
+# launch's traffic is scaled from it: reads by the tile loads (each loads a
+# tile's words), writes by the candidates emitted.  Reported only while the
+# kernel's source is the one that was captured (sha256 of its template text).
+SCAN_CAPTURE = None
 
 
-def kernel_source_sha(name="k_scan"):
-    """sha256 (16 hex digits) of a kernel template's text in query_kernels.cu."""
+def kernel_source_sha(name="k_scan", path=None):
+    """sha256 (16 hex digits) of a kernel template's text."""
     import hashlib
-    path = os.path.join(ROOT, "paper_2411_17483_gb300", "csrc", "query_kernels.cu")
+    path = path or os.path.join(ROOT, "paper_2411_17483_gb300", "csrc", "query_kernels.cu")
     s = open(path).read()
-    i = s.index(f"{name}(QueryParams P")
+    i = s.index(f" {name}(")
     a = s.rindex("template <", 0, i)
     b = s.index("\n}\n", i) + 3
     return hashlib.sha256(s[a:b].encode()).hexdigest()[:16]
+
+
+def scaled_scan_traffic(tile_loads, candidates):
+    """Per-launch DRAM bytes of the scan scaled from the stored small-case
+    capture, or None when there is none for the current kernel source."""
+    c = SCAN_CAPTURE
+    if not c or kernel_source_sha("k_scan") != c["source_sha"]:
+        return None
+    return (c["dram_read"] * tile_loads / c["tile_loads"]
+            + c["dram_write"] * candidates / max(1, c["candidates"]))
 
 
 def precision_text(a, stats) -> str:
@@ -177,6 +190,21 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def nvtx_push(name):
+    """Host-thread NVTX range around one mode's warm-up and timed steps, so a
+    profiler can select that mode's launches (ncu --nvtx --nvtx-include)."""
+    try:
+        torch.cuda.nvtx.range_push(name)
+        return True
+    except (AttributeError, RuntimeError):
+        return False
+
+
+def nvtx_pop(pushed):
+    if pushed:
+        torch.cuda.nvtx.range_pop()
 
 
 def peaks():
@@ -412,15 +440,24 @@ def run_sofa_multi(a, ws, rank, local):
     LW = ixs[0].info()["word_bytes"]
     roof = {"kernel": phase, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
             "traffic": None}
+    alu = None
     if phase == "scan":
+        tile_pairs = sum(s_["tile_pairs"] for s_ in r["stats"])
+        alg = (tile_pairs * 256 * LW + prof["scan_tile_checks"] * 2 * LW) / launches
+        ach = alg / per_launch_s / 1e9
+        roof = {"kernel": "k_scan", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "algorithmic_bytes_per_launch": alg,
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "note": "logical bytes: LW bytes per (query, series) pair bounded plus 2 LW per tile envelope "
+                        "checked; the queries of a work unit share each tile's read, so frac can exceed 1"}
         clk = (r["clocks"].get("sm_mhz") or 1920.0) * 1e6
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_b = sms * 128 * clk / (3 * LW) / 1e9
-        bounds = sum(s_["tile_pairs"] for s_ in r["stats"]) * 256 / launches
-        ach_b = bounds / per_launch_s / 1e9
-        roof = {"kernel": "scan", "bound": "alu", "achieved": ach_b, "peak": peak_b,
-                "unit": "G (query, series) bounds/s", "frac": ach_b / peak_b, "traffic": None,
-                "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz / (3 x {LW})"}
+        ach_b = tile_pairs * 256 / launches / per_launch_s / 1e9
+        alu = {"kernel": "k_scan", "achieved": ach_b, "peak": peak_b, "unit": "G (query, series) bounds/s",
+               "frac": ach_b / peak_b,
+               "peak_kind": f"derived from the kernel's own 3 FP32 lane operations per value: {sms} SMs x 128 "
+                            f"lanes x {clk / 1e6:.0f} MHz / (3 x {LW})"}
     step_bytes = 0.0
     for (N, n), s_ in zip(MULTI_SETS, r["stats"]):
         vf, f8, rf = s_.get("value_filtered", 0), s_.get("filtered", 0), s_["refined"]
@@ -464,6 +501,7 @@ def run_sofa_multi(a, ws, rank, local):
                        "l2": "flushed between timed steps (256 MB write)", "build_s": round(build_s, 3),
                        "gen_s": round(gen_s, 3), "parallelism": f"replicas x{ws}"},
             "roofline": roof,
+            "alu_view": alu,
             "step_roofline": {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_roof,
                               "frac": step_roof / hbm_peak, "peak": hbm_peak},
             "cpu_baseline": cpu,
@@ -514,8 +552,13 @@ def run_sofa(a, ws, rank, local):
     dist = torch.empty((a.Q, a.k), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    modes = {"plain": 0}
-    chosen = "plain"
+    # plain: key-window seed, FP32 bounds and refinement, default tuning;
+    # plain_seed: the same seed with the chosen mode's refinement filters and
+    # autotuned knobs; learned: the proposal network's seed with those same
+    # filters and knobs.  plain_seed and learned differ only in the seed.
+    # All three are exact and must give identical answers.
+    modes = {"plain": (0, False), "plain_seed": (0, True)}
+    chosen = "plain_seed"
     train = None
     if a.seed_mode in ("chosen", "learned"):
         torch.cuda.synchronize()
@@ -526,28 +569,36 @@ def run_sofa(a, ws, rank, local):
         train = {"seconds": round(time.perf_counter() - tt0, 2), "pairs": inf2["proposal_train"],
                  "classes": inf2["proposal_classes"], "loss": inf2["proposal_loss"],
                  "heldout_top1": inf2["proposal_top1"], "heldout_top4": inf2["proposal_topm"]}
-        modes["learned"] = 1
+        modes["learned"] = (1, True)
         chosen = "learned"
-    # the chosen mode's run-time tuning: the autotuner's pick on 2048 queries
-    # of a separate stream (seed 100 + rank), never on the timed queries
-    chosen_tuning = dict(refine_filter=2)
+    if a.modes:
+        keep = [m.strip() for m in a.modes.split(",") if m.strip()]
+        if chosen not in keep:
+            raise SystemExit(f"--modes must include the chosen mode ({chosen})")
+        modes = {m: modes[m] for m in modes if m in keep}
+    # run-time tuning of the tuned modes: the autotuner's pick for each seed
+    # mode, on 2048 queries of a separate stream (seed 100 + rank), never on
+    # the timed queries; both start from the same refinement filters
+    tunings = {m: dict(refine_filter=2) for m in modes}
     if not a.no_autotune:
         qt = make_rows(a, 2048, 100 + rank, dev)
-        ix.set_seed_mode(modes[chosen])
-        ix.set_tuning(refine_filter=2)
-        t = ix.autotune(qt, a.k)
-        chosen_tuning = {k: v for k, v in t.items() if v}
+        for m, (mode, tuned) in modes.items():
+            if not tuned:
+                continue
+            ix.set_seed_mode(mode)
+            ix.set_tuning(refine_filter=2)
+            t = ix.autotune(qt, a.k)
+            tunings[m] = {k: v for k, v in t.items() if v}
         del qt
-    results = {}
-    for mode_name, mode in modes.items():
-        # plain: FP32 bounds and refinement, key-window seed, default tuning;
-        # chosen: learned seed, the refinement filters (value codes, then int8
-        # rows) and the autotuned knobs (all exact)
+    chosen_tuning = tunings[chosen]
+    results, answers = {}, {}
+    for mode_name, (mode, tuned) in modes.items():
         ix.set_seed_mode(mode)
-        if mode_name == chosen:
-            ix.set_tuning(**chosen_tuning)
+        if tuned:
+            ix.set_tuning(**tunings[mode_name])
         else:
             ix.set_tuning()
+        pushed = nvtx_push(f"mode_{mode_name}")
         for _ in range(a.warmup):
             ix.query(q, a.k, idx, dist)
         torch.cuda.synchronize()
@@ -572,6 +623,7 @@ def run_sofa(a, ws, rank, local):
             tot_ms += e0.elapsed_time(e1)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        nvtx_pop(pushed)
         clocks = clk.stop()
         code = ix.status()
         if code != 0:
@@ -582,17 +634,28 @@ def run_sofa(a, ws, rank, local):
         stats = ix.stats(reset=True)
         ms_step = max_over_ranks(tot_ms / a.steps, ws, dev)
         results[mode_name] = dict(ms=ms_step, prof=prof, stats=stats, clocks=clocks, wall=wall)
+        answers[mode_name] = (idx.clone(), dist.clone())
+    for m in answers:
+        if not (torch.equal(answers[m][0], answers[chosen][0]) and torch.equal(answers[m][1], answers[chosen][1])):
+            raise RuntimeError(f"modes {m} and {chosen} gave different answers")
     r = results[chosen]
     value = ws * a.Q / (r["ms"] / 1e3)
 
-    # roofline of the dominant kernel (live CUDA-event times from the library)
+    # roofline of the dominant kernel (live CUDA-event times from the library,
+    # recorded on the stream the kernels run on)
     prof, stats = r["prof"], r["stats"]
     phase = max(prof["ms"], key=lambda k: prof["ms"][k])
     launches = max(1, prof["launches"][phase])
     per_launch_s = prof["ms"][phase] / 1e3 / launches
     LW = info["word_bytes"]
-    if phase == "scan":
-        alg_bytes = (prof["scan_tile_loads"] * 256 * LW + prof["scan_tile_checks"] * 2 * LW) / launches
+    dense_pairs = stats.get("dense_pairs", 0)
+    scan_units = None
+    if phase == "scan" and dense_pairs == 0:
+        # algorithmic bytes: the word of every (query, series) pair bounded
+        # (LW bytes each) and the tile envelopes checked (2 LW bytes each);
+        # above 1 means the queries of a work unit share each tile's read
+        alg_bytes = (stats["tile_pairs"] * 256 * LW + prof["scan_tile_checks"] * 2 * LW) / launches
+        scan_units = dict(tile_loads=prof["scan_tile_loads"] / launches, candidates=stats["candidates"] / launches)
     elif phase == "refine":
         alg_bytes = stats["refined"] * a.n * 4 / launches
     elif phase == "seed":
@@ -600,12 +663,20 @@ def run_sofa(a, ws, rank, local):
     else:
         alg_bytes = None
     hbm = {"kernel": phase, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None,
-           "traffic": None, "peak_kind": peak_kind}
+           "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     if alg_bytes is not None and per_launch_s > 0:
         ach = alg_bytes / per_launch_s / 1e9
-        hbm.update(achieved=ach, frac=ach / hbm_peak)
+        hbm.update(achieved=ach, frac=ach / hbm_peak, algorithmic_bytes_per_launch=alg_bytes)
+    if scan_units is not None:
+        hbm["kernel"] = "k_scan"
+        hbm["note"] = ("logical bytes: LW bytes per (query, series) pair bounded plus 2 LW per tile envelope "
+                       "checked; the queries of a work unit share each tile's read, so frac can exceed 1")
+        hbm["traffic"] = scaled_scan_traffic(scan_units["tile_loads"], scan_units["candidates"])
+        if hbm["traffic"] is not None:
+            hbm["traffic_kind"] = ("scaled from the stored ncu capture of " + SCAN_CAPTURE["case"] +
+                                   ": reads by tile loads, writes by candidates")
     roof = hbm
-    dense_pairs = stats.get("dense_pairs", 0)
+    alu = None
     if phase == "scan" and dense_pairs > 0:
         # dense batches: the bound phase is the tcgen05 contraction, TF32
         # operands, or FP16 when the index holds an FP16 copy.  Tensor
@@ -622,29 +693,33 @@ def run_sofa(a, ws, rank, local):
             bf16, pk_kind = 1900.0, f"fallback bf16 {rname}"
         peak_t = bf16 * ratio
         npad = (a.n + 31) // 32 * 32
-        flops = 2.0 * dense_pairs * npad / launches
-        ach_t = flops / per_launch_s / 1e12
-        roof = {"kernel": "dense", "bound": "tensor", "achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s",
-                "frac": ach_t / peak_t, "traffic": None, "peak_kind": pk_kind, "hbm_view": hbm}
+        # one k_dense launch per dense pass; the phase also holds the query
+        # norms (and the FP16 query copy), a few microseconds, so the time per
+        # launch is an upper bound of the contraction's
+        dense_launches = max(1, stats.get("dense_passes", 0))
+        per_dense_s = prof["ms"][phase] / 1e3 / dense_launches
+        flops = 2.0 * dense_pairs * npad / dense_launches
+        ach_t = flops / per_dense_s / 1e12
+        roof = {"kernel": "k_dense", "bound": "tensor", "achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s",
+                "frac": ach_t / peak_t, "traffic": None, "peak_kind": pk_kind,
+                "flops_per_launch": flops, "launch_ms": per_dense_s * 1e3,
+                "note": "launch_ms is the dense phase's time per k_dense launch, including the query-side "
+                        "helper kernels of the phase"}
     elif phase == "scan":
-        # ALU roofline: one (query, series) bound needs, per value, 3 FP32 lane
-        # operations (q - c, the scaled clamp, the square-accumulate); the FP32
-        # pipe does 128 lane operations per SM per clock, packed or not:
-        # peak = SMs x 128 x SM clock / (3 LW)
+        # a second view of the same kernel: its own instruction mix is 3 FP32
+        # lane operations per value (q - c, the scaled clamp, the
+        # square-accumulate), so the FP32 pipe's 128 lanes per SM per clock
+        # cap it at SMs x 128 x SM clock / (3 LW) bounds/s.  The denominator
+        # is this kernel's formulation, not an algorithmic bound.
         clk = (r["clocks"].get("sm_mhz") or 1920.0) * 1e6
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_b = sms * 128 * clk / (3 * LW) / 1e9
         bounds = stats["tile_pairs"] * 256 / launches
         ach_b = bounds / per_launch_s / 1e9
-        traffic = None
-        if ((a.N, a.n, a.Q, a.k, a.l) == SCAN_TRAFFIC["workload"] and chosen == "learned"
-                and kernel_source_sha("k_scan") == SCAN_TRAFFIC["source_sha"]):
-            traffic = SCAN_TRAFFIC["bytes_per_launch"]
-        hbm["traffic"] = traffic
-        roof = {"kernel": "scan", "bound": "alu", "achieved": ach_b, "peak": peak_b,
-                "unit": "G (query, series) bounds/s", "frac": ach_b / peak_b, "traffic": traffic,
-                "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz / (3 x {LW})",
-                "hbm_view": hbm}
+        alu = {"kernel": "k_scan", "achieved": ach_b, "peak": peak_b, "unit": "G (query, series) bounds/s",
+               "frac": ach_b / peak_b,
+               "peak_kind": f"derived from the kernel's own 3 FP32 lane operations per value: {sms} SMs x 128 "
+                            f"lanes x {clk / 1e6:.0f} MHz / (3 x {LW})"}
     # whole-step algorithmic bytes: SFA words of every bounded series; for
     # each candidate reaching a filter, its value codes (2 LW bytes + scale
     # and margin) and / or its int8 row; the fp32 rows refined
@@ -655,7 +730,9 @@ def run_sofa(a, ws, rank, local):
                   + rf * a.n * 4) / a.steps
     step_roof = step_bytes / (r["ms"] / 1e3) / 1e9
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers, in the chosen mode
+    ix.set_seed_mode(modes[chosen][0])
+    ix.set_tuning(**chosen_tuning)
     e2e = None
     if not a.no_e2e:
         qh = q.cpu().pin_memory()
@@ -728,6 +805,20 @@ def run_sofa(a, ws, rank, local):
                "sample": f"{done} queries brute-forced (FP64) over the first {cpu_rows.shape[0]} of {a.N} series "
                          f"in {el:.1f} s, scaled by {cpu_rows.shape[0]}/{a.N}"}
 
+    # the learned seed against the plain seed, both with the chosen filters
+    # and tuning: the proposal network's own effect
+    seed_gain = None
+    if "learned" in results and "plain_seed" in results:
+        L_, P_ = results["learned"], results["plain_seed"]
+        seed_gain = {"queries_per_s_ratio": P_["ms"] / L_["ms"],
+                     "tile_pairs_ratio": L_["stats"]["tile_pairs"] / max(1, P_["stats"]["tile_pairs"]),
+                     "candidates_ratio": L_["stats"]["candidates"] / max(1, P_["stats"]["candidates"]),
+                     "seed_ms_per_step": {m: (results[m]["prof"]["ms"]["seed"] + results[m]["prof"]["ms"]["proposal"])
+                                          / a.steps for m in ("plain_seed", "learned")},
+                     "seed_over_final_dist": {m: results[m]["stats"]["seed_dist_sum"] /
+                                              max(1e-9, results[m]["stats"]["final_dist_sum"])
+                                              for m in ("plain_seed", "learned")}}
+    build_bytes = a.N * a.n * 4
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": a.steps,
@@ -737,7 +828,13 @@ def run_sofa(a, ws, rank, local):
                        "alphabet": a.alphabet, "seed_mode": chosen, "tuning": chosen_tuning, "precision": precision_text(a, stats),
                        "l2": "flushed between timed steps (256 MB write)", "build_s": round(t2 - t1, 3),
                        "gen_s": round(t1 - t0, 3), "parallelism": f"replicas x{ws}"},
+            "build": {"seconds": round(t2 - t1, 3), "input_bytes": build_bytes,
+                      "input_gbs": build_bytes / max(1e-9, t2 - t1) / 1e9,
+                      "frac_of_hbm_read": build_bytes / max(1e-9, t2 - t1) / 1e9 / hbm_peak},
             "roofline": roof,
+            "alu_view": alu,
+            "learned_vs_plain_seed": seed_gain,
+            "tunings": {m: (tunings[m] if modes[m][1] else "defaults") for m in modes},
             "step_roofline": {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_roof,
                               "frac": step_roof / hbm_peak, "peak": hbm_peak},
             "cpu_baseline": cpu,
@@ -749,7 +846,9 @@ def run_sofa(a, ws, rank, local):
                           max(1e-9, results[m]["stats"]["final_dist_sum"]),
                           "pruning": {k: v / a.steps for k, v in results[m]["stats"].items()
                                       if k not in ("n_leaves", "n_tiles", "seed_dist_sum", "final_dist_sum")},
-                          "phases_ms_per_step": {k: v / a.steps for k, v in results[m]["prof"]["ms"].items()}}
+                          "scan_tile_loads_per_step": results[m]["prof"]["scan_tile_loads"] / a.steps,
+                          "phases_ms_per_step": {k: v / a.steps for k, v in results[m]["prof"]["ms"].items()},
+                          "launches_per_step": {k: v / a.steps for k, v in results[m]["prof"]["launches"].items()}}
                       for m in results},
             "proposal_training": train,
             "latency_64_queries": latency,

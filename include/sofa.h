@@ -22,6 +22,10 @@
  *   - Arrays are row-major, without padding, unless stated otherwise.
  *   - Arguments are validated before any device work is enqueued; an invalid
  *     argument changes nothing.
+ *   - A handle belongs to the device that was current when it was built or
+ *     loaded.  Every call that launches device work for a handle (query,
+ *     lower bounds, training, autotuning, the dense contraction) returns
+ *     SOFA_ERR_INVALID_ARG when another device is current.
  *   - There is no CPU fallback: every step runs in this library's CUDA kernels.
  */
 #ifndef SOFA_H_
@@ -52,6 +56,7 @@ enum {
 /* Limits. */
 #define SOFA_MAX_WORD 32      /* l <= 32 word values                            */
 #define SOFA_MAX_K 64         /* k <= 64 neighbours per query                   */
+#define SOFA_MAX_WINDOW 96    /* entries of a k-NN window (sofa_query_window)   */
 
 /* Build options (sofa_build uses the defaults: every field zero). */
 typedef struct {
@@ -89,6 +94,23 @@ sofa_handle sofa_build(const float* data, int64_t N, int32_t n, int32_t l, int32
 sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, int32_t alphabet,
                           const sofa_build_opts* opts, sofa_stream stream);
 
+/* Incremental insert (Sec. IV "Structure": the index takes new series, which
+ * the paper's tree routes to the leaf of their word).  N_add new series of the
+ * index's length n (data: N_add x n fp32, host or device memory, read during
+ * the call only) are z-normalised and summarised with the index's learned
+ * summary (Alg. 2; the selection and bins are not relearned), and merged by
+ * layout key into the appended region: a second key-sorted run after the
+ * build's, with its own tiles and leaf blocks.  New series get the row ids
+ * N, N+1, ... in data order (N the size before the call).  Later queries,
+ * lower bounds, the dense contraction and sofa_save cover every row; the seed
+ * searches both runs by key.  A trained proposal network keeps its classes
+ * (blocks of the positions it was trained on); its seed stays an upper bound,
+ * so answers stay exact.  While the rows are merged the old and the grown
+ * arrays are held together: SOFA_ERR_OOM, returned before any change, means
+ * the device lacks that room.  N + N_add < 2^31.  The call synchronises
+ * `stream`; N_add = 0 is a no-op. */
+int sofa_insert(sofa_handle h, const float* data, int64_t N_add, sofa_stream stream);
+
 /* Exact k-NN (Sec. II NN problem; k-NN as in Sec. V Table III) of Q queries.
  * queries: Q x n fp32 (raw, z-normalised inside); idx: Q x k int64 original
  * row ids; dist: Q x k fp32 z-normalised Euclidean distances (not squared),
@@ -99,6 +121,24 @@ sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, in
  * 1 <= k <= min(SOFA_MAX_K, N).  Q = 0 is a no-op.  Returns the status code. */
 int sofa_query(sofa_handle h, const float* queries, int64_t Q, int32_t k,
                int64_t* idx, float* dist, sofa_stream stream);
+
+/* k-NN windows for merging the answers of several indexes over disjoint row
+ * ranges (series sharding: each shard searched exactly on its own, the
+ * k-NN of the union merged from per-shard windows; Sec. II NN problem and the
+ * k-NN extension of Sec. V Table III, with the tie rule of sofa_query).  For
+ * each query: every series of this index whose distance d satisfies
+ * d <= D_k + 1e-6 D_k, D_k its k-th smallest distance in this index -- the
+ * only rows that can take one of the first k places of the tie rule in the
+ * union, whose k-th distance is at most D_k.  ids: Q x cap int64 original
+ * row ids of this index; d2: Q x cap FP64 squared distances (the
+ * left-to-right FP64 sum of squared differences of the canonical series, the
+ * precision in which the tie rule is decided); both ascending by (distance,
+ * id) and padded with -1 / +inf; counts: Q int32 window sizes.  A window of
+ * more than cap rows is cut to cap and flagged SOFA_ERR_TIE_OVERFLOW in the
+ * status word (sofa_query_status).  k <= cap <= SOFA_MAX_WINDOW.  Pointers
+ * may be host or device memory (same rules as sofa_query). */
+int sofa_query_window(sofa_handle h, const float* queries, int64_t Q, int32_t k, int32_t cap,
+                      int64_t* ids, double* d2, int32_t* counts, sofa_stream stream);
 
 /* Mixed workload: queries of different lengths against several indexes in
  * one call.  Query i (packed at float offset q_offsets[i] of `queries`, length
@@ -249,6 +289,7 @@ typedef struct {
   double proposal_loss;            /* mean cross-entropy of the last epoch     */
   double proposal_top1, proposal_topm;  /* held-out hit rate of the block of the
                                            exact nearest neighbour (top-1, top-m) */
+  int64_t appended;                /* rows added by sofa_insert since the build */
 } sofa_info_t;
 int sofa_info(sofa_handle h, sofa_info_t* out);
 
@@ -274,9 +315,10 @@ int sofa_lower_bounds(sofa_handle h, const float* queries, int64_t Q, float* out
  * allocation's implicit synchronisation): its work space is a fixed 16 MiB
  * array in the library's device image, held by every GPU that loads the
  * library until the process exits.  Same arguments and output as
- * sofa_lower_bounds (device pointers); Q <= 2^22 / (n + 2 * word_bytes)
- * queries per call, larger Q is rejected with SOFA_ERR_INVALID_ARG before any
- * work.  It calls no cudaMalloc or cudaFree.  The first call on a device looks
+ * sofa_lower_bounds (device or managed pointers); Q <= 2^22 / (n + 2 *
+ * word_bytes) queries per call, larger Q is rejected with SOFA_ERR_INVALID_ARG
+ * before any work, and so is a call made while a device other than the
+ * index's is current.  It calls no cudaMalloc or cudaFree.  The first call on a device looks
  * up the work space's device address (cudaGetSymbolAddress) and should happen
  * before any stream capture.  All calls share the one work space: calls whose
  * device work overlaps (different streams, or host threads) race and must be

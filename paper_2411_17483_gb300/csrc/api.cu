@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sofa_internal.cuh"
 
 namespace sofa {
@@ -54,8 +56,13 @@ cudaEvent_t Prof::get() {
   return e;
 }
 
+static const char* const kPhaseName[NPHASE] = {"sofa.qprep", "sofa.seed",  "sofa.route",    "sofa.scan",
+                                                 "sofa.refine", "sofa.final", "sofa.proposal", "sofa.pool"};
+
 void Prof::begin(int phase, cudaStream_t st, int kernels) {
   launches[phase] += kernels;
+  nvtxRangePushA(kPhaseName[phase]);
+  ++nvtx_depth;
   if (!on) return;
   cudaEvent_t a = get(), b = get();
   cudaEventRecord(a, st);
@@ -63,9 +70,27 @@ void Prof::begin(int phase, cudaStream_t st, int kernels) {
 }
 
 void Prof::end(cudaStream_t st) {
+  if (nvtx_depth > 0) {
+    nvtxRangePop();
+    --nvtx_depth;
+  }
   if (!on || open.empty()) return;
   cudaEventRecord(open.back().second.second, st);
 }
+
+void Prof::unwind(int depth) {
+  while (nvtx_depth > depth) {
+    nvtxRangePop();
+    --nvtx_depth;
+  }
+}
+
+NvtxScope::NvtxScope(Prof& p, const char* name) : prof(p), depth(p.nvtx_depth) {
+  nvtxRangePushA(name);
+  ++prof.nvtx_depth;
+}
+
+NvtxScope::~NvtxScope() { prof.unwind(depth); }
 
 void Prof::collect() {
   for (auto& o : open) {
@@ -84,13 +109,22 @@ void Prof::release() {
   pool.clear();
 }
 
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_device(const Index* ix) {
+  int dev = -1;
+  SOFA_CUDA(cudaGetDevice(&dev));
+  if (dev != ix->device)
+    return fail(SOFA_ERR_INVALID_ARG, "the current device (" + std::to_string(dev) + ") is not the index's device (" +
+                                          std::to_string(ix->device) + "): make that device current first");
+  return 0;
 }
 
 static int num_candidates_host(int n, int pool) {
@@ -189,7 +223,11 @@ sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, in
     }
     x = owned;
   }
-  int rc = build_index(ix, x, o, st);
+  int rc = 0;
+  {
+    NvtxScope range(ix->prof, "sofa_build");
+    rc = build_index(ix, x, o, st);
+  }
   if (owned) {
     cudaStreamSynchronize(st);
     cudaFree(owned);
@@ -208,6 +246,56 @@ sofa_handle sofa_build(const float* data, int64_t N, int32_t n, int32_t l, int32
   return sofa_build_ex(data, N, n, l, alphabet, nullptr, nullptr);
 }
 
+int sofa_insert(sofa_handle h, const float* data, int64_t N_add, sofa_stream stream) {
+  g_err.clear();
+  if (!h) return fail(SOFA_ERR_INVALID_ARG, "handle is NULL");
+  if (N_add < 0) return fail(SOFA_ERR_INVALID_ARG, "N_add must be >= 0");
+  if (N_add == 0) return 0;
+  if (!data) return fail(SOFA_ERR_INVALID_ARG, "data is NULL");
+  if (h->N + N_add >= ((int64_t)1 << 31)) return fail(SOFA_ERR_INVALID_ARG, "N + N_add must stay below 2^31");
+  if (int rc = check_device(h)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  SOFA_CUDA(cudaStreamSynchronize(st));
+  // the query scratch is regrown on demand: release it to make room for the
+  // grown index
+  Index* ix = h;
+  DevBuf* bufs[] = {&ix->qs.zq, &ix->qs.qv, &ix->qs.qn, &ix->qs.zqh, &ix->qs.llb, &ix->qs.thr, &ix->qs.list_d,
+                    &ix->qs.list_p, &ix->qs.list_n, &ix->qs.leaf_cnt, &ix->qs.leaf_off, &ix->qs.leaf_q,
+                    &ix->qs.leaf_cursor, &ix->qs.unit_off, &ix->qs.units, &ix->qs.cand_p, &ix->qs.cand_lb,
+                    &ix->qs.cand_n, &ix->qs.qflag, &ix->qs.qslot, &ix->qs.qsel, &ix->qs.chunk_d, &ix->qs.chunk_p,
+                    &ix->qs.chunk_n, &ix->qs.pool_q, &ix->qs.pool_p, &ix->qs.pool_lb, &ix->qs.pool_sp,
+                    &ix->qs.pool_slb, &ix->qs.qpool_cnt, &ix->qs.qpool_off, &ix->qs.qcursor, &ix->qs.choff,
+                    &ix->qs.chunk_q, &ix->qs.qof, &ix->qs.stage_in, &ix->qs.stage_out, &ix->qs.graph_in,
+                    &ix->qs.graph_out};
+  for (DevBuf* b : bufs) b->release();
+  ++g_buf_generation;
+  const float* x = data;
+  float* owned = nullptr;
+  if (!is_device_ptr(data)) {
+    cudaError_t e = cudaMalloc(&owned, (size_t)N_add * h->n * sizeof(float));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SOFA_ERR_OOM, "device allocation for the input copy failed; the index is unchanged");
+    }
+    e = cudaMemcpyAsync(owned, data, (size_t)N_add * h->n * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cudaFree(owned);
+      return fail(SOFA_ERR_CUDA, std::string("input copy failed: ") + cudaGetErrorString(e));
+    }
+    x = owned;
+  }
+  int rc = 0;
+  {
+    NvtxScope range(ix->prof, "sofa_insert");
+    rc = insert_rows(h, x, N_add, st);
+  }
+  if (owned) {
+    cudaStreamSynchronize(st);
+    cudaFree(owned);
+  }
+  return rc;
+}
+
 int sofa_query(sofa_handle h, const float* queries, int64_t Q, int32_t k, int64_t* idx, float* dist,
                sofa_stream stream) {
   g_err.clear();
@@ -217,6 +305,7 @@ int sofa_query(sofa_handle h, const float* queries, int64_t Q, int32_t k, int64_
   if (Q == 0) return 0;
   if (!queries || !idx || !dist) return fail(SOFA_ERR_INVALID_ARG, "null pointer argument");
   if (Q > ((int64_t)1 << 31) / std::max(1, h->n)) return fail(SOFA_ERR_INVALID_ARG, "Q too large");
+  if (int rc = check_device(h)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   Index* ix = h;
   const bool qd = is_device_ptr(queries), id = is_device_ptr(idx), dd = is_device_ptr(dist);
@@ -238,6 +327,48 @@ int sofa_query(sofa_handle h, const float* queries, int64_t Q, int32_t k, int64_
   if (!id) SOFA_CUDA(cudaMemcpyAsync(idx, idev, (size_t)Q * k * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   if (!dd) SOFA_CUDA(cudaMemcpyAsync(dist, ddev, (size_t)Q * k * sizeof(float), cudaMemcpyDeviceToHost, st));
   if (!qd || !id || !dd) SOFA_CUDA(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int sofa_query_window(sofa_handle h, const float* queries, int64_t Q, int32_t k, int32_t cap, int64_t* ids,
+                      double* d2, int32_t* counts, sofa_stream stream) {
+  g_err.clear();
+  if (!h) return fail(SOFA_ERR_INVALID_ARG, "handle is NULL");
+  if (Q < 0) return fail(SOFA_ERR_INVALID_ARG, "Q must be >= 0");
+  if (k < 1 || k > SOFA_MAX_K || k > h->N) return fail(SOFA_ERR_INVALID_ARG, "k must lie in [1, min(64, N)]");
+  if (cap < k || cap > SOFA_MAX_WINDOW) return fail(SOFA_ERR_INVALID_ARG, "cap must lie in [k, SOFA_MAX_WINDOW]");
+  if (Q == 0) return 0;
+  if (!queries || !ids || !d2 || !counts) return fail(SOFA_ERR_INVALID_ARG, "null pointer argument");
+  if (Q > ((int64_t)1 << 31) / std::max(1, h->n)) return fail(SOFA_ERR_INVALID_ARG, "Q too large");
+  if (int rc = check_device(h)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  Index* ix = h;
+  const bool qd = is_device_ptr(queries);
+  const bool od = is_device_ptr(ids) && is_device_ptr(d2) && is_device_ptr(counts);
+  const float* qdev = queries;
+  int64_t* idev = ids;
+  double* ddev = d2;
+  int32_t* cdev = counts;
+  const size_t nw = (size_t)Q * cap;
+  if (!qd) {
+    if (int rc = ix->qs.stage_in.ensure((size_t)Q * ix->n * sizeof(float))) return rc;
+    SOFA_CUDA(cudaMemcpyAsync(ix->qs.stage_in.p, queries, (size_t)Q * ix->n * sizeof(float), cudaMemcpyHostToDevice, st));
+    qdev = ix->qs.stage_in.as<float>();
+  }
+  if (!od) {
+    if (int rc = ix->qs.stage_out.ensure(nw * (sizeof(int64_t) + sizeof(double)) + (size_t)Q * sizeof(int32_t)))
+      return rc;
+    idev = ix->qs.stage_out.as<int64_t>();
+    ddev = reinterpret_cast<double*>(idev + nw);
+    cdev = reinterpret_cast<int32_t*>(ddev + nw);
+  }
+  if (int rc = run_query_window(ix, qdev, Q, k, cap, idev, ddev, cdev, st)) return rc;
+  if (!od) {
+    SOFA_CUDA(cudaMemcpyAsync(ids, idev, nw * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SOFA_CUDA(cudaMemcpyAsync(d2, ddev, nw * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SOFA_CUDA(cudaMemcpyAsync(counts, cdev, (size_t)Q * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  }
+  if (!qd || !od) SOFA_CUDA(cudaStreamSynchronize(st));
   return 0;
 }
 
@@ -328,6 +459,7 @@ int sofa_info(sofa_handle h, sofa_info_t* out) {
   out->delta_data = h->delta_d;
   out->delta_query = h->delta_q;
   out->device_bytes = h->device_bytes;
+  out->appended = h->N - h->Ns;
   mlp_report(h, &out->proposal_loss, &out->proposal_top1, &out->proposal_topm, &out->proposal_classes,
              &out->proposal_train);
   return 0;
@@ -362,6 +494,7 @@ int sofa_lower_bounds(sofa_handle h, const float* queries, int64_t Q, float* out
   if (!h || !queries || !out) return fail(SOFA_ERR_INVALID_ARG, "null argument");
   if (Q <= 0) return Q == 0 ? 0 : fail(SOFA_ERR_INVALID_ARG, "Q must be >= 0");
   if (!is_device_ptr(queries) || !is_device_ptr(out)) return fail(SOFA_ERR_INVALID_ARG, "device pointers required");
+  if (int rc = check_device(h)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if (int rc = h->qs.zq.ensure((size_t)Q * h->n * sizeof(float))) return rc;
   if (int rc = h->qs.qv.ensure((size_t)Q * h->NB * sizeof(float))) return rc;

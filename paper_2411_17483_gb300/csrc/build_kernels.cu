@@ -948,7 +948,7 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
 
   // ---- squared norms of the canonical series (dense path)
   TRY(dalloc(&ix->xn, N, acct));
-  TRY(launch_row_norms(ix, st));
+  TRY(launch_row_norms(ix->Z, N, n, ix->xn, st));
 
   // ---- envelopes
   ix->T = ceil_div(N, TILE);
@@ -963,6 +963,241 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
                                                                          ix->lenv);
   SOFA_CUDA(cudaGetLastError());
   SOFA_CUDA(cudaStreamSynchronize(st));
+  ix->Ns = N;
+  return 0;
+}
+
+// ========================================================================
+// Incremental insert (Sec. IV "Structure": the index takes new series; the
+// paper's tree inserts each into the leaf of its word and splits full
+// leaves).  Here the new series are summarised with the index's learned
+// summary (Alg. 2, no relearning of selection or bins), then merged by layout
+// key into the appended region [Ns, N): a second key-sorted run after the
+// build's.  Both runs are cut into tiles and leaf blocks like the build's
+// layout, so the scan, the routing and the refinement cover every row
+// unchanged, and the seed searches each run by key.
+// ========================================================================
+
+// Rows j = 0..R-1 of dst (row_bytes each): row src_idx[j] of the sequence
+// "rows [0, n_old) of old, then rows of fresh".  Warp per row, 4-byte words
+// when the row size allows.
+__global__ void k_gather_rows2(const uint8_t* __restrict__ old, int64_t n_old, const uint8_t* __restrict__ fresh,
+                               const uint32_t* __restrict__ src_idx, int64_t R, int row_bytes,
+                               uint8_t* __restrict__ dst) {
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= R) return;
+  const int64_t s = src_idx[j];
+  const uint8_t* src = s < n_old ? old + s * row_bytes : fresh + (s - n_old) * row_bytes;
+  uint8_t* d = dst + j * row_bytes;
+  if ((row_bytes & 3) == 0) {
+    const uint32_t* s4 = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d4 = reinterpret_cast<uint32_t*>(d);
+    for (int i = lane; i < row_bytes / 4; i += 32) d4[i] = s4[i];
+  } else {
+    for (int i = lane; i < row_bytes; i += 32) d[i] = src[i];
+  }
+}
+
+// Original row ids of an inserted batch: base + batch row.
+__global__ void k_ids_from(uint32_t* __restrict__ ids, int64_t A, int64_t base) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < A) ids[i] = (uint32_t)(base + i);
+}
+
+// One per-row array of the index and its grown replacement: rows [0, Ns)
+// copied, rows [Ns, N_old + A) gathered by src_idx from the old appended
+// region (indices < N_old - Ns) and the batch rows `fresh`.
+struct Grow {
+  void** arr;
+  int row_bytes;
+  const void* fresh;
+  uint8_t* nw;
+};
+
+static void launch_grow(const Grow& g, int64_t N_old, int64_t Ns, int64_t A, const uint32_t* src_idx,
+                        cudaStream_t st) {
+  const uint8_t* od = static_cast<const uint8_t*>(*g.arr);
+  const int64_t rb = g.row_bytes;
+  if (Ns > 0) cudaMemcpyAsync(g.nw, od, (size_t)(Ns * rb), cudaMemcpyDeviceToDevice, st);
+  const int64_t R = N_old - Ns + A;
+  k_gather_rows2<<<(unsigned)ceil_div(R * 32, 256), 256, 0, st>>>(od + Ns * rb, N_old - Ns,
+                                                                   static_cast<const uint8_t*>(g.fresh), src_idx, R,
+                                                                   g.row_bytes, g.nw + Ns * rb);
+}
+
+int insert_rows(Index* ix, const float* x, int64_t A, cudaStream_t st) {
+  const int64_t N_old = ix->N, Ns = ix->Ns, R_old = N_old - Ns, N_new = N_old + A;
+  const int n = ix->n, l = ix->l, alpha = ix->alpha, LW = ix->LW, NB = ix->NB;
+  Tmp tmp;
+  int64_t* acct = &ix->device_bytes;
+  const size_t row_smem = (size_t)ROWS * (n + 1) * sizeof(float);
+
+  // ---- Alg. 2 on the batch with the index's summary: words, keys, statistics
+  uint8_t* words_b;
+  uint64_t* keys_b;
+  uint32_t* rows_b;
+  double2* stats;
+  TRY(tmp.get(&words_b, A * LW));
+  TRY(tmp.get(&keys_b, A));
+  TRY(tmp.get(&rows_b, A));
+  TRY(tmp.get(&stats, A));
+  const size_t wsmem = row_smem + (size_t)LW * (alpha + 1) * sizeof(float);
+  if (LW == 16) {
+    SOFA_CUDA(cudaFuncSetAttribute(k_words<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
+    k_words<16><<<(unsigned)ceil_div(A, ROWS), ROWS, wsmem, st>>>(x, A, n, ix->basis, NB, ix->beta, alpha, l,
+                                                                   ix->keyorder, ix->keybits, words_b, keys_b,
+                                                                   rows_b, stats);
+  } else {
+    SOFA_CUDA(cudaFuncSetAttribute(k_words<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
+    k_words<32><<<(unsigned)ceil_div(A, ROWS), ROWS, wsmem, st>>>(x, A, n, ix->basis, NB, ix->beta, alpha, l,
+                                                                   ix->keyorder, ix->keybits, words_b, keys_b,
+                                                                   rows_b, stats);
+  }
+  SOFA_CUDA(cudaGetLastError());
+
+  // ---- the batch's per-row arrays in batch order (rows_b is the identity)
+  float* Zb;
+  uint8_t* Wb;
+  TRY(tmp.get(&Zb, A * n));
+  TRY(tmp.get(&Wb, A * LW));
+  if (LW == 16)
+    k_layout<16><<<(unsigned)ceil_div(A * 32, 256), 256, 0, st>>>(x, A, n, rows_b, stats, words_b, Zb, Wb);
+  else
+    k_layout<32><<<(unsigned)ceil_div(A * 32, 256), 256, 0, st>>>(x, A, n, rows_b, stats, words_b, Zb, Wb);
+  SOFA_CUDA(cudaGetLastError());
+  int8_t *Z8b = nullptr, *VCb = nullptr;
+  float *s8b = nullptr, *e8b = nullptr, *xnb = nullptr;
+  float2* vsrb = nullptr;
+  __half* Zhb = nullptr;
+  if (ix->Z8) {
+    TRY(tmp.get(&Z8b, A * n));
+    TRY(tmp.get(&s8b, A));
+    TRY(tmp.get(&e8b, A));
+    k_quant8<<<(unsigned)ceil_div(A * 32, 256), 256, 0, st>>>(Zb, A, n, Z8b, s8b, e8b);
+    SOFA_CUDA(cudaGetLastError());
+  }
+  if (ix->VC) {
+    TRY(tmp.get(&VCb, A * NB));
+    TRY(tmp.get(&vsrb, A));
+    const float dmargin = std::nextafter(
+        (float)(std::sqrt(2.0 * ix->nsel) * (ix->delta_d + ix->delta_q) * 1.0001), INFINITY);
+    if (NB == 32) {
+      SOFA_CUDA(cudaFuncSetAttribute(k_quantv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
+      k_quantv<32><<<(unsigned)ceil_div(A, ROWS), ROWS, row_smem, st>>>(Zb, A, n, ix->basis, ix->vw, dmargin, VCb,
+                                                                        vsrb);
+    } else {
+      SOFA_CUDA(cudaFuncSetAttribute(k_quantv<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
+      k_quantv<64><<<(unsigned)ceil_div(A, ROWS), ROWS, row_smem, st>>>(Zb, A, n, ix->basis, ix->vw, dmargin, VCb,
+                                                                        vsrb);
+    }
+    SOFA_CUDA(cudaGetLastError());
+  }
+  if (ix->Zh) {
+    TRY(tmp.get(&Zhb, A * n));
+    k_to_half<<<(unsigned)ceil_div(A * n, 1024), 256, 0, st>>>(Zb, A * n, Zhb);
+    SOFA_CUDA(cudaGetLastError());
+  }
+  TRY(tmp.get(&xnb, A));
+  TRY(launch_row_norms(Zb, A, n, xnb, st));
+  uint32_t* idb;
+  TRY(tmp.get(&idb, A));
+  k_ids_from<<<(unsigned)ceil_div(A, 256), 256, 0, st>>>(idb, A, N_old);
+  SOFA_CUDA(cudaGetLastError());
+
+  // ---- merge the appended region's keys with the batch's: one key sort of
+  // both, carrying each row's source index (region rows first, then batch)
+  const int64_t R = R_old + A;
+  uint64_t *kin, *kout;
+  uint32_t *vin, *vout;
+  TRY(tmp.get(&kin, R));
+  TRY(tmp.get(&kout, R));
+  TRY(tmp.get(&vin, R));
+  TRY(tmp.get(&vout, R));
+  if (R_old > 0)
+    SOFA_CUDA(cudaMemcpyAsync(kin, ix->keys + Ns, (size_t)R_old * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+  SOFA_CUDA(cudaMemcpyAsync(kin + R_old, keys_b, (size_t)A * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+  k_iota<<<(unsigned)ceil_div(R, 256), 256, 0, st>>>(vin, R);
+  SOFA_CUDA(cudaGetLastError());
+  {
+    size_t tb = 0;
+    const int begin_bit = 64 - std::min(64, ix->keybits);
+    SOFA_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, kin, kout, vin, vout, R, begin_bit, 64, st));
+    char* tstore;
+    TRY(tmp.get(&tstore, (int64_t)tb));
+    SOFA_CUDA(cub::DeviceRadixSort::SortPairs(tstore, tb, kin, kout, vin, vout, R, begin_bit, 64, st));
+  }
+
+  // ---- every per-row array grows by A rows, its region merged in key order.
+  // All grown arrays (and the new envelopes) are allocated before any is
+  // written, and the old ones are freed only once every copy is done: an
+  // allocation failure leaves the index as it was.
+  std::vector<Grow> grows = {{(void**)&ix->Z, n * (int)sizeof(float), Zb, nullptr},
+                             {(void**)&ix->words, LW, Wb, nullptr},
+                             {(void**)&ix->perm, (int)sizeof(uint32_t), idb, nullptr},
+                             {(void**)&ix->keys, (int)sizeof(uint64_t), keys_b, nullptr},
+                             {(void**)&ix->xn, (int)sizeof(float), xnb, nullptr}};
+  if (ix->Z8) {
+    grows.push_back({(void**)&ix->Z8, n, Z8b, nullptr});
+    grows.push_back({(void**)&ix->s8, (int)sizeof(float), s8b, nullptr});
+    grows.push_back({(void**)&ix->e8, (int)sizeof(float), e8b, nullptr});
+  }
+  if (ix->VC) {
+    grows.push_back({(void**)&ix->VC, NB, VCb, nullptr});
+    grows.push_back({(void**)&ix->vsr, (int)sizeof(float2), vsrb, nullptr});
+  }
+  if (ix->Zh) grows.push_back({(void**)&ix->Zh, n * (int)sizeof(__half), Zhb, nullptr});
+  const int64_t T = ceil_div(N_new, TILE), L = ceil_div(T, ix->leaf_tiles);
+  uint8_t *tenv = nullptr, *lenv = nullptr;
+  auto release_new = [&]() {
+    for (Grow& g : grows)
+      if (g.nw) cudaFree(g.nw);
+    if (tenv) cudaFree(tenv);
+    if (lenv) cudaFree(lenv);
+  };
+  int rc = 0;
+  for (Grow& g : grows) {
+    rc = dalloc(&g.nw, N_new * (int64_t)g.row_bytes, nullptr);
+    if (rc) break;
+  }
+  if (!rc) rc = dalloc(&tenv, T * 2 * LW, nullptr);
+  if (!rc) rc = dalloc(&lenv, L * 2 * LW, nullptr);
+  if (rc) {
+    release_new();
+    return fail(SOFA_ERR_OOM, "sofa_insert: no room on the device for the grown index (the old and the grown "
+                              "arrays are held together while the rows are merged); the index is unchanged");
+  }
+  for (const Grow& g : grows) launch_grow(g, N_old, Ns, A, vout, st);
+  uint8_t* words_new = nullptr;
+  for (const Grow& g : grows)
+    if (g.arr == (void**)&ix->words) words_new = g.nw;
+  if (LW == 16)
+    k_tile_env<16><<<(unsigned)T, TILE, 0, st>>>(words_new, N_new, tenv);
+  else
+    k_tile_env<32><<<(unsigned)T, TILE, 0, st>>>(words_new, N_new, tenv);
+  k_leaf_env<<<(unsigned)ceil_div(L * (LW / 4), 256), 256, 0, st>>>(tenv, T, LW, ix->leaf_tiles, L, lenv);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    release_new();
+    return fail(SOFA_ERR_CUDA, std::string("sofa_insert: ") + cudaGetErrorString(e));
+  }
+  // commit: the grown arrays replace the old ones
+  for (Grow& g : grows) {
+    cudaFree(*g.arr);
+    *g.arr = g.nw;
+    g.nw = nullptr;
+    *acct += A * (int64_t)g.row_bytes;
+  }
+  cudaFree(ix->tenv);
+  cudaFree(ix->lenv);
+  *acct += (T - ix->T) * 2 * LW + (L - ix->L) * 2 * LW;
+  ix->tenv = tenv;
+  ix->lenv = lenv;
+  ix->N = N_new;
+  ix->T = T;
+  ix->L = L;
+  ++g_buf_generation;  // recorded query graphs hold the old array addresses
   return 0;
 }
 

@@ -24,6 +24,7 @@
 #include <cstring>
 
 #include "sofa_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace sofa {
 
@@ -36,7 +37,6 @@ constexpr int B_BYTES = DN * DK * 4;     // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int DENSE_SMEM = DSTAGES * STAGE_BYTES + 1024;  // + alignment slack
 constexpr int DKMAX = 16;                // largest k of the dense path
-constexpr unsigned long long WAIT_NS = 2000000000ull;     // bounded waits: 2 s
 
 // Instruction descriptor of tcgen05.mma kind::tf32 / kind::f16: D fp32
 // (bits 4-5 = 1), A and B tf32 (bits 7-9, 10-12 = 2) or f16 (= 0), both
@@ -59,61 +59,6 @@ struct DenseParams {
   float f_half;        // f_prune / 2: threshold of a real k-th squared distance
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Wait for the completion of the phase with the given parity; false when the
-// wait ran out (2 s).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  const unsigned long long t0 = global_ns();
-  for (uint32_t it = 0;; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 63) == 63 && global_ns() - t0 > WAIT_NS) return false;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
-// swizzled layout TMA writes: rows of 128 bytes, 8-row atoms of 1024 bytes
-// (stride byte offset), descriptor version 1, layout type 2 (128B swizzle).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;            // leading byte offset: unused for swizzled K-major tiles
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
-  return d;
-}
 
 // One MMA of K = 32 bytes of each operand row (8 tf32 or 16 f16 values).
 template <bool F16>
@@ -132,43 +77,9 @@ __device__ __forceinline__ void mma_dense(uint32_t d_tmem, uint64_t adesc, uint6
         "l"(adesc), "l"(bdesc), "r"(dense_idesc<false>()), "r"(accumulate));
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
 
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 consecutive fp32 columns of this thread's TMEM lane (load and wait in
-// one statement: no use of the outputs can be scheduled before the wait).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {  // whole warp
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // whole warp
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// ||x||^2 of every canonical series: left-to-right FP64 sum, rounded to fp32.
+// ||x||^2 of every canonical series: FP64 sum (lane-strided partial sums,
+// then a warp reduction), rounded to fp32.
 __global__ void k_row_norms(const float* __restrict__ Z, int64_t N, int n, float* __restrict__ out) {
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -203,9 +114,6 @@ __device__ __forceinline__ float topk_kth(const float* top, int k) {
   return v;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Warp-specialised CTA of 6 warps: warp 0 issues the TMA loads, warp 1 the
 // MMAs (and owns the tensor memory: two 256-column accumulators, so the
@@ -481,6 +389,27 @@ static EncodeTiled encode_fn() {
   return fn;
 }
 
+int make_tensor_map_2d(CUtensorMap* m, const void* base, int64_t rows, int cols, int elem_bytes, int box_cols,
+                       int box_rows, int swizzle_bytes) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return fail(SOFA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * (cuuint64_t)elem_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                                      : CU_TENSOR_MAP_SWIZZLE_NONE;
+  CUresult r = fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SOFA_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return 0;
+}
+
 // 2-d map of a row-major matrix (rows x n) of fp32 or fp16 values, boxes of
 // one 128-byte row (32 fp32 or 64 fp16 values) x box_rows, 128-byte swizzle;
 // elements outside the matrix read as zero.
@@ -550,8 +479,9 @@ __global__ void k_qnorms(const float* __restrict__ zq, int Q, int n, float* __re
   if (lane == 0) out[row] = (float)s;
 }
 
-int launch_row_norms(Index* ix, cudaStream_t st) {
-  k_row_norms<<<(unsigned)ceil_div(ix->N * 32, 256), 256, 0, st>>>(ix->Z, ix->N, ix->n, ix->xn);
+int launch_row_norms(const float* Z, int64_t N, int n, float* xn, cudaStream_t st) {
+  if (N <= 0) return 0;
+  k_row_norms<<<(unsigned)ceil_div(N * 32, 256), 256, 0, st>>>(Z, N, n, xn);
   SOFA_CUDA(cudaGetLastError());
   return 0;
 }
@@ -621,12 +551,9 @@ extern "C" int sofa_dense_sqdist(sofa_handle h, const float* queries, int64_t Q,
   if (Q * h->N > ((int64_t)1 << 31)) return fail(SOFA_ERR_INVALID_ARG, "Q * N must be <= 2^31");
   if (!dense_supported(h, 1))
     return fail(SOFA_ERR_INVALID_ARG, "the dense contraction needs n % 4 == 0 (n % 8 == 0 with FP16 operands)");
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, queries) != cudaSuccess || a.type != cudaMemoryTypeDevice ||
-      cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
-    cudaGetLastError();
+  if (!is_device_ptr(queries) || !is_device_ptr(out))
     return fail(SOFA_ERR_INVALID_ARG, "queries and out must be device memory");
-  }
+  if (int rc = check_device(h)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   QueryScratch& s = h->qs;
   TRYD(s.zq.ensure((size_t)Q * h->n * sizeof(float)));

@@ -714,6 +714,7 @@ extern "C" int sofa_train_proposal(sofa_handle h, const sofa_train_opts* o, sofa
     return fail(SOFA_ERR_INVALID_ARG, "bad training options");
   if (o->n_classes > 0 && o->n_classes > h->N) return fail(SOFA_ERR_INVALID_ARG, "more classes than series");
   if (o->n_classes == 0 && h->N < 4096) return fail(SOFA_ERR_INVALID_ARG, "n_classes must be set when N < 4096");
+  if (int rc = check_device(h)) return rc;
   return mlp_train(h, *o, (cudaStream_t)stream);
 }
 

@@ -8,12 +8,13 @@
 
 namespace sofa {
 
+// One CTA per gathered row (R < 2^31 rows on gridDim.x).
 __global__ void k_gather_rows(const float* __restrict__ src, const int64_t* __restrict__ offs,
                               const int32_t* __restrict__ sel, int64_t R, int n, float* __restrict__ dst) {
-  int64_t r = blockIdx.y;
+  const int64_t r = blockIdx.x;
   if (r >= R) return;
   const float* s = src + offs[sel[r]];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) dst[r * n + t] = s[t];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) dst[r * n + t] = s[t];
 }
 
 __global__ void k_scatter_out(const int64_t* __restrict__ gi, const float* __restrict__ gd, int64_t R, int k,
@@ -28,14 +29,7 @@ __global__ void k_scatter_out(const int64_t* __restrict__ gi, const float* __res
   dist[o] = gd[e];
 }
 
-static bool dev_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+static bool dev_ptr(const void* p) { return is_device_ptr(p); }
 
 template <class T>
 static int to_host(const T* p, int64_t count, std::vector<T>& out) {
@@ -64,6 +58,9 @@ extern "C" int sofa_query_multi(const sofa_handle* hs, int32_t nh, const float* 
   if (Q == 0) return 0;
   if (!queries || !q_offsets || !q_len || !q_k || !idx || !dist || !out_offsets)
     return fail(SOFA_ERR_INVALID_ARG, "null pointer argument");
+  for (int j = 0; j < nh; ++j)
+    if (hs[j])
+      if (int rc = check_device(hs[j])) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int64_t> off, oo;
   std::vector<int32_t> len, kk;
@@ -127,8 +124,7 @@ extern "C" int sofa_query_multi(const sofa_handle* hs, int32_t nh, const float* 
     const int k = g.first.second;
     const int64_t R = (int64_t)g.second.size();
     const int32_t* sel = (const int32_t*)dsel.p + base;
-    dim3 gg((unsigned)std::min<int64_t>(ceil_div(ix->n, 256), 4), (unsigned)R);
-    k_gather_rows<<<gg, 256, 0, st>>>(qdev, (const int64_t*)doff.p, sel, R, ix->n, (float*)dgq.p);
+    k_gather_rows<<<(unsigned)R, 256, 0, st>>>(qdev, (const int64_t*)doff.p, sel, R, ix->n, (float*)dgq.p);
     SOFA_CUDA(cudaGetLastError());
     if (int rc = run_query(ix, (const float*)dgq.p, R, k, (int64_t*)dgi.p, (float*)dgd.p, st)) return rc;
     k_scatter_out<<<(unsigned)ceil_div(R * k, 256), 256, 0, st>>>((const int64_t*)dgi.p, (const float*)dgd.p, R, k,

@@ -26,12 +26,10 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static float* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 static std::mutex g_noalloc_mutex;
 
-// Device address of the work space on the current device.  The name of the
-// array is only a host-side stand-in; the address must come from the runtime,
-// once per device, with that device current.
-static int noalloc_scratch(float** out) {
-  int dev = 0;
-  SOFA_CUDA(cudaGetDevice(&dev));
+// Device address of the work space on device `dev`, which must be the current
+// device.  The name of the array is only a host-side stand-in; the address must
+// come from the runtime, once per device, with that device current.
+static int noalloc_scratch(int dev, float** out) {
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(SOFA_ERR_INVALID_ARG, "device index out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_ptr[dev]) {
@@ -60,17 +58,14 @@ extern "C" int sofa_lower_bounds_noalloc(sofa_handle h, const float* queries, in
     return fail(SOFA_ERR_INVALID_ARG, "Q = " + std::to_string(Q) + " exceeds the allocation-free work space: at most " +
                                           std::to_string(NOALLOC_FLOATS / per_query) + " queries of length " +
                                           std::to_string(h->n) + " per call");
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, queries) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
-    cudaGetLastError();
-    return fail(SOFA_ERR_INVALID_ARG, "queries must be device memory");
-  }
-  if (cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
-    cudaGetLastError();
-    return fail(SOFA_ERR_INVALID_ARG, "out must be device memory");
-  }
+  if (!is_device_ptr(queries)) return fail(SOFA_ERR_INVALID_ARG, "queries must be device memory");
+  if (!is_device_ptr(out)) return fail(SOFA_ERR_INVALID_ARG, "out must be device memory");
+  // the work space is looked up for the current device, and the index's
+  // buffers live on the device it was built on: the two must agree, or the
+  // kernels would mix addresses of two GPUs
+  if (int rc = check_device(h)) return rc;
   float* ws = nullptr;
-  if (int rc = noalloc_scratch(&ws)) return rc;
+  if (int rc = noalloc_scratch(h->device, &ws)) return rc;
   // Every entry the kernels read is written first in this call (series, then
   // values), so nothing needs clearing between calls.
   float* zq = ws;

@@ -2,7 +2,9 @@
 // trained proposal network) to one file; sofa_load recreates the handle on the
 // current device from it, without the raw data or any of the build's work.
 //
-// File: the 8-byte magic "SOFAIDX2", a fixed header of 64-bit fields, then one
+// File: the 8-byte magic "SOFAIDX3", a fixed header of 64-bit fields, the
+// size of the build's key-sorted run (rows beyond it are the appended region
+// of sofa_insert; a "SOFAIDX2" file has no such field and no region), then one
 // section per array -- a 64-bit byte count followed by the bytes, in a fixed
 // order (optional arrays have count 0 when absent) -- then the proposal
 // network.  Arrays move between device and file through a pinned staging
@@ -20,7 +22,8 @@ void set_error(const std::string& msg);
 
 namespace {
 
-constexpr char MAGIC[8] = {'S', 'O', 'F', 'A', 'I', 'D', 'X', '2'};
+constexpr char MAGIC[8] = {'S', 'O', 'F', 'A', 'I', 'D', 'X', '3'};
+constexpr char MAGIC_V2[8] = {'S', 'O', 'F', 'A', 'I', 'D', 'X', '2'};
 constexpr size_t PIECE = (size_t)64 << 20;
 
 struct Header {
@@ -127,7 +130,8 @@ int save_index(const Index* ix, FILE* f) {
   h.vmax = ix->vmax;
   h.outer = ix->outer;
   h.has_mlp = ix->mlp ? 1 : 0;
-  if (fwrite(MAGIC, 1, 8, f) != 8 || fwrite(&h, sizeof(h), 1, f) != 1)
+  const int64_t Ns = ix->Ns;
+  if (fwrite(MAGIC, 1, 8, f) != 8 || fwrite(&h, sizeof(h), 1, f) != 1 || fwrite(&Ns, sizeof(Ns), 1, f) != 1)
     return fail(SOFA_ERR_INVALID_ARG, "write failed");
   const Sizes z = sizes_of(ix);
   Staging sg;
@@ -150,15 +154,20 @@ int save_index(const Index* ix, FILE* f) {
 int load_index(Index* ix, FILE* f, cudaStream_t st) {
   char magic[8];
   Header h;
-  if (fread(magic, 1, 8, f) != 8 || std::memcmp(magic, MAGIC, 8) != 0)
-    return fail(SOFA_ERR_INVALID_ARG, "not an index file");
+  if (fread(magic, 1, 8, f) != 8) return fail(SOFA_ERR_INVALID_ARG, "not an index file");
+  const bool v3 = std::memcmp(magic, MAGIC, 8) == 0;
+  if (!v3 && std::memcmp(magic, MAGIC_V2, 8) != 0) return fail(SOFA_ERR_INVALID_ARG, "not an index file");
   if (fread(&h, sizeof(h), 1, f) != 1) return fail(SOFA_ERR_INVALID_ARG, "truncated index file");
+  int64_t Ns = h.N;
+  if (v3 && fread(&Ns, sizeof(Ns), 1, f) != 1) return fail(SOFA_ERR_INVALID_ARG, "truncated index file");
+  if (Ns < 1 || Ns > h.N) return fail(SOFA_ERR_INVALID_ARG, "index file header is inconsistent");
   if (h.N < 1 || h.N >= ((int64_t)1 << 31) || h.n < 4 || h.n > 1024 || (h.LW != 16 && h.LW != 32) ||
       h.NB != 2 * h.LW || h.nsel < 1 || h.nsel > 2 * h.LW || h.alpha < 2 || h.alpha > 256 || h.keybits < 0 ||
       h.keybits > 64 || h.leaf_tiles < 1 || h.leaf_tiles > 256 || h.T != ceil_div(h.N, TILE) ||
       h.L != ceil_div(h.T, h.leaf_tiles))
     return fail(SOFA_ERR_INVALID_ARG, "index file header is inconsistent");
   ix->N = h.N;
+  ix->Ns = Ns;
   ix->n = (int)h.n;
   ix->l = (int)h.l;
   ix->alpha = (int)h.alpha;

@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "sofa_internal.cuh"
+#include "bounds.cuh"
 
 namespace sofa {
 
@@ -22,58 +23,11 @@ constexpr int SEED_TL = 512;     // tiles of a predicted block examined per pass
 
 struct QueryParams {
   int64_t N, T, L;
+  int64_t Ns;     // rows of the build's key-sorted run; [Ns, N) is the appended run
   int n, NB, leaf_tiles, k, cap, group, seed_count, seed_window;
   float f_prune;  // threshold = d2_kth * f_prune / 2 (half units)
   float f_keep;   // kept list: d2 <= d2_kth * f_keep
 };
-
-// Envelope bound (leaf block or tile): per value j the interval spanned by
-// symbols lo_j..hi_j, i.e. [edge(lo_j).lo, edge(hi_j).hi].
-template <int LW, bool NYQ>
-__device__ __forceinline__ float env_bound(const uint8_t* __restrict__ env, const float* q,
-                                           const float2* __restrict__ edge) {
-  const uint32_t* e32 = reinterpret_cast<const uint32_t*>(env);
-  float acc = 0.f;
-#pragma unroll
-  for (int w = 0; w < LW / 4; ++w) {
-    uint32_t lo = e32[w], hi = e32[LW / 4 + w];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = 4 * w + b;
-      float elo = edge[j * MAX_ALPHA + ((lo >> (8 * b)) & 0xFFu)].x;
-      float ehi = edge[j * MAX_ALPHA + ((hi >> (8 * b)) & 0xFFu)].y;
-      float m = fmaxf(fmaxf(elo - q[j], q[j] - ehi), 0.f);
-      float mm = (NYQ && j == 0) ? 0.5f * m : m;
-      acc = fmaf(mm, m, acc);
-    }
-  }
-  return acc;
-}
-
-// Envelope bound from the (centre, half-width) table: the interval of
-// symbols lo_j..hi_j is contained in [c(lo) - h(lo), c(hi) + h(hi)], both ends
-// rounded outward (a hair looser than the edge table, never tighter).
-template <int LW, bool NYQ>
-__device__ __forceinline__ float env_bound_ch(const uint8_t* __restrict__ env, const float* q,
-                                              const float2* __restrict__ chs) {
-  const uint32_t* e32 = reinterpret_cast<const uint32_t*>(env);
-  float acc = 0.f;
-#pragma unroll
-  for (int w = 0; w < LW / 4; ++w) {
-    uint32_t lo = e32[w], hi = e32[LW / 4 + w];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = 4 * w + b;
-      const float2 vl = chs[j * MAX_ALPHA + ((lo >> (8 * b)) & 0xFFu)];
-      const float2 vh = chs[j * MAX_ALPHA + ((hi >> (8 * b)) & 0xFFu)];
-      const float elo = __fsub_rd(vl.x, vl.y), ehi = __fadd_ru(vh.x, vh.y);
-      float m = fmaxf(fmaxf(elo - q[j], q[j] - ehi), 0.f);
-      float mm = (NYQ && j == 0) ? 0.5f * m : m;
-      acc = fmaf(mm, m, acc);
-    }
-  }
-  return acc;
-}
 
 // Series bound from a word: m_j = max(|q_j - c_j| - h_j, 0) with (c, h) the
 // symbol's widened interval as centre / half-width.
@@ -291,44 +245,64 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
       key |= (uint64_t)((qsym[d] >> bb) & 1u) << (63 - t);
     }
     s_qkey = key;
-    s_lo = 0;
-    s_hi = P.N;
   }
-  __syncthreads();
-  // 256-ary search for the first position a whose key is >= the query's key.
-  // Invariant: keys[p] < qkey for p < lo, keys[p] >= qkey for p >= hi.  Each
-  // round probes lo + span*t/256; the probes below the key form a prefix of m,
-  // so a lies in [probe m-1 + 1, probe m]; lo grows by >= 1 or hi becomes lo.
-  for (int it = 0; it < 64; ++it) {
-    const int64_t lo = s_lo, hi = s_hi;
-    if (hi <= lo) break;
-    const int64_t span = hi - lo;
-    if (tid == 0) s_less = 0;
-    __syncthreads();
-    const int64_t pos = lo + (span * tid) / 256;
-    if (keys[pos] < s_qkey) atomicAdd(&s_less, 1);
-    __syncthreads();
+  // The layout holds one or two key-sorted runs: the build's [0, Ns) and the
+  // rows added since, [Ns, N).  In each, a 256-ary search finds the first
+  // position a whose key is >= the query's key.  Invariant: keys[p] < qkey for
+  // p < lo, keys[p] >= qkey for p >= hi.  Each round probes lo + span*t/256;
+  // the probes below the key form a prefix of m, so a lies in
+  // [probe m-1 + 1, probe m]; lo grows by >= 1 or hi becomes lo.
+  int64_t ins[2] = {0, P.Ns};
+  for (int run = 0; run < 2; ++run) {
+    const int64_t r_lo = run == 0 ? 0 : P.Ns, r_hi = run == 0 ? P.Ns : P.N;
+    if (r_hi <= r_lo) continue;
     if (tid == 0) {
-      const int m = s_less;
-      if (m == 0) {
-        s_hi = lo;
-      } else {
-        s_lo = lo + (span * (m - 1)) / 256 + 1;
-        if (m < 256) s_hi = lo + (span * m) / 256;
-      }
+      s_lo = r_lo;
+      s_hi = r_hi;
     }
     __syncthreads();
+    for (int it = 0; it < 64; ++it) {
+      const int64_t lo = s_lo, hi = s_hi;
+      if (hi <= lo) break;
+      const int64_t span = hi - lo;
+      if (tid == 0) s_less = 0;
+      __syncthreads();
+      const int64_t pos = lo + (span * tid) / 256;
+      if (keys[pos] < s_qkey) atomicAdd(&s_less, 1);
+      __syncthreads();
+      if (tid == 0) {
+        const int m = s_less;
+        if (m == 0) {
+          s_hi = lo;
+        } else {
+          s_lo = lo + (span * (m - 1)) / 256 + 1;
+          if (m < 256) s_hi = lo + (span * m) / 256;
+        }
+      }
+      __syncthreads();
+    }
+    ins[run] = s_lo;
+    __syncthreads();
   }
+  // the key window: W consecutive positions around each insertion point, at
+  // most half of them in the appended run while the build's run has room
   const int64_t W = P.N < P.seed_window ? P.N : P.seed_window;
-  int64_t p0 = s_lo - W / 2;
-  if (p0 > P.N - W) p0 = P.N - W;
-  if (p0 < 0) p0 = 0;
+  const int64_t na = P.Ns, nb = P.N - P.Ns;
+  int64_t Wb = nb < W / 2 ? nb : W / 2;
+  const int64_t Wa = na < W - Wb ? na : W - Wb;
+  if (Wa + Wb < W) Wb = nb < W - Wa ? nb : W - Wa;
+  int64_t p0a = ins[0] - Wa / 2;
+  if (p0a > na - Wa) p0a = na - Wa;
+  if (p0a < 0) p0a = 0;
+  int64_t p0b = ins[1] - Wb / 2;
+  if (p0b > P.N - Wb) p0b = P.N - Wb;
+  if (p0b < P.Ns) p0b = P.Ns;
 
   // (3) series bounds of the key window; its seed_count smallest are the
   // approximate answer's candidates
   for (int i = tid; i < P.seed_window; i += blockDim.x) {
-    const int64_t p = p0 + i;
-    const bool valid = i < W;
+    const int64_t p = i < Wa ? p0a + i : p0b + (i - Wa);
+    const bool valid = i < Wa + Wb;
     float c[LW], h[LW];
     load_word_bounds<LW>(words, p, valid, ch, c, h);
     skey[i] = valid ? pack_key(word_bound<LW, NYQ>(c, h, sq), (uint32_t)p) : ~0ull;
@@ -1446,6 +1420,88 @@ __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __res
   }
 }
 
+// A query's k-NN window for a merge across shards: its kept list re-scored
+// with the oracle's FP64 left-to-right sum of squared differences, sorted by
+// (distance, id), and cut to the rows whose distance d satisfies
+// d <= D_k + 1e-6 D_k (D_k the k-th smallest): every row that can take one of
+// the first k places of the tie rule in any union of shards (the global k-th
+// distance is at most this shard's).  The kept list holds that window (it
+// keeps every entry within the tie window of the k-th, with margin).
+// Outputs: ids (original row ids), d2 (FP64 squared distances), -1 / +inf
+// beyond the window; cnt the window size (at most cap: a larger window is
+// cut and flagged with SOFA_ERR_TIE_OVERFLOW).
+__global__ void __launch_bounds__(128) k_window(QueryParams P, const float* __restrict__ zq,
+                                                const float* __restrict__ Z, const uint32_t* __restrict__ perm,
+                                                const uint32_t* __restrict__ list_p, const int* __restrict__ list_n,
+                                                int cap, int64_t* __restrict__ ids, double* __restrict__ d2,
+                                                int* __restrict__ cnt, int* __restrict__ status) {
+  extern __shared__ float dsm[];
+  float* szq = dsm;
+  __shared__ double sd[128], sq2[128];
+  __shared__ uint32_t sid[128];
+  __shared__ int s_cnt;
+  const int64_t q = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int nl = list_n[q];
+  for (int t = tid; t < P.n; t += blockDim.x) szq[t] = zq[q * P.n + t];
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+  double d = INFINITY, a2 = INFINITY;
+  uint32_t id = 0xFFFFFFFFu;
+  const uint32_t p = tid < nl ? list_p[q * KCAP + tid] : 0u;
+  if (tid < nl && p >= P.N) atomicExch(status, SOFA_ERR_INTERNAL);  // consistency check: skip the row
+  if (tid < nl && p < P.N) {
+    const float* row = Z + (int64_t)p * P.n;
+    double acc = 0.0;
+    for (int t = 0; t < P.n; ++t) {
+      double df = __dsub_rn((double)szq[t], (double)row[t]);
+      acc = __dadd_rn(acc, __dmul_rn(df, df));
+    }
+    a2 = acc;
+    d = __dsqrt_rn(acc);
+    id = perm[p];
+  }
+  sd[tid] = d;
+  sq2[tid] = a2;
+  sid[tid] = id;
+  for (int size = 2; size <= 128; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      if (tid < 64) {
+        int lo = 2 * tid - (tid & (stride - 1));
+        int hi = lo + stride;
+        bool up = ((lo & size) == 0);
+        bool gt = sd[lo] > sd[hi] || (sd[lo] == sd[hi] && sid[lo] > sid[hi]);
+        if (gt == up) {
+          double td = sd[lo];
+          sd[lo] = sd[hi];
+          sd[hi] = td;
+          td = sq2[lo];
+          sq2[lo] = sq2[hi];
+          sq2[hi] = td;
+          uint32_t ti = sid[lo];
+          sid[lo] = sid[hi];
+          sid[hi] = ti;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int kk = P.k < nl ? P.k : nl;
+  const double dk = kk > 0 ? sd[kk - 1] : INFINITY;
+  const double lim = __dadd_rn(dk, __dmul_rn(1e-6, dk));
+  if (tid < nl && sid[tid] != 0xFFFFFFFFu && (tid < kk || sd[tid] <= lim)) atomicMax(&s_cnt, tid + 1);
+  __syncthreads();
+  const int w = s_cnt;
+  if (tid == 0 && w > cap) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
+  if (tid < cap) {
+    const bool in = tid < w;
+    ids[q * cap + tid] = in ? (int64_t)sid[tid] : -1;
+    d2[q * cap + tid] = in ? sq2[tid] : INFINITY;
+  }
+  if (tid == 0) cnt[q] = w < cap ? w : cap;
+}
+
 // ========================================================================
 // Host driver of one sofa_query call.
 // ========================================================================
@@ -1458,6 +1514,7 @@ __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __res
 static QueryParams make_params(const Index* ix, int k) {
   QueryParams P;
   P.N = ix->N;
+  P.Ns = ix->Ns;
   P.T = ix->T;
   P.L = ix->L;
   P.n = ix->n;
@@ -1486,9 +1543,35 @@ static QueryParams make_params(const Index* ix, int k) {
 // a CUDA graph: every buffer has been sized by an earlier eager call, the
 // routed-list sizes are upper bounds instead of read-back totals, and only the
 // first scan pass is recorded (a full pool is detected after the replay).
+// Where a batch's answers go: the k-NN (idx, dist), or, with wid set, each
+// query's window (ids, FP64 squared distances, count; wcap entries per query).
+struct WindowOut {
+  int64_t* wid = nullptr;
+  double* wd2 = nullptr;
+  int* wcnt = nullptr;
+  int wcap = 0;
+};
+
+template <int LW, bool NYQ>
+static int final_launch(Index* ix, const QueryParams& P, int64_t Q, const float* zq, int64_t* idx, float* dist,
+                        const WindowOut& wo, unsigned long long* counters, int* status, cudaStream_t st) {
+  QueryScratch& s = ix->qs;
+  const size_t nsm = (size_t)ix->n * sizeof(float);
+  ix->prof.begin(5, st);
+  if (wo.wid)
+    k_window<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(),
+                                            wo.wcap, wo.wid, wo.wd2, wo.wcnt, status);
+  else
+    k_final<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(), idx,
+                                           dist, counters, status);
+  ix->prof.end(st);
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
 template <int LW, bool NYQ>
 static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* idx, float* dist,
-                       cudaStream_t st, bool capturing = false) {
+                       cudaStream_t st, bool capturing = false, const WindowOut& wo = WindowOut()) {
   QueryScratch& s = ix->qs;
   const int n = ix->n, NB = ix->NB;
   const int64_t L = ix->L;
@@ -1537,14 +1620,8 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
                                                   s.list_n.as<int>(), thr, status, counters, topm, top_m, block);
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
-  if (ix->approximate) {  // the approximate search's answer: the seed's kept list, re-scored
-    ix->prof.begin(5, st);
-    k_final<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(), idx,
-                                           dist, counters, status);
-    ix->prof.end(st);
-    SOFA_CUDA(cudaGetLastError());
-    return 0;
-  }
+  if (ix->approximate)  // the approximate search's answer: the seed's kept list, re-scored
+    return final_launch<LW, NYQ>(ix, P, Q, zq, idx, dist, wo, counters, status, st);
 
   // series-bound arithmetic: FP32, or FP16x2 with the derived factor
   // f16 = 1 + (LW/2 + 5) u16 (u16 = 2^-11) on the threshold
@@ -1654,7 +1731,8 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
       }
     }
     if (dense) {
-      ix->prof.begin(3, st, 2);
+      // the FP16 query copy (FP16 operands only), the query norms, the contraction
+      ix->prof.begin(3, st, ix->Zh ? 3 : 2);
       DenseArgs A;
       A.zq = zq;
       A.Q = (int)Q;
@@ -1774,21 +1852,16 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     qflag_out = (qflag_out == s.qflag.as<int>()) ? s.qflag.as<int>() + Q : s.qflag.as<int>();
   }
   if (rc) return rc;
-  ix->prof.begin(5, st);
-  k_final<<<(unsigned)Q, 128, nsm, st>>>(P, zq, ix->Z, ix->perm, s.list_p.as<uint32_t>(), s.list_n.as<int>(), idx,
-                                         dist, counters, status);
-  ix->prof.end(st);
-  SOFA_CUDA(cudaGetLastError());
-  return 0;
+  return final_launch<LW, NYQ>(ix, P, Q, zq, idx, dist, wo, counters, status, st);
 }
 
 static int dispatch_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* ip, float* dp, cudaStream_t st,
-                          bool capturing) {
+                          bool capturing, const WindowOut& wo = WindowOut()) {
   if (ix->LW == 16)
-    return ix->nyq_first ? query_batch<16, true>(ix, qp, qb, k, ip, dp, st, capturing)
-                         : query_batch<16, false>(ix, qp, qb, k, ip, dp, st, capturing);
-  return ix->nyq_first ? query_batch<32, true>(ix, qp, qb, k, ip, dp, st, capturing)
-                       : query_batch<32, false>(ix, qp, qb, k, ip, dp, st, capturing);
+    return ix->nyq_first ? query_batch<16, true>(ix, qp, qb, k, ip, dp, st, capturing, wo)
+                         : query_batch<16, false>(ix, qp, qb, k, ip, dp, st, capturing, wo);
+  return ix->nyq_first ? query_batch<32, true>(ix, qp, qb, k, ip, dp, st, capturing, wo)
+                       : query_batch<32, false>(ix, qp, qb, k, ip, dp, st, capturing, wo);
 }
 
 // A batch through a recorded CUDA graph.  The first batch of a shape runs
@@ -1869,6 +1942,7 @@ static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* i
 }
 
 int run_query(Index* ix, const float* q, int64_t Q, int k, int64_t* idx, float* dist, cudaStream_t st) {
+  NvtxScope range(ix->prof, "sofa_query");
   QueryScratch& s = ix->qs;
   const bool fresh = s.counters.p == nullptr;
   TRYQ(s.counters.ensure(16 * sizeof(unsigned long long)));
@@ -1884,6 +1958,30 @@ int run_query(Index* ix, const float* q, int64_t Q, int k, int64_t* idx, float* 
     const bool graph = ix->use_graph && !ix->prof.on && qb * ix->L <= ((int64_t)1 << 28);
     int rc = graph ? graph_batch(ix, qp, qb, k, ip, dp, st) : dispatch_batch(ix, qp, qb, k, ip, dp, st, false);
     if (rc) return rc;
+  }
+  ix->stats[0] += Q;
+  return 0;
+}
+
+// The k-NN windows of Q queries (sofa_query_window), batch by batch, eagerly.
+int run_query_window(Index* ix, const float* q, int64_t Q, int k, int cap, int64_t* wid, double* wd2, int* wcnt,
+                     cudaStream_t st) {
+  NvtxScope range(ix->prof, "sofa_query_window");
+  QueryScratch& s = ix->qs;
+  const bool fresh = s.counters.p == nullptr;
+  TRYQ(s.counters.ensure(16 * sizeof(unsigned long long)));
+  if (fresh) SOFA_CUDA(cudaMemsetAsync(s.counters.p, 0, 16 * sizeof(unsigned long long), st));
+  int* status = reinterpret_cast<int*>(s.counters.as<unsigned long long>() + 8);
+  SOFA_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  const int64_t QB = 8192;
+  for (int64_t q0 = 0; q0 < Q; q0 += QB) {
+    const int64_t qb = std::min(QB, Q - q0);
+    WindowOut wo;
+    wo.wid = wid + q0 * cap;
+    wo.wd2 = wd2 + q0 * cap;
+    wo.wcnt = wcnt + q0;
+    wo.wcap = cap;
+    TRYQ(dispatch_batch(ix, q + q0 * ix->n, qb, k, nullptr, nullptr, st, false, wo));
   }
   ix->stats[0] += Q;
   return 0;
@@ -1906,15 +2004,21 @@ __global__ void k_all_bounds(int64_t Q, int64_t N, int NB, const float* __restri
 }
 
 int launch_lower_bounds(Index* ix, const float* qv, int64_t Q, float* out, cudaStream_t st) {
-  dim3 g((unsigned)ceil_div(ix->N, 256), (unsigned)Q);
-  if (ix->LW == 16) {
-    if (ix->nyq_first) k_all_bounds<16, true><<<g, 256, 0, st>>>(Q, ix->N, ix->NB, qv, ix->words, ix->perm, ix->ch, out);
-    else k_all_bounds<16, false><<<g, 256, 0, st>>>(Q, ix->N, ix->NB, qv, ix->words, ix->perm, ix->ch, out);
-  } else {
-    if (ix->nyq_first) k_all_bounds<32, true><<<g, 256, 0, st>>>(Q, ix->N, ix->NB, qv, ix->words, ix->perm, ix->ch, out);
-    else k_all_bounds<32, false><<<g, 256, 0, st>>>(Q, ix->N, ix->NB, qv, ix->words, ix->perm, ix->ch, out);
+  // queries go on gridDim.y, at most 65535 per launch
+  for (int64_t q0 = 0; q0 < Q; q0 += 65535) {
+    const int64_t qc = std::min<int64_t>(65535, Q - q0);
+    const float* qvc = qv + q0 * ix->NB;
+    float* oc = out + q0 * ix->N;
+    dim3 g((unsigned)ceil_div(ix->N, 256), (unsigned)qc);
+    if (ix->LW == 16) {
+      if (ix->nyq_first) k_all_bounds<16, true><<<g, 256, 0, st>>>(qc, ix->N, ix->NB, qvc, ix->words, ix->perm, ix->ch, oc);
+      else k_all_bounds<16, false><<<g, 256, 0, st>>>(qc, ix->N, ix->NB, qvc, ix->words, ix->perm, ix->ch, oc);
+    } else {
+      if (ix->nyq_first) k_all_bounds<32, true><<<g, 256, 0, st>>>(qc, ix->N, ix->NB, qvc, ix->words, ix->perm, ix->ch, oc);
+      else k_all_bounds<32, false><<<g, 256, 0, st>>>(qc, ix->N, ix->NB, qvc, ix->words, ix->perm, ix->ch, oc);
+    }
+    SOFA_CUDA(cudaGetLastError());
   }
-  SOFA_CUDA(cudaGetLastError());
   return 0;
 }
 

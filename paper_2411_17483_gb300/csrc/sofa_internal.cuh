@@ -22,6 +22,13 @@ constexpr int SEED_MAX = 4096;     // largest seed window
 
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
+// True for device or managed memory (host memory, or an unknown pointer: false).
+bool is_device_ptr(const void* p);
+// SOFA_ERR_INVALID_ARG unless the calling thread's current device is the one
+// the index was built or loaded on: its buffers and the kernels launched for
+// it must be on the same GPU.
+struct Index;
+int check_device(const Index* ix);
 
 #define SOFA_CUDA(call)                                                               \
   do {                                                                                \
@@ -82,7 +89,10 @@ struct QueryScratch {
 
 struct Mlp;  // proposal network (mlp.cu)
 
-// Phase timing with CUDA events on the launching stream.
+// Phase timing with CUDA events on the launching stream, and an NVTX range
+// per phase ("sofa.<phase>", pushed on the calling host thread) so that
+// profilers can attribute kernels to phases.  NVTX ranges cost nothing
+// unless a tool is attached.
 constexpr int NPHASE = 8;
 struct Prof {
   bool on = false;
@@ -90,15 +100,29 @@ struct Prof {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> open;
   double ms[NPHASE] = {0};
   long long launches[NPHASE] = {0};
+  int nvtx_depth = 0;           // ranges pushed by begin() and not yet popped
   cudaEvent_t get();
   void begin(int phase, cudaStream_t st, int kernels = 1);
   void end(cudaStream_t st);
+  void unwind(int depth);       // pop ranges left open by an early error return
   void collect();  // after the stream has been synchronised
   void release();
 };
 
+// Pushes an NVTX range for its scope; on exit also closes phase ranges that
+// an early error return left open.
+struct NvtxScope {
+  Prof& prof;
+  int depth;
+  NvtxScope(Prof& p, const char* name);
+  ~NvtxScope();
+};
+
 struct Index {
   int64_t N = 0;
+  // Rows [0, Ns) are the build's key-sorted run; rows [Ns, N) were added by
+  // sofa_insert and form a second key-sorted run (the appended region).
+  int64_t Ns = 0;
   int n = 0, l = 0, alpha = 0, LW = 16, nsel = 0, NB = 16, bps = 8;
   int nyq_first = 0;
   int leaf_tiles = 64;
@@ -128,6 +152,10 @@ struct Index {
   float* vw = nullptr;         // [NB] Eq. (1) weight of each basis column (0 for unused columns)
   float* xn = nullptr;         // [N] ||x||^2 of each canonical series (dense path)
   __half* Zh = nullptr;        // [N][n] FP16 copy of the canonical series (dense path, precision 2)
+  __half* VH = nullptr;        // [N][NB] the value codes as FP16 (tensor-core series bound), with VC
+  float4* vcx = nullptr;       // [N] (-2 s, -2 r, s^2 ||c||_w^2 - r^2 - M', 0) of the value codes
+  float tc_margin = 0.f;       // M': rounding margin of the tensor-core series bound
+  int64_t tc_bytes = 0;        // device bytes of VH and vcx
   uint32_t* perm = nullptr;    // [N] sorted position -> original row
   uint64_t* keys = nullptr;    // [N] sorted layout keys
   uint8_t* keyorder = nullptr; // [64] key bit order (dim << 3 | bit)
@@ -146,6 +174,7 @@ struct Index {
   int64_t cand_budget = (int64_t)1 << 30;  // candidate-region entries of one overflow pass
   int approximate = 0;         // 1: answers from the seed alone
   int dense_mode = 0;          // 0: dense contraction when the leaf bound prunes little, 1: never, 2: always
+  int series_bound = 0;        // 0: SFA word bound (k_scan); 1: value codes on the tensor cores (k_vscan)
   struct GraphEntry {
     int64_t key[15];
     unsigned long long gen;
@@ -209,8 +238,38 @@ struct DenseArgs {
 };
 bool dense_supported(const Index* ix, int k);
 int launch_dense(Index* ix, const DenseArgs& a, cudaStream_t st);
-int launch_row_norms(Index* ix, cudaStream_t st);
+int launch_row_norms(const float* Z, int64_t N, int n, float* xn, cudaStream_t st);
+int insert_rows(Index* ix, const float* x_dev, int64_t A, cudaStream_t st);
 float dense_margin_of(const Index* ix);
+
+// Tensor-core series bound (vscan.cu).
+struct VscanArgs {
+  const int4* units;
+  const int* n_units;          // device: number of units
+  const int* leaf_q;
+  const float* qv;
+  const float* thr;
+  int cap;
+  const int* qslot;
+  uint32_t* cand_p;
+  float* cand_lb;
+  int* cand_n;
+  int64_t pool_cap;
+  int* pool_n;
+  int* pool_q;
+  uint32_t* pool_p;
+  float* pool_lb;
+  int* qpool_cnt;
+  float* dump;                 // non-null: every pair's bound (Q x N, original order) instead of emitting
+  int64_t dumpQ;
+  unsigned long long* counters;
+  int* status;
+};
+int make_tc_codes(Index* ix, cudaStream_t st);
+void release_tc_codes(Index* ix);
+bool vscan_supported(const Index* ix);
+int launch_vscan(Index* ix, const VscanArgs& a, cudaStream_t st);
+double tc_margin(const Index* ix);
 
 void destroy_index(Index* ix);
 int mlp_save(const Index* ix, void* file);   // FILE*; 0 or an error code
@@ -218,6 +277,8 @@ int mlp_load(Index* ix, void* file, cudaStream_t st);
 
 int run_query(Index* ix, const float* q_dev, int64_t Q, int k, int64_t* idx_dev, float* dist_dev,
               cudaStream_t st);
+int run_query_window(Index* ix, const float* q_dev, int64_t Q, int k, int cap, int64_t* wid, double* wd2, int* wcnt,
+                     cudaStream_t st);
 int launch_qprep(Index* ix, const float* q_dev, int64_t Q, float* zq, float* qv, cudaStream_t st);
 int launch_lower_bounds(Index* ix, const float* qv, int64_t Q, float* out, cudaStream_t st);
 int launch_znorm(const float* x, int64_t R, int n, float* z, cudaStream_t st);

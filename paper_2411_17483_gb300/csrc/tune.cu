@@ -82,11 +82,8 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
                              sofa_tuning* chosen, sofa_stream stream) {
   if (!h || !queries || Q < 1 || k < 1 || k > SOFA_MAX_K || k > h->N)
     return fail(SOFA_ERR_INVALID_ARG, "bad autotune argument");
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, queries) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
-    cudaGetLastError();
-    return fail(SOFA_ERR_INVALID_ARG, "autotune queries must be device memory");
-  }
+  if (!is_device_ptr(queries)) return fail(SOFA_ERR_INVALID_ARG, "autotune queries must be device memory");
+  if (int rc = check_device(h)) return rc;
   Index* ix = h;
   cudaStream_t st = (cudaStream_t)stream;
   const std::string key = tune_key(ix, k, Q);

@@ -19,6 +19,7 @@ SOFA_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "NOT_TRAINED", -6: "TIE_OVERFLOW", -7: "INTERNAL"}
 MAX_K = 64
 MAX_WORD = 32
+MAX_WINDOW = 96
 
 _lib = None
 
@@ -76,7 +77,8 @@ class Info(ctypes.Structure):
                 ("delta_data", ctypes.c_double), ("delta_query", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("proposal_classes", ctypes.c_int64),
                 ("proposal_train", ctypes.c_int64), ("proposal_loss", ctypes.c_double),
-                ("proposal_top1", ctypes.c_double), ("proposal_topm", ctypes.c_double)]
+                ("proposal_top1", ctypes.c_double), ("proposal_topm", ctypes.c_double),
+                ("appended", ctypes.c_int64)]
 
 
 def load():
@@ -93,8 +95,10 @@ def load():
     sig = {
         "sofa_build": (P, [P, i64, i32, i32, i32]),
         "sofa_build_ex": (P, [P, i64, i32, i32, i32, ctypes.POINTER(BuildOpts), P]),
+        "sofa_insert": (ctypes.c_int, [P, P, i64, P]),
         "sofa_query": (ctypes.c_int, [P, P, i64, i32, P, P, P]),
         "sofa_query_multi": (ctypes.c_int, [P, i32, P, P, P, P, i64, P, P, P, P]),
+        "sofa_query_window": (ctypes.c_int, [P, P, i64, i32, i32, P, P, P, P]),
         "sofa_train_proposal": (ctypes.c_int, [P, ctypes.POINTER(TrainOpts), P]),
         "sofa_set_seed_mode": (ctypes.c_int, [P, i32]),
         "sofa_mlp_grad": (ctypes.c_int, [i32, i32, i32, P, P, P, i32, P, ctypes.POINTER(ctypes.c_float), P]),
@@ -172,6 +176,16 @@ class Index:
         self.h = ctypes.c_void_p(h)
         self.N, self.n, self.l, self.alphabet = data.shape[0], data.shape[1], l, alphabet
 
+    def insert(self, data: torch.Tensor, stream=None):
+        """sofa_insert: add the rows of data (N_add x n fp32, host or device);
+        they get the row ids N, N+1, ... in order."""
+        if data.dtype != torch.float32 or data.dim() != 2 or data.shape[1] != self.n:
+            raise ValueError("data must be a 2-d float32 tensor with the index's series length")
+        data = data.contiguous()
+        st = _stream(stream) if data.is_cuda else ctypes.c_void_p(0)
+        _check(load().sofa_insert(self.h, _ptr(data), data.shape[0], st))
+        self.N += data.shape[0]
+
     def save(self, path: str):
         """sofa_save: every array of the index (and a trained proposal network) to one file."""
         _check(load().sofa_save(self.h, str(path).encode()))
@@ -212,6 +226,19 @@ class Index:
             dist = torch.empty((Q, k), dtype=torch.float32, device=dev)
         _check(load().sofa_query(self.h, _ptr(q), Q, k, _ptr(idx), _ptr(dist), _stream(stream)))
         return idx, dist
+
+    def query_window(self, q: torch.Tensor, k: int = 1, cap: int = MAX_WINDOW, stream=None):
+        """sofa_query_window: per query, the rows within the tie window of its
+        k-th distance in this index -- (ids int64 [Q,cap], d2 float64 [Q,cap],
+        counts int32 [Q]), ascending by (distance, id), padded -1 / inf."""
+        q = q.contiguous()
+        Q = q.shape[0]
+        dev = q.device
+        ids = torch.empty((Q, cap), dtype=torch.int64, device=dev)
+        d2 = torch.empty((Q, cap), dtype=torch.float64, device=dev)
+        cnt = torch.empty((Q,), dtype=torch.int32, device=dev)
+        _check(load().sofa_query_window(self.h, _ptr(q), Q, k, cap, _ptr(ids), _ptr(d2), _ptr(cnt), _stream(stream)))
+        return ids, d2, cnt
 
     def set_tuning(self, group=0, cand_cap=0, seed_count=0, seed_window=0, bound_precision=0, pool_cap=0,
                    refine_filter=0, use_graph=0, cand_budget=0, dense=0, approximate=0):

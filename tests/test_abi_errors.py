@@ -76,6 +76,13 @@ def test_calls_on_a_null_handle_are_refused(lib):
     assert lib.sofa_lower_bounds_noalloc(None, host(q), 2, host(d), None) == INVALID
     assert lib.sofa_save(None, b"/nonexistent/x.sofa") == INVALID
     assert lib.sofa_query_multi(None, 1, host(q), None, None, None, 2, host(i), host(d), None, None) == INVALID
+    d2 = np.zeros((2, 8), np.float64)
+    c = np.zeros(2, np.int32)
+    w = np.zeros((2, 8), np.int64)
+    assert lib.sofa_query_window(None, host(q), 2, 1, 8, host(w), host(d2), host(c), None) == INVALID
+    assert "handle is NULL" in last_error(lib)
+    assert lib.sofa_insert(None, host(q), 2, None) == INVALID
+    assert "handle is NULL" in last_error(lib)
     lib.sofa_free(None)                         # a no-op
 
 

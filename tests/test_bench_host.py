@@ -54,3 +54,19 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"].startswith("random walks 20000x256")
+
+
+def test_scan_traffic_scales_from_the_stored_capture(monkeypatch):
+    """The scan's per-launch DRAM traffic is scaled from a stored small-case
+    capture (reads by tile loads, writes by candidates), and only while the
+    kernel's source matches the captured one."""
+    sha = bench.kernel_source_sha("k_scan")
+    assert len(sha) == 16 and sha == bench.kernel_source_sha("k_scan")
+    cap = {"case": "test", "source_sha": sha, "dram_read": 1000.0, "dram_write": 300.0, "tile_loads": 10,
+           "candidates": 30}
+    monkeypatch.setattr(bench, "SCAN_CAPTURE", cap)
+    assert bench.scaled_scan_traffic(40, 60) == 1000.0 * 4 + 300.0 * 2
+    monkeypatch.setattr(bench, "SCAN_CAPTURE", {**cap, "source_sha": "0" * 16})
+    assert bench.scaled_scan_traffic(40, 60) is None
+    monkeypatch.setattr(bench, "SCAN_CAPTURE", None)
+    assert bench.scaled_scan_traffic(40, 60) is None

@@ -273,7 +273,7 @@ def test_query_multi(sofa):
     for i in range(30):
         x = xs[lens.index(ql[i])]
         oi, od = oracle_knn(x, qs[i][None, :], qk[i])
-        assert list(idx[oo[i]:oo[i] + qk[i]].cpu().numpy()) == list(oi[0])
+        assert_knn_equal(idx[oo[i]:oo[i] + qk[i]][None, :], dist[oo[i]:oo[i] + qk[i]][None, :], oi, od)
     for ix in ixs:
         ix.close()
 
@@ -358,6 +358,7 @@ def test_save_load_roundtrip(sofa, tmp_path):
     iy = sofa.Index.load(path)
     assert iy.info()["N"] == N and iy.info()["proposal_classes"] == 64
     assert torch.equal(iy.perm(), ix.perm()) and torch.equal(iy.words(), ix.words())
+    oi, od = oracle_knn(x, q, 4)
     for tuning, seed_mode in ((dict(), 0), (dict(refine_filter=2), 1), (dict(approximate=1), 1), (dict(dense=2), 0)):
         for h in (ix, iy):
             h.set_seed_mode(seed_mode)
@@ -365,6 +366,8 @@ def test_save_load_roundtrip(sofa, tmp_path):
         a = ix.query(q, 4)
         b = iy.query(q, 4)
         assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), tuning
+        if not tuning.get("approximate"):
+            assert_knn_equal(b[0], b[1], oi, od)   # the loaded index answers the oracle's k-NN
     ix.close()
     iy.close()
 
