@@ -54,6 +54,9 @@ def parse():
                          "the dense tensor-core form")
     ap.add_argument("--no-autotune", action="store_true",
                     help="chosen mode with the default tuning instead of the autotuner's choice")
+    ap.add_argument("--tune", default="",
+                    help="comma-separated knob=value overrides applied to the tuned modes after the autotuner, "
+                         "e.g. series_bound=1")
     ap.add_argument("--modes", default="",
                     help="comma-separated subset of the modes to time (plain, plain_seed, learned); default all")
     ap.add_argument("--gen", default="rw", choices=["rw", "mixed", "sin", "multi"],
@@ -590,6 +593,11 @@ def run_sofa(a, ws, rank, local):
             t = ix.autotune(qt, a.k)
             tunings[m] = {k: v for k, v in t.items() if v}
         del qt
+    if a.tune:
+        over = {kv.split("=")[0].strip(): int(kv.split("=")[1]) for kv in a.tune.split(",") if "=" in kv}
+        for m, (mode, tuned) in modes.items():
+            if tuned:
+                tunings[m] = {**tunings[m], **over}
     chosen_tuning = tunings[chosen]
     results, answers = {}, {}
     for mode_name, (mode, tuned) in modes.items():

@@ -221,6 +221,14 @@ typedef struct {
                            answers are real distances re-scored in FP64 and
                            ordered by the tie rule, but not necessarily the
                            exact k-NN.  0: exact (default)                     */
+  int32_t series_bound; /* series-level bound of the scan, after the leaf and
+                           tile envelope checks: 0 the SFA word bound (Eq. 1
+                           with Eq. dist_i, default); 1 Eq. (1) on all the
+                           selected values from their int8 codes, one tcgen05
+                           contraction per (work unit, tile) with a derived
+                           FP16 rounding margin (needs precision >= 1).  Both
+                           are lower bounds of the distance: answers do not
+                           change                                               */
 } sofa_tuning;
 int sofa_set_tuning(sofa_handle h, const sofa_tuning* t);
 
@@ -346,6 +354,17 @@ sofa_handle sofa_load(const char* path, sofa_stream stream);
  * on.  queries (Q x n) and out (Q x N) are device memory; 1 <= Q <= 8192,
  * Q * N <= 2^31, n % 4 == 0.  Returns 0 or a negative SOFA_ERR_* code. */
 int sofa_dense_sqdist(sofa_handle h, const float* queries, int64_t Q, float* out, float* margin,
+                      sofa_stream stream);
+
+/* Lower bounds of the tensor-core series bound (series_bound = 1; a test and
+ * inspection aid, the paper has no counterpart): for every query q (raw,
+ * z-normalised here) and every series x, out[q * N + id] (original row ids)
+ * = max(sqrt(max(e~ - M', 0)) - r_x, 0)^2 <= ||q - v_x||_w^2 <= ED^2, e~ the
+ * tensor-core value of ||q~ - y_x||_w^2 (Eq. 1 on the selected values, y_x the
+ * value codes, r_x their margin).  *margin (may be NULL) receives M'.  queries
+ * (Q x n) and out (Q x N) are device memory; 1 <= Q, Q * N <= 2^31; needs an
+ * index with the value codes (precision >= 1). */
+int sofa_value_bounds(sofa_handle h, const float* queries, int64_t Q, float* out, float* margin,
                       sofa_stream stream);
 
 /* Canonical z-normalisation of R rows (Sec. II Def. z-ED) as the index uses

@@ -135,7 +135,7 @@ static int num_candidates_host(int n, int pool) {
 void destroy_index(Index* ix) {
   if (!ix) return;
   void* ptrs[] = {ix->sel, ix->sel_k, ix->sel_part, ix->var, ix->basis, ix->beta, ix->edge, ix->ch, ix->ch16,
-                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->VC, ix->vsr, ix->vw, ix->xn, ix->Zh, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
+                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->VC, ix->vsr, ix->vw, ix->xn, ix->Zh, ix->VH, ix->vcx, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   DevBuf* bufs[] = {&ix->qs.zq, &ix->qs.qv, &ix->qs.qn, &ix->qs.zqh, &ix->qs.llb, &ix->qs.thr, &ix->qs.list_d, &ix->qs.list_p,
@@ -430,6 +430,9 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   if (t->dense < 0 || t->dense > 2) return fail(SOFA_ERR_INVALID_ARG, "dense must be 0, 1 or 2");
   if (t->approximate < 0 || t->approximate > 1) return fail(SOFA_ERR_INVALID_ARG, "approximate must be 0 or 1");
   if (t->use_graph < 0 || t->use_graph > 1) return fail(SOFA_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+  if (t->series_bound < 0 || t->series_bound > 1) return fail(SOFA_ERR_INVALID_ARG, "series_bound must be 0 or 1");
+  if (t->series_bound == 1 && !vscan_supported(h))
+    return fail(SOFA_ERR_INVALID_ARG, "series_bound 1 needs an index built with precision >= 1");
   h->group = t->group ? t->group : 64;
   h->cand_cap = t->cand_cap ? t->cand_cap : 65536;
   h->seed_count = t->seed_count ? t->seed_count : 128;
@@ -441,6 +444,7 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   h->cand_budget = t->cand_budget ? t->cand_budget : ((int64_t)1 << 30);
   h->dense_mode = t->dense;
   h->approximate = t->approximate;
+  h->series_bound = t->series_bound;
   return 0;
 }
 

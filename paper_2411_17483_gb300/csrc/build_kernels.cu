@@ -11,16 +11,33 @@
 
 namespace sofa {
 
-constexpr int ROWS = 32;  // rows per CTA in the thread-per-row kernels (one warp)
+constexpr int ROWS = 32;       // rows per CTA in the row kernels
+constexpr int WTHREADS = 256;  // threads per CTA of the row kernels (all stage; per-row work as stated)
 
-// Stage ROWS rows (global rows row_of(r)) into shared memory with a padded
-// stride n+1 so that thread r walking its own row hits distinct banks.
-__device__ inline void stage_rows(const float* __restrict__ x, int64_t first, int64_t R, int64_t stride,
-                                  int n, float* sm) {
+// Stage rows first..first+ROWS-1 (global rows row*stride) of a row-major
+// matrix by every thread of the CTA, 16-byte loads when n % 4 == 0, into the
+// padded layout: row r at r*(n+1), so that a thread walking its own row hits
+// its own banks.
+__device__ inline void stage_rows_vec(const float* __restrict__ x, int64_t first, int64_t R, int n, float* sm,
+                                      int64_t stride = 1) {
   const int nr = (int)(R - first < ROWS ? R - first : ROWS);
-  for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
-    int r = e / n, t = e - r * n;
-    sm[r * (n + 1) + t] = x[(first + r) * stride * (int64_t)n + t];
+  if ((n & 3) == 0) {
+    const int n4 = n >> 2;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (int e = threadIdx.x; e < nr * n4; e += blockDim.x) {
+      const int r = e / n4, c = e - r * n4;
+      const float4 v = __ldg(x4 + (first + r) * stride * n4 + c);
+      float* d = sm + r * (n + 1) + 4 * c;
+      d[0] = v.x;
+      d[1] = v.y;
+      d[2] = v.z;
+      d[3] = v.w;
+    }
+  } else {
+    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+      const int r = e / n, t = e - r * n;
+      sm[r * (n + 1) + t] = x[(first + r) * stride * (int64_t)n + t];
+    }
   }
   __syncthreads();
 }
@@ -37,10 +54,10 @@ __global__ void k_rows_project(const float* __restrict__ x, int64_t R, int n, in
                                float* __restrict__ v, int vt, double2* __restrict__ stats) {
   extern __shared__ float sm[];
   const int64_t first = (int64_t)blockIdx.x * ROWS;
-  stage_rows(x, first, R, stride, n, sm);
+  stage_rows_vec(x, first, R, n, sm, stride);  // every thread of the CTA stages
   const int r = threadIdx.x;
   const int64_t row = first + r;
-  if (r >= ROWS || row >= R) return;
+  if (r >= ROWS || row >= R) return;        // one thread per row from here
   const float* my = sm + r * (n + 1);
   double mu = 0.0, inv = 1.0;
   if (NORMALIZE) znorm_stats_seq(my, n, 1, mu, inv);
@@ -146,57 +163,77 @@ static int launch_qprep_rq(Index* ix, const float* q, int64_t Q, float* zq, floa
 // SFA words of every series (Alg. 2): z-normalise, project on the l word
 // columns in FP32, quantise by counting breakpoints <= value (half-open bins
 // [beta(a-1), beta(a))), then form the 64-bit layout key from the symbol bits
-// in the order given by keyorder (dim << 3 | bit).
+// in the order given by keyorder (dim << 3 | bit).  A CTA of WTHREADS
+// threads takes ROWS rows: all threads stage them; one thread per row runs
+// the canonical FP64 statistics (a sequential chain); all threads write the
+// z-values in place; thread (r, g) projects row r on columns g*CPT..+CPT, one
+// FMA per t in ascending t for each column (so every value is the same FP32
+// sequence as a thread-per-row projection); one thread per row packs the
+// word and its key.
 template <int LW>
-__global__ void k_words(const float* __restrict__ x, int64_t N, int n, const float* __restrict__ basis,
-                        int NB, const float* __restrict__ beta, int alpha, int l,
-                        const uint8_t* __restrict__ keyorder, int keybits, uint8_t* __restrict__ words,
-                        uint64_t* __restrict__ keys, uint32_t* __restrict__ ids,
-                        double2* __restrict__ stats) {
+__global__ void __launch_bounds__(WTHREADS) k_words(const float* __restrict__ x, int64_t N, int n,
+                                                    const float* __restrict__ basis, int NB,
+                                                    const float* __restrict__ beta, int alpha, int l,
+                                                    const uint8_t* __restrict__ keyorder, int keybits,
+                                                    uint8_t* __restrict__ words, uint64_t* __restrict__ keys,
+                                                    uint32_t* __restrict__ ids, double2* __restrict__ stats) {
+  constexpr int GPR = WTHREADS / ROWS;  // threads per row in the projection (8)
+  constexpr int CPT = LW / GPR;         // columns per thread (2 or 4)
   extern __shared__ float sm[];
   float* sbeta = sm;                                  // LW x (alpha+1)
-  float* srows = sm + LW * (alpha + 1);
+  float* srows = sm + LW * (alpha + 1);               // ROWS x (n+1)
+  uint8_t* ssym = reinterpret_cast<uint8_t*>(srows + ROWS * (n + 1));  // ROWS x LW
+  __shared__ double s_mu[ROWS], s_inv[ROWS];
   for (int e = threadIdx.x; e < LW * (alpha + 1); e += blockDim.x) sbeta[e] = beta[e];
   const int64_t first = (int64_t)blockIdx.x * ROWS;
-  stage_rows(x, first, N, 1, n, srows);
-  const int r = threadIdx.x;
-  const int64_t row = first + r;
-  if (r >= ROWS || row >= N) return;
-  const float* my = srows + r * (n + 1);
-  double mu, inv;
-  znorm_stats_seq(my, n, 1, mu, inv);
-  stats[row] = make_double2(mu, inv);
-  float acc[LW];
+  const int nr = (int)(N - first < ROWS ? N - first : ROWS);
+  stage_rows_vec(x, first, N, n, srows);
+  const int tid = threadIdx.x;
+  if (tid < nr) {
+    double mu, inv;
+    znorm_stats_seq(srows + tid * (n + 1), n, 1, mu, inv);
+    s_mu[tid] = mu;
+    s_inv[tid] = inv;
+    stats[first + tid] = make_double2(mu, inv);
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * n; e += blockDim.x) {
+    const int r = e / n, t = e - r * n;
+    srows[r * (n + 1) + t] = znorm_value(srows[r * (n + 1) + t], s_mu[r], s_inv[r]);
+  }
+  __syncthreads();
+  const int r = tid / GPR, g = tid - r * GPR;
+  if (r < nr) {
+    const float* my = srows + r * (n + 1);
+    float acc[CPT];
 #pragma unroll
-  for (int j = 0; j < LW; ++j) acc[j] = 0.f;
-  for (int t = 0; t < n; ++t) {
-    float zt = znorm_value(my[t], mu, inv);
-    const float4* b = reinterpret_cast<const float4*>(basis + (int64_t)t * NB);
+    for (int c = 0; c < CPT; ++c) acc[c] = 0.f;
+    const float* bcol = basis + g * CPT;
+    for (int t = 0; t < n; ++t) {
+      const float zt = my[t];
 #pragma unroll
-    for (int j4 = 0; j4 < LW / 4; ++j4) {
-      float4 bb = __ldg(b + j4);
-      acc[4 * j4 + 0] = fmaf(zt, bb.x, acc[4 * j4 + 0]);
-      acc[4 * j4 + 1] = fmaf(zt, bb.y, acc[4 * j4 + 1]);
-      acc[4 * j4 + 2] = fmaf(zt, bb.z, acc[4 * j4 + 2]);
-      acc[4 * j4 + 3] = fmaf(zt, bb.w, acc[4 * j4 + 3]);
+      for (int c = 0; c < CPT; ++c) acc[c] = fmaf(zt, __ldg(bcol + (int64_t)t * NB + c), acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int j = g * CPT + c;
+      int sym = 0;
+      if (j < l) {
+        const float* bj = sbeta + j * (alpha + 1);
+        for (int step = 128; step > 0; step >>= 1)
+          if (sym + step <= alpha - 1 && bj[sym + step] <= acc[c]) sym += step;
+      }
+      ssym[r * LW + j] = (uint8_t)sym;
     }
   }
-  uint8_t sym[LW];
-#pragma unroll
-  for (int j = 0; j < LW; ++j) {
-    int c = 0;
-    if (j < l) {
-      const float* bj = sbeta + j * (alpha + 1);
-      for (int step = 128; step > 0; step >>= 1)
-        if (c + step <= alpha - 1 && bj[c + step] <= acc[j]) c += step;
-    }
-    sym[j] = (uint8_t)c;
-  }
+  __syncthreads();
+  if (tid >= nr) return;
+  const int64_t row = first + tid;
   uint32_t packed[LW / 4];
 #pragma unroll
   for (int q = 0; q < LW / 4; ++q)
-    packed[q] = (uint32_t)sym[4 * q] | ((uint32_t)sym[4 * q + 1] << 8) | ((uint32_t)sym[4 * q + 2] << 16) |
-                ((uint32_t)sym[4 * q + 3] << 24);
+    packed[q] = (uint32_t)ssym[tid * LW + 4 * q] | ((uint32_t)ssym[tid * LW + 4 * q + 1] << 8) |
+                ((uint32_t)ssym[tid * LW + 4 * q + 2] << 16) | ((uint32_t)ssym[tid * LW + 4 * q + 3] << 24);
   uint4* wo = reinterpret_cast<uint4*>(words + row * LW);
 #pragma unroll
   for (int q = 0; q < LW / 16; ++q)
@@ -513,9 +550,14 @@ __global__ void k_layout(const float* __restrict__ x, int64_t N, int n, const ui
 
 // Int8 copy of every key-sorted canonical series for the refinement filter:
 // scale s = max|z| / 127 (1 for the zero series), v_t = rint(z_t / s) in
-// [-127, 127], and the residual norm e = ||z - s v|| (every term exact in
-// FP64: s v_t has at most 32 significant bits), rounded up to fp32 with a
-// 1e-6 relative cushion.  Warp per series.
+// [-127, 127] (any integer code is valid: the residual is of the codes
+// chosen), and an upper bound e of the residual norm ||z - s v||.  Each
+// residual d_t = fma(-s, v_t, z_t) is rounded once (|d~ - d| <= u |d|, u =
+// 2^-24), and the FP32 sum of the m = ceil(n / 32) + 5 terms a lane and the
+// warp's tree add has relative error <= (m + 1) u (non-negative terms), so
+// ||z - s v||^2 <= e~^2 (1 + u)^2 (1 + (m + 1) u)^... <= e~^2 (1 + (m + 4) 2^-23):
+// e = sqrt_ru(e~^2 (1 + (m + 4) 2^-23)) with a 1e-6 relative cushion.  Warp
+// per series.
 __global__ void k_quant8(const float* __restrict__ Z, int64_t N, int n, int8_t* __restrict__ Z8,
                          float* __restrict__ scale, float* __restrict__ err) {
   const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -526,18 +568,21 @@ __global__ void k_quant8(const float* __restrict__ Z, int64_t N, int n, int8_t* 
   for (int t = lane; t < n; t += 32) mx = fmaxf(mx, fabsf(z[t]));
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
   const float sc = mx > 0.f ? mx / 127.0f : 1.0f;
-  double e2 = 0.0;
+  const float inv = 1.0f / sc;
+  float e2 = 0.f;
   for (int t = lane; t < n; t += 32) {
-    float v = rintf(z[t] / sc);
+    float v = rintf(z[t] * inv);
     v = fminf(fmaxf(v, -127.f), 127.f);
     Z8[p * n + t] = (int8_t)v;
-    const double d = (double)z[t] - (double)sc * (double)v;
-    e2 += d * d;
+    const float d = fmaf(-sc, v, z[t]);
+    e2 = fmaf(d, d, e2);
   }
   for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, o);
   if (lane == 0) {
     scale[p] = sc;
-    err[p] = __double2float_ru(sqrt(e2) * (1.0 + 1e-6) + 1e-30);
+    const float m = (float)((n + 31) / 32 + 5);
+    const float cush = __fadd_ru(1.0f, __fmul_ru(m + 4.0f, 0x1p-23f));
+    err[p] = __fadd_ru(__fmul_ru(__fsqrt_ru(__fmul_ru(e2, cush)), 1.000001f), 1e-30f);
   }
 }
 
@@ -561,58 +606,65 @@ __global__ void k_vweights(int n, int NB, int LW, int l, int nsel, const int32_t
 // W = sum of the weights, so that for the exact values v of the series and q
 // of a query (computed as q~):  ||q - v||_w >= ||q~ - y||_w - r  by the
 // triangle inequality in the weighted norm, and Eq. (1) restricted to the
-// selected values gives ||q - v||_w <= ED.  Thread per series, rows staged in
-// shared memory.
+// selected values gives ||q - v||_w <= ED.  A CTA of WTHREADS threads takes
+// ROWS rows (staged by all threads); thread (r, g) projects row r on columns
+// g*CPT..+CPT in ascending t (one FMA per t and column), the row's maximum
+// and squared residual are reduced over its GPR threads.
 template <int NBT>
-__global__ void k_quantv(const float* __restrict__ Z, int64_t N, int n, const float* __restrict__ basis,
-                         const float* __restrict__ vw, float dmargin, int8_t* __restrict__ vc,
-                         float2* __restrict__ vsr) {
+__global__ void __launch_bounds__(WTHREADS) k_quantv(const float* __restrict__ Z, int64_t N, int n,
+                                                     const float* __restrict__ basis, const float* __restrict__ vw,
+                                                     float dmargin, int8_t* __restrict__ vc,
+                                                     float2* __restrict__ vsr) {
+  constexpr int GPR = WTHREADS / ROWS;  // 8 threads per row
+  constexpr int CPT = NBT / GPR;        // 4 or 8 columns per thread
   extern __shared__ float sm[];
   const int64_t first = (int64_t)blockIdx.x * ROWS;
-  stage_rows(Z, first, N, 1, n, sm);
-  const int r = threadIdx.x;
-  const int64_t row = first + r;
-  if (r >= ROWS || row >= N) return;
-  const float* my = sm + r * (n + 1);
-  float acc[NBT];
+  const int nr = (int)(N - first < ROWS ? N - first : ROWS);
+  stage_rows_vec(Z, first, N, n, sm);
+  const int tid = threadIdx.x, r = tid / GPR, g = tid - r * GPR;
+  const bool active = r < nr;
+  float acc[CPT];
 #pragma unroll
-  for (int j = 0; j < NBT; ++j) acc[j] = 0.f;
-  for (int t = 0; t < n; ++t) {
-    const float zt = my[t];
-    const float4* b = reinterpret_cast<const float4*>(basis + (int64_t)t * NBT);
+  for (int c = 0; c < CPT; ++c) acc[c] = 0.f;
+  if (active) {
+    const float* my = sm + r * (n + 1);
+    const float* bcol = basis + g * CPT;
+    for (int t = 0; t < n; ++t) {
+      const float zt = my[t];
 #pragma unroll
-    for (int j4 = 0; j4 < NBT / 4; ++j4) {
-      const float4 bb = __ldg(b + j4);
-      acc[4 * j4 + 0] = fmaf(zt, bb.x, acc[4 * j4 + 0]);
-      acc[4 * j4 + 1] = fmaf(zt, bb.y, acc[4 * j4 + 1]);
-      acc[4 * j4 + 2] = fmaf(zt, bb.z, acc[4 * j4 + 2]);
-      acc[4 * j4 + 3] = fmaf(zt, bb.w, acc[4 * j4 + 3]);
+      for (int c = 0; c < CPT; ++c) acc[c] = fmaf(zt, __ldg(bcol + (int64_t)t * NBT + c), acc[c]);
     }
   }
   float mx = 0.f;
 #pragma unroll
-  for (int j = 0; j < NBT; ++j) mx = fmaxf(mx, fabsf(acc[j]));
+  for (int c = 0; c < CPT; ++c) mx = fmaxf(mx, fabsf(acc[c]));
+  // the GPR threads of a row are consecutive lanes of one warp
+#pragma unroll
+  for (int o = 1; o < GPR; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
   const float sc = mx > 0.f ? mx / 127.0f : 1.0f;
   double e2 = 0.0;
-  uint32_t packed[NBT / 4];
+  uint32_t packed[CPT / 4];
 #pragma unroll
-  for (int j4 = 0; j4 < NBT / 4; ++j4) {
+  for (int c4 = 0; c4 < CPT / 4; ++c4) {
     uint32_t w = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int j = 4 * j4 + b;
-      const float c = fminf(fmaxf(rintf(acc[j] / sc), -127.f), 127.f);
-      const double d = (double)acc[j] - (double)sc * (double)c;
+      const int c = 4 * c4 + b, j = g * CPT + c;
+      const float code = fminf(fmaxf(rintf(acc[c] / sc), -127.f), 127.f);
+      const double d = (double)acc[c] - (double)sc * (double)code;
       e2 += (double)__ldg(vw + j) * d * d;
-      w |= ((uint32_t)(int)c & 0xFFu) << (8 * b);
+      w |= ((uint32_t)(int)code & 0xFFu) << (8 * b);
     }
-    packed[j4] = w;
+    packed[c4] = w;
   }
-  uint4* o = reinterpret_cast<uint4*>(vc + row * NBT);
 #pragma unroll
-  for (int q = 0; q < NBT / 16; ++q)
-    o[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
-  vsr[row] = make_float2(sc, __double2float_ru(sqrt(e2) * (1.0 + 1e-6) + (double)dmargin + 1e-30));
+  for (int o = 1; o < GPR; o <<= 1) e2 += __shfl_xor_sync(0xFFFFFFFFu, e2, o);
+  if (!active) return;
+  const int64_t row = first + r;
+  uint32_t* o4 = reinterpret_cast<uint32_t*>(vc + row * NBT + g * CPT);
+#pragma unroll
+  for (int c4 = 0; c4 < CPT / 4; ++c4) o4[c4] = packed[c4];
+  if (g == 0) vsr[row] = make_float2(sc, __double2float_ru(sqrt(e2) * (1.0 + 1e-6) + (double)dmargin + 1e-30));
 }
 
 // FP16 copy (round to nearest) of count fp32 values, 4 per thread.
@@ -727,7 +779,7 @@ int launch_znorm(const float* x, int64_t R, int n, float* z, cudaStream_t st) {
   if (R <= 0) return 0;
   size_t smem = (size_t)ROWS * (n + 1) * sizeof(float);
   SOFA_CUDA(cudaFuncSetAttribute(k_rows_project<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_rows_project<true><<<(unsigned)ceil_div(R, ROWS), ROWS, smem, st>>>(x, R, n, 1, nullptr, 0, 0, z, nullptr, 0,
+  k_rows_project<true><<<(unsigned)ceil_div(R, ROWS), WTHREADS, smem, st>>>(x, R, n, 1, nullptr, 0, 0, z, nullptr, 0,
                                                                          nullptr);
   SOFA_CUDA(cudaGetLastError());
   return 0;
@@ -765,7 +817,7 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
   // ---- Alg. 1 step 1: sample, z-normalise, DFT variance of every candidate value
   float* Zs;
   TRY(tmp.get(&Zs, S * n));
-  k_rows_project<true><<<(unsigned)ceil_div(S, ROWS), ROWS, row_smem, st>>>(x, S, n, stride, nullptr, 0, 0, Zs,
+  k_rows_project<true><<<(unsigned)ceil_div(S, ROWS), WTHREADS, row_smem, st>>>(x, S, n, stride, nullptr, 0, 0, Zs,
                                                                              nullptr, 0, nullptr);
   SOFA_CUDA(cudaGetLastError());
   float* Bf;
@@ -818,7 +870,7 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
     float *vals, *sorted;
     TRY(tmp.get(&vals, S * l));
     TRY(tmp.get(&sorted, S * l));
-    k_rows_project<false><<<(unsigned)ceil_div(S, ROWS), ROWS, row_smem, st>>>(Zs, S, n, 1, ix->basis, NB, l,
+    k_rows_project<false><<<(unsigned)ceil_div(S, ROWS), WTHREADS, row_smem, st>>>(Zs, S, n, 1, ix->basis, NB, l,
                                                                                 nullptr, vals, 1, nullptr);
     SOFA_CUDA(cudaGetLastError());
     size_t tb = 0;
@@ -873,15 +925,15 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
   uint64_t* keys1 = ix->keys;
   TRY(tmp.get(&ids0, N));
   TRY(tmp.get(&stats, N));
-  const size_t wsmem = row_smem + (size_t)LW * (alpha + 1) * sizeof(float);
+  const size_t wsmem = row_smem + (size_t)LW * (alpha + 1) * sizeof(float) + (size_t)ROWS * LW;
   if (LW == 16) {
     SOFA_CUDA(cudaFuncSetAttribute(k_words<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
-    k_words<16><<<(unsigned)ceil_div(N, ROWS), ROWS, wsmem, st>>>(x, N, n, ix->basis, NB, ix->beta, alpha, l,
-                                                                   keyorder, keybits, words0, keys0, ids0, stats);
+    k_words<16><<<(unsigned)ceil_div(N, ROWS), WTHREADS, wsmem, st>>>(x, N, n, ix->basis, NB, ix->beta, alpha, l,
+                                                                       keyorder, keybits, words0, keys0, ids0, stats);
   } else {
     SOFA_CUDA(cudaFuncSetAttribute(k_words<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
-    k_words<32><<<(unsigned)ceil_div(N, ROWS), ROWS, wsmem, st>>>(x, N, n, ix->basis, NB, ix->beta, alpha, l,
-                                                                   keyorder, keybits, words0, keys0, ids0, stats);
+    k_words<32><<<(unsigned)ceil_div(N, ROWS), WTHREADS, wsmem, st>>>(x, N, n, ix->basis, NB, ix->beta, alpha, l,
+                                                                       keyorder, keybits, words0, keys0, ids0, stats);
   }
   SOFA_CUDA(cudaGetLastError());
 
@@ -928,11 +980,11 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
     const size_t vsmem = (size_t)ROWS * (n + 1) * sizeof(float);
     if (NB == 32) {
       SOFA_CUDA(cudaFuncSetAttribute(k_quantv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
-      k_quantv<32><<<(unsigned)ceil_div(N, ROWS), ROWS, vsmem, st>>>(ix->Z, N, n, ix->basis, ix->vw, dmargin,
+      k_quantv<32><<<(unsigned)ceil_div(N, ROWS), WTHREADS, vsmem, st>>>(ix->Z, N, n, ix->basis, ix->vw, dmargin,
                                                                      ix->VC, ix->vsr);
     } else {
       SOFA_CUDA(cudaFuncSetAttribute(k_quantv<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
-      k_quantv<64><<<(unsigned)ceil_div(N, ROWS), ROWS, vsmem, st>>>(ix->Z, N, n, ix->basis, ix->vw, dmargin,
+      k_quantv<64><<<(unsigned)ceil_div(N, ROWS), WTHREADS, vsmem, st>>>(ix->Z, N, n, ix->basis, ix->vw, dmargin,
                                                                      ix->VC, ix->vsr);
     }
     SOFA_CUDA(cudaGetLastError());
@@ -962,6 +1014,8 @@ int build_index(Index* ix, const float* x, const sofa_build_opts& o, cudaStream_
   k_leaf_env<<<(unsigned)ceil_div(ix->L * (LW / 4), 256), 256, 0, st>>>(ix->tenv, ix->T, LW, ix->leaf_tiles, ix->L,
                                                                          ix->lenv);
   SOFA_CUDA(cudaGetLastError());
+  // FP16 value codes and constants of the tensor-core series bound
+  TRY(make_tc_codes(ix, st));
   SOFA_CUDA(cudaStreamSynchronize(st));
   ix->Ns = N;
   return 0;
@@ -1042,15 +1096,15 @@ int insert_rows(Index* ix, const float* x, int64_t A, cudaStream_t st) {
   TRY(tmp.get(&keys_b, A));
   TRY(tmp.get(&rows_b, A));
   TRY(tmp.get(&stats, A));
-  const size_t wsmem = row_smem + (size_t)LW * (alpha + 1) * sizeof(float);
+  const size_t wsmem = row_smem + (size_t)LW * (alpha + 1) * sizeof(float) + (size_t)ROWS * LW;
   if (LW == 16) {
     SOFA_CUDA(cudaFuncSetAttribute(k_words<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
-    k_words<16><<<(unsigned)ceil_div(A, ROWS), ROWS, wsmem, st>>>(x, A, n, ix->basis, NB, ix->beta, alpha, l,
+    k_words<16><<<(unsigned)ceil_div(A, ROWS), WTHREADS, wsmem, st>>>(x, A, n, ix->basis, NB, ix->beta, alpha, l,
                                                                    ix->keyorder, ix->keybits, words_b, keys_b,
                                                                    rows_b, stats);
   } else {
     SOFA_CUDA(cudaFuncSetAttribute(k_words<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
-    k_words<32><<<(unsigned)ceil_div(A, ROWS), ROWS, wsmem, st>>>(x, A, n, ix->basis, NB, ix->beta, alpha, l,
+    k_words<32><<<(unsigned)ceil_div(A, ROWS), WTHREADS, wsmem, st>>>(x, A, n, ix->basis, NB, ix->beta, alpha, l,
                                                                    ix->keyorder, ix->keybits, words_b, keys_b,
                                                                    rows_b, stats);
   }
@@ -1084,11 +1138,11 @@ int insert_rows(Index* ix, const float* x, int64_t A, cudaStream_t st) {
         (float)(std::sqrt(2.0 * ix->nsel) * (ix->delta_d + ix->delta_q) * 1.0001), INFINITY);
     if (NB == 32) {
       SOFA_CUDA(cudaFuncSetAttribute(k_quantv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
-      k_quantv<32><<<(unsigned)ceil_div(A, ROWS), ROWS, row_smem, st>>>(Zb, A, n, ix->basis, ix->vw, dmargin, VCb,
+      k_quantv<32><<<(unsigned)ceil_div(A, ROWS), WTHREADS, row_smem, st>>>(Zb, A, n, ix->basis, ix->vw, dmargin, VCb,
                                                                         vsrb);
     } else {
       SOFA_CUDA(cudaFuncSetAttribute(k_quantv<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
-      k_quantv<64><<<(unsigned)ceil_div(A, ROWS), ROWS, row_smem, st>>>(Zb, A, n, ix->basis, ix->vw, dmargin, VCb,
+      k_quantv<64><<<(unsigned)ceil_div(A, ROWS), WTHREADS, row_smem, st>>>(Zb, A, n, ix->basis, ix->vw, dmargin, VCb,
                                                                         vsrb);
     }
     SOFA_CUDA(cudaGetLastError());
@@ -1198,6 +1252,13 @@ int insert_rows(Index* ix, const float* x, int64_t A, cudaStream_t st) {
   ix->T = T;
   ix->L = L;
   ++g_buf_generation;  // recorded query graphs hold the old array addresses
+  // the tensor-core codes of the grown layout (derived from the value codes;
+  // if they cannot be allocated the index stays usable with the word bound)
+  if (ix->VC && make_tc_codes(ix, st) != 0) {
+    release_tc_codes(ix);
+    if (ix->series_bound == 1) ix->series_bound = 0;
+  }
+  SOFA_CUDA(cudaStreamSynchronize(st));
   return 0;
 }
 

@@ -215,6 +215,8 @@ int load_index(Index* ix, FILE* f, cudaStream_t st) {
   rc = rc ? rc : read_array(f, sg, &ix->Zh, z.Zh, true, acct);
   if (rc) return rc;
   if (!ix->Z8 != !ix->VC) return fail(SOFA_ERR_INVALID_ARG, "index file holds only part of the precision copies");
+  if (int rc2 = make_tc_codes(ix, st)) return rc2;  // derived from the value codes, not stored
+  SOFA_CUDA(cudaStreamSynchronize(st));
   if (h.has_mlp)
     if (int rc2 = mlp_load(ix, f, st)) return rc2;
   return 0;

@@ -1629,6 +1629,9 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   const float f16 = std::nextafter((float)(1.0 + (LW / 2 + 5) * std::ldexp(1.0, -11)), 2.0f);
   const float inv_f16 = std::nextafter(1.0f / f16, 0.0f);
   auto scan_fn = h16 ? k_scan<LW, NYQ, true> : k_scan<LW, NYQ, false>;
+  // series-level bound: the SFA word bound, or Eq. (1) on the value codes on
+  // the tensor cores (same candidate store, same refinement)
+  const bool use_tc = ix->series_bound == 1 && vscan_supported(ix);
   // symbol tables, then the per-tile query lists (leaf_tiles x MAX_GROUP bytes)
   const size_t scan_smem = (size_t)LW * MAX_ALPHA * (sizeof(float2) + (h16 ? sizeof(__half2) : 0)) +
                            (size_t)ix->leaf_tiles * MAX_GROUP;
@@ -1766,11 +1769,36 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
       SOFA_CUDA(cudaMemcpyAsync(n_units, s.unit_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToDevice, st));
       ix->prof.end(st);
       ix->prof.begin(3, st);
-      scan_fn<<<nb, 256, scan_smem, st>>>(P, s.units.as<int4>(), n_units, s.leaf_q.as<int>(), qv, thr,
-                                           ix->tenv, ix->words, ix->edge, ix->ch, ix->ch16, f16, inv_f16, qslot,
-                                           s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(),
-                                           pool_cap, pool_n, s.pool_q.as<int>(), s.pool_p.as<uint32_t>(),
-                                           s.pool_lb.as<float>(), s.qpool_cnt.as<int>(), counters);
+      if (use_tc) {  // Eq. (1) on the value codes, one tcgen05 contraction per (unit, tile)
+        VscanArgs V;
+        V.units = s.units.as<int4>();
+        V.n_units = n_units;
+        V.leaf_q = s.leaf_q.as<int>();
+        V.qv = qv;
+        V.thr = thr;
+        V.cap = P.cap;
+        V.qslot = qslot;
+        V.cand_p = s.cand_p.as<uint32_t>();
+        V.cand_lb = s.cand_lb.as<float>();
+        V.cand_n = s.cand_n.as<int>();
+        V.pool_cap = pool_cap;
+        V.pool_n = pool_n;
+        V.pool_q = s.pool_q.as<int>();
+        V.pool_p = s.pool_p.as<uint32_t>();
+        V.pool_lb = s.pool_lb.as<float>();
+        V.qpool_cnt = s.qpool_cnt.as<int>();
+        V.dump = nullptr;
+        V.dumpQ = 0;
+        V.counters = counters;
+        V.status = status;
+        TRYQ(launch_vscan(ix, V, st));
+      } else {
+        scan_fn<<<nb, 256, scan_smem, st>>>(P, s.units.as<int4>(), n_units, s.leaf_q.as<int>(), qv, thr,
+                                             ix->tenv, ix->words, ix->edge, ix->ch, ix->ch16, f16, inv_f16, qslot,
+                                             s.cand_p.as<uint32_t>(), s.cand_lb.as<float>(), s.cand_n.as<int>(),
+                                             pool_cap, pool_n, s.pool_q.as<int>(), s.pool_p.as<uint32_t>(),
+                                             s.pool_lb.as<float>(), s.qpool_cnt.as<int>(), counters);
+      }
       ix->prof.end(st);
     }
     SOFA_CUDA(cudaGetLastError());
@@ -1876,17 +1904,18 @@ static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* i
     SOFA_CUDA(cudaEventCreateWithFlags(&ix->gev[0], cudaEventDisableTiming));
     SOFA_CUDA(cudaEventCreateWithFlags(&ix->gev[1], cudaEventDisableTiming));
   }
-  const int64_t key[15] = {qb, k, ix->bound_precision, ix->refine_filter, ix->seed_mode, ix->group, ix->cand_cap,
-                           ix->seed_count, ix->seed_window, ix->pool_cap, ix->LW, ix->nyq_first, ix->approximate, ix->dense_mode, ix->cand_budget};
+  const int64_t key[16] = {qb, k, ix->bound_precision, ix->refine_filter, ix->seed_mode, ix->group, ix->cand_cap,
+                           ix->seed_count, ix->seed_window, ix->pool_cap, ix->LW, ix->nyq_first, ix->approximate,
+                           ix->dense_mode, ix->cand_budget, ix->series_bound};
   Index::GraphEntry* e = nullptr;
   for (auto& g : ix->graphs)
-    if (std::equal(key, key + 15, g.key)) e = &g;
+    if (std::equal(key, key + 16, g.key)) e = &g;
   if (e && !e->failed && e->gen != g_buf_generation) {  // buffers moved since the recording
     cudaGraphExecDestroy(e->exec);
     e->exec = nullptr;
     e = nullptr;
     ix->graphs.erase(std::remove_if(ix->graphs.begin(), ix->graphs.end(),
-                                    [&](const Index::GraphEntry& g) { return std::equal(key, key + 15, g.key); }),
+                                    [&](const Index::GraphEntry& g) { return std::equal(key, key + 16, g.key); }),
                      ix->graphs.end());
   }
   if (e && e->failed) return dispatch_batch(ix, qp, qb, k, ip, dp, st, false);
@@ -1897,7 +1926,7 @@ static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* i
     SOFA_CUDA(cudaStreamSynchronize(st));
     const unsigned long long gen0 = g_buf_generation;
     Index::GraphEntry ne;
-    std::copy(key, key + 15, ne.key);
+    std::copy(key, key + 16, ne.key);
     ne.exec = nullptr;
     ne.failed = true;
     const bool prof_on = ix->prof.on;

@@ -176,7 +176,7 @@ struct Index {
   int dense_mode = 0;          // 0: dense contraction when the leaf bound prunes little, 1: never, 2: always
   int series_bound = 0;        // 0: SFA word bound (k_scan); 1: value codes on the tensor cores (k_vscan)
   struct GraphEntry {
-    int64_t key[15];
+    int64_t key[16];
     unsigned long long gen;
     cudaGraphExec_t exec;
     bool failed;

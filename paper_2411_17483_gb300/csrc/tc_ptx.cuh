@@ -35,10 +35,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 }
 
 // Wait for the completion of the phase with the given parity; false when the
-// wait ran out (2 s).
+// wait ran out (2 s).  The clock is read only once the wait has polled 64
+// times without success, so a wait that completes promptly never touches
+// the global timer.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
-  const unsigned long long t0 = global_ns();
+  unsigned long long t0 = 0;
   for (uint32_t it = 0;; ++it) {
     uint32_t done;
     asm volatile(
@@ -49,7 +51,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 63) == 63 && global_ns() - t0 > WAIT_NS) return false;
+    if (it == 64) t0 = global_ns();
+    else if (it > 64 && (it & 63) == 0 && global_ns() - t0 > WAIT_NS) return false;
   }
 }
 

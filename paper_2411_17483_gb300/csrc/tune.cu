@@ -24,7 +24,7 @@ static std::string tune_key(const Index* ix, int k, int64_t Q) {
   int64_t qb = Q <= 256 ? 256 : Q <= 4096 ? 4096 : 65536;
   std::ostringstream s;
   s << prop.name << "|N=" << ix->N << "|n=" << ix->n << "|l=" << ix->l << "|k<=" << kb << "|Q<=" << qb
-    << "|filter=" << (ix->Z8 ? 1 : 0) << "|learned=" << ix->seed_mode;
+    << "|filter=" << (ix->Z8 ? 1 : 0) << "|tc=" << (vscan_supported(ix) ? 1 : 0) << "|learned=" << ix->seed_mode;
   std::string key = s.str();
   for (char& c : key)
     if (c == ' ') c = '_';
@@ -44,6 +44,8 @@ static bool cache_lookup(const char* path, const std::string& key, const sofa_tu
     if (ls >> k >> c.group >> c.cand_cap >> c.seed_count >> c.seed_window >> c.bound_precision >> pool >>
         c.refine_filter) {
       c.pool_cap = pool;
+      int sb = 0;
+      if (ls >> sb) c.series_bound = sb;  // absent in lines written before this knob
       if (k == key) {
         *t = c;
         return true;
@@ -57,7 +59,8 @@ static void cache_store(const char* path, const std::string& key, const sofa_tun
   if (!path) return;
   std::ofstream out(path, std::ios::app);
   out << key << " " << c.group << " " << c.cand_cap << " " << c.seed_count << " " << c.seed_window << " "
-      << c.bound_precision << " " << (long long)c.pool_cap << " " << c.refine_filter << "\n";
+      << c.bound_precision << " " << (long long)c.pool_cap << " " << c.refine_filter << " " << c.series_bound
+      << "\n";
 }
 
 static void apply(Index* ix, const sofa_tuning& t) {
@@ -72,6 +75,7 @@ static void apply(Index* ix, const sofa_tuning& t) {
   ix->cand_budget = t.cand_budget ? t.cand_budget : ((int64_t)1 << 30);
   ix->dense_mode = t.dense;
   ix->approximate = t.approximate;
+  ix->series_bound = t.series_bound == 1 && vscan_supported(ix) ? 1 : 0;
 }
 
 }  // namespace sofa
@@ -100,6 +104,7 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
   cur.cand_budget = ix->cand_budget;
   cur.dense = ix->dense_mode;
   cur.approximate = ix->approximate;
+  cur.series_bound = ix->series_bound;
   sofa_tuning best = cur;
   if (cache_lookup(cache_path, key, cur, &best)) {
     apply(ix, best);
@@ -112,18 +117,21 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
   const int groups[] = {32, 64};
   const int windows[] = {1024, 4096};
   const int counts[] = {64, 128, 256};
+  const int max_bound = vscan_supported(ix) ? 1 : 0;
   for (int g : groups)
     for (int w : windows)
       for (int c : counts)
-        for (int f = 0; f <= ((ix->Z8 && ix->VC) ? 2 : 0); ++f) {
-          sofa_tuning t = cur;
-          t.group = g;
-          t.seed_window = w;
-          t.seed_count = c;
-          t.refine_filter = f;
-          t.bound_precision = 0;
-          cands.push_back(t);
-        }
+        for (int f = 0; f <= ((ix->Z8 && ix->VC) ? 2 : 0); ++f)
+          for (int sb = 0; sb <= max_bound; ++sb) {
+            sofa_tuning t = cur;
+            t.group = g;
+            t.seed_window = w;
+            t.seed_count = c;
+            t.refine_filter = f;
+            t.bound_precision = 0;
+            t.series_bound = sb;
+            cands.push_back(t);
+          }
   DevBuf outi, outd;
   if (int rc = outi.ensure((size_t)Q * k * sizeof(int64_t))) return rc;
   if (int rc = outd.ensure((size_t)Q * k * sizeof(float))) return rc;

@@ -1,0 +1,612 @@
+// Series bound on the tensor cores: Eq. (1) restricted to the NB selected
+// Fourier values (Sec. IV "SFA", Eq. 1; the lower bound GEMINI prunes with,
+// Sec. II-A), evaluated from int8 value codes for every (series, query) pair
+// of a work unit's surviving tiles as one tcgen05 contraction per tile.
+//
+// Each series x of the index holds its selected values v as int8 codes c with
+// one scale s (y = s c, exact) and a margin r >= ||v - y||_w + (projection
+// error), see k_quantv.  For a query with computed values q~:
+//   ||q~ - y||_w^2 = ||q~||_w^2 + s^2 ||c||_w^2 - 2 s (w o q~) . c,
+// and ||q - v||_w >= ||q~ - y||_w - r, ||q - v||_w <= ED (Parseval).  The
+// dot products (w o q~) . c of a tile's 256 series (rows, M) and a unit's up
+// to 64 queries (columns, N) are one MMA of K = NB on the tensor cores: the
+// codes are exact in FP16 (|c| <= 127), the query operand w o q~ is rounded to
+// FP16, the accumulation is FP32.  A derived margin M' bounds every error of
+// that contraction and of the epilogue's FP32 arithmetic (tc_margin below),
+// so a pair is pruned only when
+//   sqrt(max(e~ - M', 0)) - r > sqrt(2 T)      (T: the query's threshold),
+// which implies ED > sqrt(2 T): no series that can reach the first k places
+// is pruned.  Leaf blocks and tiles are still pruned by their SFA symbol
+// envelopes first, exactly as in the word scan.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bounds.cuh"
+#include "sofa_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace sofa {
+
+constexpr int VS_WARPS = 10;             // 8 epilogue warps, 1 TMA producer, 1 MMA issuer
+constexpr int VS_THREADS = 32 * VS_WARPS;
+constexpr int VS_EPI = 256;              // epilogue threads: one series of the tile each
+constexpr int VS_N = 64;                 // queries per MMA (the work unit's capacity)
+constexpr int VS_TMEM = 256;             // two accumulators of 2 halves x 64 columns
+constexpr int MAX_LEAF_TILES_VS = 256;
+
+template <int NB>
+struct VsCfg {
+  static constexpr int ROWB = NB * 2;             // bytes of one operand row (64 or 128)
+  static constexpr int ATILE = TILE * ROWB;       // codes of one tile (16 KB or 32 KB)
+  static constexpr int BTILE = VS_N * ROWB;       // query operand of one unit (4 KB or 8 KB)
+  static constexpr int STAGES = NB == 32 ? 3 : 2; // TMA pipeline depth (two CTAs per SM at NB = 32)
+  static constexpr int MIN_CTAS = NB == 32 ? 2 : 1;
+  static constexpr int KSTEPS = NB / 16;          // MMAs of K = 16 per half
+};
+
+// Instruction descriptor of tcgen05.mma kind::f16: D fp32 (bits 4-5 = 1), A
+// and B f16 (bits 7-9, 10-12 = 0), both K-major, N = 64 (bits 17-22: N >> 3),
+// M = 128 (bits 24-28: M >> 4).
+__host__ __device__ constexpr uint32_t vscan_idesc() {
+  return (1u << 4) | ((uint32_t)(VS_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int NB>
+__device__ __forceinline__ uint64_t vs_desc(uint32_t saddr) {
+  if constexpr (NB == 32) return sw64_desc(saddr);
+  else return sw128_desc(saddr);
+}
+
+// Physical 16-byte chunk of logical chunk c in row r of a K-major operand
+// tile with the TMA swizzle of its row size (address bits [4, 4+b) are
+// XORed with bits [7, 7+b): b = 2 for 64-byte rows, 3 for 128-byte rows).
+template <int NB>
+__device__ __forceinline__ int vs_chunk(int r, int c) {
+  if constexpr (NB == 32) return c ^ ((r >> 1) & 3);
+  else return c ^ (r & 7);
+}
+
+__device__ __forceinline__ void mma_f16_n64(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(vscan_idesc()), "r"(accumulate));
+}
+
+// Four accumulator columns of this thread's TMEM lane, one wait.
+__device__ __forceinline__ void tmem_ld1x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, float* v) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%4];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%1}, [%5];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%2}, [%6];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%3}, [%7];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+      : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ------------------------------------------------------------------------
+// Derived per-series arrays of the tensor-core bound, from the value codes:
+// VH[p] = the codes as FP16 (exact); vcx[p] = (-2 s, -2 r, S', 0) with
+// S = s^2 ||c||_w^2 (FP64, rounded down) and S' = S - r^2 - M' rounded down.
+__global__ void k_vcodes_tc(const int8_t* __restrict__ VC, const float2* __restrict__ vsr,
+                            const float* __restrict__ vw, int64_t N, int NB, float Mp, __half* __restrict__ VH,
+                            float4* __restrict__ vcx) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double cw = 0.0;
+  for (int j = 0; j < NB; ++j) {
+    const int c = VC[p * NB + j];
+    VH[p * NB + j] = __int2half_rn(c);
+    cw += (double)vw[j] * (double)(c * c);
+  }
+  const float2 sr = vsr[p];
+  const double S = (double)sr.x * (double)sr.x * cw;
+  const float r2 = __fmul_ru(sr.y, sr.y);
+  const float Sp = __fsub_rd(__fsub_rd(__double2float_rd(S), r2), Mp);
+  vcx[p] = make_float4(-2.0f * sr.x, -2.0f * sr.y, Sp, 0.f);
+}
+
+// The margin M' >= |e~ - ||q~ - y||_w^2| of the tensor-core form plus the
+// rounding of the epilogue.  With R = sqrt(n) (1 + 2^-20) + sqrt(W) (delta_d
+// + delta_q) >= ||q~||_w, ||v~||_w (Parseval; W <= 2 nsel) and ||y||_w <= 1.04 R
+// (||v~ - y||_w <= sqrt(W) s / 2, s = max|v~| / 127):
+//  * query operand rounded to FP16: |fl(b) - b| <= 2^-11 |b| (+2^-25 below the
+//    normal range), so |2 s (fl(b) - b) . c| <= 2 (2^-11 + 2^-24) ||y||_w ||q~||_w
+//    + 2 s 127 NB 2^-25;
+//  * FP32 accumulation of NB products, up to 2 ulps each:
+//    2 NB 2^-22 ||y||_w ||q~||_w (1 + 2^-10);
+//  * ||q~||_w^2 summed in FP32 over NB terms: (NB + 1) 2^-24 R^2;
+//  * the epilogue (stored S, r^2, two FMAs and the comparison's terms, each
+//    at most 8 R^2 in magnitude): 64 2^-24 R^2.
+double tc_margin(const Index* ix) {
+  const double n = ix->n, W = 2.0 * ix->nsel;
+  const double R = std::sqrt(n) * (1.0 + std::ldexp(1.0, -20)) + std::sqrt(W) * (ix->delta_d + ix->delta_q);
+  const double Y = 1.04 * R;
+  const double m_tc = 2.0 * (std::ldexp(1.0, -11) + std::ldexp(1.0, -24)) * Y * R +
+                      2.0 * (R / 127.0) * 127.0 * ix->NB * std::ldexp(1.0, -25);
+  const double m_acc = 2.0 * ix->NB * std::ldexp(1.0, -22) * Y * R * (1.0 + std::ldexp(1.0, -10));
+  const double m_ep = (64.0 + ix->NB + 1) * std::ldexp(1.0, -24) * R * R;
+  return (m_tc + m_acc + m_ep) * 1.01;
+}
+
+int make_tc_codes(Index* ix, cudaStream_t st) {
+  if (!ix->VC || !ix->vsr || !ix->vw) return 0;
+  release_tc_codes(ix);
+  const size_t hb = (size_t)ix->N * ix->NB * sizeof(__half), xb = (size_t)ix->N * sizeof(float4);
+  if (cudaMalloc((void**)&ix->VH, hb) != cudaSuccess || cudaMalloc((void**)&ix->vcx, xb) != cudaSuccess) {
+    cudaGetLastError();
+    release_tc_codes(ix);
+    return fail(SOFA_ERR_OOM, "allocation of the tensor-core value codes failed");
+  }
+  ix->tc_bytes = (int64_t)(hb + xb);
+  ix->device_bytes += ix->tc_bytes;
+  ix->tc_margin = (float)tc_margin(ix);
+  k_vcodes_tc<<<(unsigned)ceil_div(ix->N, 256), 256, 0, st>>>(ix->VC, ix->vsr, ix->vw, ix->N, ix->NB,
+                                                               ix->tc_margin, ix->VH, ix->vcx);
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
+void release_tc_codes(Index* ix) {
+  if (ix->VH) cudaFree(ix->VH);
+  if (ix->vcx) cudaFree(ix->vcx);
+  ix->VH = nullptr;
+  ix->vcx = nullptr;
+  ix->device_bytes -= ix->tc_bytes;
+  ix->tc_bytes = 0;
+}
+
+// ------------------------------------------------------------------------
+// The tensor-core series scan.  A persistent CTA takes work units (leaf
+// block, up to 64 queries).  All warps first stage the unit: the queries'
+// SFA values (for the tile envelope checks), their FP16 operand w o q~ in the
+// swizzled layout the MMA reads, and their constants a = sqrt(2 T) rounded up
+// and c = a^2 - ||q~||_w^2; then the tile envelope checks give each tile its
+// mask of live queries (as in the word scan) and a list of live tiles.  Then:
+// warp 8 streams the live tiles' FP16 codes by TMA into a ring of stages;
+// warp 9 issues per tile 2 halves x NB/16 MMAs (M = 128 series, N = 64
+// queries, K = 16) into one of two TMEM accumulators; warps 0-7 (thread i =
+// series i of the tile) read, per live query, its accumulator column and
+// test  fma(-2r, a, fma(-2s, D, S')) <= c,  emitting survivors into the
+// candidate store with warp-aggregated atomics.  Every wait is bounded; a
+// wait that runs out stops all roles, lets issued copies and MMAs finish,
+// and sets SOFA_ERR_TIMEOUT.  With `dump` the kernel instead writes every
+// pair's lower bound (Q x N, original order) and emits nothing.
+template <int NB, bool NYQ>
+__global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
+    k_vscan(const __grid_constant__ CUtensorMap tmA, int64_t N, int64_t T, int n_leaf_tiles, int NBq,
+            const int4* __restrict__ units, const int* __restrict__ n_units_ptr, const int* __restrict__ leaf_q,
+            const float* __restrict__ qv, const float* __restrict__ thr, const uint8_t* __restrict__ tenv,
+            const float2* __restrict__ ch, const float4* __restrict__ vcx, const float* __restrict__ vw,
+            int cap, const int* __restrict__ qslot, uint32_t* __restrict__ cand_p, float* __restrict__ cand_lb,
+            int* __restrict__ cand_n, int64_t pool_cap, int* __restrict__ pool_n, int* __restrict__ pool_q,
+            uint32_t* __restrict__ pool_p, float* __restrict__ pool_lb, int* __restrict__ qpool_cnt,
+            float* __restrict__ dump, int64_t dumpQ, const uint32_t* __restrict__ perm,
+            unsigned long long* __restrict__ counters, int* __restrict__ status) {
+  constexpr int LW = NB / 2;
+  using C = VsCfg<NB>;
+  extern __shared__ __align__(16) uint8_t vsm[];
+  float2* sch = reinterpret_cast<float2*>(vsm);  // LW x 256 (tile checks)
+  const uint32_t raw = smem_u32(vsm);
+  const uint32_t tab_end = raw + (uint32_t)(LW * MAX_ALPHA * sizeof(float2));
+  uint8_t* stages = vsm + (((tab_end + 1023u) & ~1023u) - raw);  // 1024-byte aligned swizzle atoms
+  uint8_t* sB = stages + C::STAGES * C::ATILE;
+  __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], tfull[2], tempty[2], drain;
+  __shared__ uint16_t s_off[MAX_LEAF_TILES_VS + 1];
+  __shared__ uint16_t stl[MAX_LEAF_TILES_VS];
+  __shared__ __align__(16) float sq[VS_N][LW];
+  __shared__ float sT[VS_N], sQw[VS_N];
+  __shared__ float2 sAC[VS_N];  // (a, c) of each query: a = sqrt(2 T) rounded up, c = a^2 - ||q~||_w^2
+  __shared__ int sslot[VS_N], sqid[VS_N];
+  __shared__ unsigned long long smask[MAX_LEAF_TILES_VS];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_fail, s_ntl;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  volatile int* vfail = &s_fail;
+  for (int e = tid; e < LW * MAX_ALPHA; e += blockDim.x) sch[e] = ch[e];
+  if (warp == 9) tmem_alloc(&s_tmem, VS_TMEM);
+  if (tid == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], VS_EPI);
+    }
+    mbar_init(&drain, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  unsigned long long n_tile_pairs = 0, n_cand = 0, n_loads = 0, n_checks = 0;
+  long long gi = 0;  // running index of this CTA's live tiles (the same in every role)
+  const int n_units = *n_units_ptr;
+  for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+    __syncthreads();
+    if (*vfail) break;  // read after the barrier: the same verdict in every thread
+    const int4 un = units[u];
+    const int64_t b = un.x;
+    const int cnt = un.z;
+    const int64_t t0 = b * n_leaf_tiles;
+    const int nt = (int)((T - t0) < n_leaf_tiles ? (T - t0) : n_leaf_tiles);
+    // ---- stage the unit's queries
+    for (int e = tid; e < cnt * LW; e += blockDim.x) {
+      const int g = e / LW, j = e - g * LW;
+      const int qq = leaf_q[un.y + g];
+      sq[g][j] = qv[(int64_t)qq * NBq + j];
+      if (j == 0) {
+        sqid[g] = qq;
+        sslot[g] = qslot ? qslot[qq] : qq;
+        sT[g] = dump ? 0.f : thr[qq];
+      }
+    }
+    constexpr int CH = NB / 8;  // 16-byte chunks of an operand row
+    for (int e = tid; e < VS_N * CH; e += blockDim.x) {
+      const int g = e / CH, c = e - g * CH;
+      __align__(16) __half hv[8];
+      if (g < cnt) {
+        const int qq = leaf_q[un.y + g];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) hv[i] = __float2half_rn(__ldg(vw + 8 * c + i) * qv[(int64_t)qq * NBq + 8 * c + i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) hv[i] = __float2half_rn(0.f);
+      }
+      *reinterpret_cast<uint4*>(sB + g * C::ROWB + vs_chunk<NB>(g, c) * 16) = *reinterpret_cast<const uint4*>(hv);
+    }
+    fence_proxy_async();  // the operand's generic stores, before the MMAs read it
+    for (int t = tid; t < nt; t += blockDim.x) smask[t] = 0ull;
+    __syncthreads();
+    if (tid < cnt) {
+      // ||q~||_w^2 in FP32 (its rounding, <= (NB + 1) 2^-24 ||q~||_w^2, is part of M')
+      const int qq = sqid[tid];
+      float Qw = 0.f;
+      for (int j = 0; j < NB; ++j) {
+        const float v = qv[(int64_t)qq * NBq + j];
+        Qw = fmaf(__ldg(vw + j) * v, v, Qw);
+      }
+      const float a = __fsqrt_ru(__fmul_ru(2.0f, sT[tid]));
+      sQw[tid] = Qw;
+      sAC[tid] = make_float2(a, __fsub_ru(__fmul_ru(a, a), Qw));
+    }
+    // ---- tile envelope checks (every pair when dumping)
+    if (dump) {
+      const unsigned long long all = cnt >= 64 ? ~0ull : ((1ull << cnt) - 1ull);
+      for (int t = tid; t < nt; t += blockDim.x) smask[t] = all;
+    } else {
+      for (int e = tid; e < nt * cnt; e += blockDim.x) {
+        const int t = e / cnt, g = e - t * cnt;
+        const float a = env_bound_ch<LW, NYQ>(tenv + (t0 + t) * 2 * LW, sq[g], sch);
+        if (a <= sT[g]) atomicOr(&smask[t], 1ull << g);
+      }
+      n_checks += (tid == 0) ? (unsigned long long)nt : 0ull;
+    }
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of the per-tile counts; the live tiles in order
+      int run = 0, nl = 0;
+      for (int base = 0; base < nt; base += 32) {
+        const int t = base + lane;
+        const int c = t < nt ? __popcll(smask[t]) : 0;
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (t < nt) s_off[t] = (uint16_t)(run + x - c);
+        run += __shfl_sync(0xFFFFFFFFu, x, 31);
+        const unsigned live = __ballot_sync(0xFFFFFFFFu, c > 0);
+        if (c > 0) stl[nl + __popc(live & ((1u << lane) - 1u))] = (uint16_t)t;
+        nl += __popc(live);
+      }
+      if (lane == 0) {
+        s_off[nt] = (uint16_t)run;
+        s_ntl = nl;
+      }
+    }
+    __syncthreads();
+    const int ntl = s_ntl;
+    if (warp == 8) {
+      if (lane == 0) {  // TMA producer
+        for (int i = 0; i < ntl; ++i) {
+          const long long g_ = gi + i;
+          const int s = (int)(g_ % C::STAGES);
+          if (g_ >= C::STAGES && !mbar_wait(&empty[s], (uint32_t)(((g_ / C::STAGES) - 1) & 1))) {
+            *vfail = 1;
+            break;
+          }
+          if (*vfail) break;
+          mbar_expect_tx(&full[s], C::ATILE);
+          tma_load_2d(stages + s * C::ATILE, &tmA, 0, (int)((t0 + stl[i]) * TILE), &full[s]);
+        }
+      }
+    } else if (warp == 9) {
+      if (lane == 0) {  // MMA issuer
+        const uint32_t sb = smem_u32(sB);
+        for (int i = 0; i < ntl; ++i) {
+          const long long g_ = gi + i;
+          const int s = (int)(g_ % C::STAGES), acc = (int)(g_ & 1);
+          if (g_ >= 2 && !mbar_wait(&tempty[acc], (uint32_t)(((g_ >> 1) - 1) & 1))) {
+            *vfail = 1;
+            break;
+          }
+          if (!mbar_wait(&full[s], (uint32_t)((g_ / C::STAGES) & 1))) {
+            *vfail = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(stages + s * C::ATILE);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int kk = 0; kk < C::KSTEPS; ++kk)
+              mma_f16_n64(tmem + (uint32_t)(acc * 128 + h * 64), vs_desc<NB>(sa + h * 128 * C::ROWB) + 2 * kk,
+                          vs_desc<NB>(sb) + 2 * kk, kk > 0 ? 1u : 0u);
+          mma_commit(&empty[s]);
+          mma_commit(&tfull[acc]);
+        }
+      }
+    } else {
+      // epilogue: thread tid = series tid of the tile; TMEM lanes of its warp's
+      // quadrant, columns of its half
+      const int half = warp >> 2;
+      const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+      for (int i = 0; i < ntl; ++i) {
+        const long long g_ = gi + i;
+        const int acc = (int)(g_ & 1);
+        const int t = stl[i];
+        const int o0 = s_off[t], o1 = s_off[t + 1];
+        const int64_t p = (t0 + t) * TILE + tid;
+        const bool valid = p < N;
+        const float4 cx = valid ? __ldg(vcx + p) : make_float4(0.f, 0.f, INFINITY, 0.f);
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait(&tfull[acc], (uint32_t)((g_ >> 1) & 1)))) {
+          *vfail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tb = tmem + lane_base + (uint32_t)(acc * 128 + half * 64);
+        if (tid == 0) {
+          n_tile_pairs += (unsigned long long)(o1 - o0);
+          n_loads += 1;
+        }
+        const unsigned long long tmask = smask[t];
+        // the tile's live queries, 32 accumulator columns at a time: one TMEM
+        // load per half, then a walk over the mask bits (uniform in the CTA)
+#pragma unroll 1
+        for (int h32 = 0; h32 < 2; ++h32) {
+          const uint32_t m = (uint32_t)(tmask >> (32 * h32));
+          if (m == 0u) continue;
+          float v[32];
+          tmem_ld32(tb + (uint32_t)(32 * h32), v);  // warp-collective
+          if (dump) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (!(m & (1u << j)) || !valid) continue;
+              const int g = 32 * h32 + j;
+              const float rr = -0.5f * cx.y;
+              const float el = fmaf(cx.x, v[j], cx.z) + sQw[g] + __fmul_rd(rr, rr);
+              const float mm = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(el, 0.f)), rr), 0.f);
+              dump[(int64_t)sqid[g] * N + perm[p]] = __fmul_rd(mm, mm);
+            }
+            continue;
+          }
+          uint32_t mine = 0u;  // bit j: this lane's series survives query 32 h32 + j
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (m & (1u << j)) {
+              const int g = 32 * h32 + j;
+              const float2 ac = sAC[g];
+              float uu = fmaf(cx.x, v[j], cx.z);
+              uu = fmaf(cx.y, ac.x, uu);
+              if (uu <= ac.y) mine |= 1u << j;
+            }
+          }
+          if (!valid) mine = 0u;
+          uint32_t any = __reduce_or_sync(0xFFFFFFFFu, mine);
+          while (any) {  // rare: the columns where some lane of the warp survives
+            const int j = __ffs(any) - 1;
+            any &= any - 1u;
+            const int g = 32 * h32 + j;
+            const bool live = (mine >> j) & 1u;
+            const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
+            float dcol[4];
+            tmem_ld1x4(tb + (uint32_t)g, tb + (uint32_t)g, tb + (uint32_t)g, tb + (uint32_t)g, dcol);
+            float acc_lb = 0.f;
+            if (live) {  // the pair's lower bound in half units, rounded down
+              const float rr = -0.5f * cx.y;
+              const float el = fmaf(cx.x, dcol[0], cx.z) + sQw[g] + __fmul_rd(rr, rr);
+              const float mm = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(el, 0.f)), rr), 0.f);
+              acc_lb = __fmul_rd(__fmul_rd(mm, mm), 0.5f);
+            }
+            const int qs = sslot[g];
+            const int npop = __popc(hit);
+            int base = 0, pbase = 0;
+            if (lane == 0) base = atomicAdd(cand_n + qs, npop);
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            const int over0 = base > cap ? base : cap;
+            const int nover = base + npop - over0;
+            if (lane == 0 && nover > 0) {
+              // the pool counter grows only while the pool has room (it cannot wrap)
+              pbase = *reinterpret_cast<volatile int*>(pool_n) < pool_cap ? atomicAdd(pool_n, nover) : (int)pool_cap;
+              const int64_t room = pool_cap - pbase;
+              const int written = room <= 0 ? 0 : (room < nover ? (int)room : nover);
+              if (written > 0) atomicAdd(qpool_cnt + qs, written);
+            }
+            pbase = __shfl_sync(0xFFFFFFFFu, pbase, 0);
+            if (live) {
+              const int slot = base + __popc(hit & ((1u << lane) - 1u));
+              if (slot < cap) {
+                cand_p[(int64_t)qs * cap + slot] = (uint32_t)p;
+                cand_lb[(int64_t)qs * cap + slot] = acc_lb;
+              } else {
+                const int64_t pi = (int64_t)pbase + (slot - over0);
+                if (pi < pool_cap) {
+                  pool_q[pi] = qs;
+                  pool_p[pi] = (uint32_t)p;
+                  pool_lb[pi] = acc_lb;
+                }
+              }
+            }
+            if (lane == 0) n_cand += (unsigned long long)npop;
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[acc]);  // the accumulator is free for the MMA warp
+      }
+    }
+    gi += ntl;
+  }
+  // drain: the MMA warp's issued MMAs and the producer's issued copies finish
+  // before the tensor memory is freed and the CTA exits (they always have on
+  // the normal path; after a timed-out wait this waits for them, bounded)
+  __syncthreads();
+  if (warp == 9 && lane == 0) {
+    mma_commit(&drain);
+    if (!mbar_wait(&drain, 0u)) *vfail = 1;
+  }
+  if (warp == 8 && lane == 0 && *vfail) {
+    for (long long g_ = gi > C::STAGES ? gi - C::STAGES : 0; g_ < gi; ++g_)
+      mbar_wait(&full[g_ % C::STAGES], (uint32_t)((g_ / C::STAGES) & 1));
+  }
+  __syncthreads();
+  if (warp == 9) {
+    tc_fence_after();
+    tmem_dealloc(tmem, VS_TMEM);
+  }
+  if (tid == 0 && *vfail) atomicExch(status, SOFA_ERR_TIMEOUT);
+  if (n_tile_pairs) atomicAdd(counters + 1, n_tile_pairs);
+  if (n_cand) atomicAdd(counters + 2, n_cand);
+  if (n_loads) atomicAdd(counters + 4, n_loads);
+  if (n_checks) atomicAdd(counters + 5, n_checks);
+}
+
+// ------------------------------------------------------------------------
+// host side
+
+static size_t vscan_smem(const Index* ix) {
+  const int LW = ix->LW;
+  const size_t tab = (size_t)LW * MAX_ALPHA * sizeof(float2);
+  const size_t stage = ix->NB == 32 ? (size_t)VsCfg<32>::STAGES * VsCfg<32>::ATILE + VsCfg<32>::BTILE
+                                    : (size_t)VsCfg<64>::STAGES * VsCfg<64>::ATILE + VsCfg<64>::BTILE;
+  return tab + 1024 + stage;
+}
+
+bool vscan_supported(const Index* ix) {
+  return ix->VH && ix->vcx && (ix->NB == 32 || ix->NB == 64) && ix->leaf_tiles <= MAX_LEAF_TILES_VS &&
+         ix->group <= VS_N;
+}
+
+template <int NB, bool NYQ>
+static int launch_vscan_t(Index* ix, const VscanArgs& A, cudaStream_t st) {
+  CUtensorMap tm;
+  if (int rc = make_tensor_map_2d(&tm, ix->VH, ix->N, NB, 2, NB, TILE, NB == 32 ? 64 : 128)) return rc;
+  const size_t smem = vscan_smem(ix);
+  auto fn = k_vscan<NB, NYQ>;
+  SOFA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // all of the SM's unified memory as shared memory, so that two CTAs fit
+  SOFA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+  int sms = 0, dev = 0, smem_sm = 0, regs_sm = 0;
+  SOFA_CUDA(cudaGetDevice(&dev));
+  SOFA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SOFA_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  SOFA_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  cudaFuncAttributes fa;
+  SOFA_CUDA(cudaFuncGetAttributes(&fa, fn));
+  // resident CTAs per SM from the kernel's own resources: shared memory
+  // (dynamic + static + the 1 KB the system reserves per CTA), registers
+  // (allocated per warp in units of 256), and the tensor memory (each CTA
+  // holds VS_TMEM of the SM's 512 columns for its lifetime)
+  const int64_t smem_cta = (int64_t)smem + fa.sharedSizeBytes + 1024;
+  const int64_t regs_cta = (int64_t)VS_WARPS * (((int64_t)fa.numRegs * 32 + 255) / 256 * 256);
+  int per_sm = (int)std::min<int64_t>(smem_sm / smem_cta, regs_sm / std::max<int64_t>(1, regs_cta));
+  per_sm = std::max(1, std::min(per_sm, 512 / VS_TMEM));
+  const int grid = sms * per_sm;
+  fn<<<grid, VS_THREADS, smem, st>>>(tm, ix->N, ix->T, ix->leaf_tiles, ix->NB, A.units, A.n_units, A.leaf_q, A.qv,
+                                     A.thr, ix->tenv, ix->ch, ix->vcx, ix->vw, A.cap, A.qslot, A.cand_p, A.cand_lb,
+                                     A.cand_n, A.pool_cap, A.pool_n, A.pool_q, A.pool_p, A.pool_lb, A.qpool_cnt,
+                                     A.dump, A.dumpQ, ix->perm, A.counters, A.status);
+  SOFA_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int launch_vscan(Index* ix, const VscanArgs& A, cudaStream_t st) {
+  if (!vscan_supported(ix)) return fail(SOFA_ERR_INVALID_ARG, "the tensor-core bound needs the value codes");
+  if (ix->NB == 32)
+    return ix->nyq_first ? launch_vscan_t<32, true>(ix, A, st) : launch_vscan_t<32, false>(ix, A, st);
+  return ix->nyq_first ? launch_vscan_t<64, true>(ix, A, st) : launch_vscan_t<64, false>(ix, A, st);
+}
+
+}  // namespace sofa
+
+using namespace sofa;
+
+// Every pair's tensor-core lower bound (see sofa.h): the scan kernel in its
+// dump mode over units that pair every leaf block with every query (all
+// tiles live, no envelope checks).
+extern "C" int sofa_value_bounds(sofa_handle h, const float* queries, int64_t Q, float* out, float* margin,
+                                 sofa_stream stream) {
+  if (!h || !queries || !out) return fail(SOFA_ERR_INVALID_ARG, "null argument");
+  if (Q < 1 || Q * h->N > ((int64_t)1 << 31)) return fail(SOFA_ERR_INVALID_ARG, "need 1 <= Q and Q * N <= 2^31");
+  if (!vscan_supported(h)) return fail(SOFA_ERR_INVALID_ARG, "the tensor-core bound needs an index with precision >= 1");
+  if (!is_device_ptr(queries) || !is_device_ptr(out))
+    return fail(SOFA_ERR_INVALID_ARG, "queries and out must be device memory");
+  if (int rc = check_device(h)) return rc;
+  Index* ix = h;
+  cudaStream_t st = (cudaStream_t)stream;
+  QueryScratch& s = ix->qs;
+  if (int rc = s.zq.ensure((size_t)Q * ix->n * sizeof(float))) return rc;
+  if (int rc = s.qv.ensure((size_t)Q * ix->NB * sizeof(float))) return rc;
+  if (int rc = s.counters.ensure(16 * sizeof(unsigned long long))) return rc;
+  if (int rc = launch_qprep(ix, queries, Q, s.zq.as<float>(), s.qv.as<float>(), st)) return rc;
+  std::vector<int4> units;
+  std::vector<int> lq((size_t)ix->L * Q);
+  for (int64_t b = 0; b < ix->L; ++b) {
+    for (int64_t i = 0; i < Q; ++i) lq[(size_t)(b * Q + i)] = (int)i;
+    for (int64_t g0 = 0; g0 < Q; g0 += VS_N)
+      units.push_back(make_int4((int)b, (int)(b * Q + g0), (int)std::min<int64_t>(VS_N, Q - g0), 0));
+  }
+  DevBuf du, dl, dn;
+  if (int rc = du.ensure(units.size() * sizeof(int4))) return rc;
+  if (int rc = dl.ensure(lq.size() * sizeof(int))) return rc;
+  if (int rc = dn.ensure(sizeof(int))) return rc;
+  const int nu = (int)units.size();
+  SOFA_CUDA(cudaMemcpyAsync(du.p, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  SOFA_CUDA(cudaMemcpyAsync(dl.p, lq.data(), lq.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  SOFA_CUDA(cudaMemcpyAsync(dn.p, &nu, sizeof(int), cudaMemcpyHostToDevice, st));
+  VscanArgs V;
+  std::memset(&V, 0, sizeof(V));
+  V.units = du.as<int4>();
+  V.n_units = dn.as<int>();
+  V.leaf_q = dl.as<int>();
+  V.qv = s.qv.as<float>();
+  V.cap = 1;
+  V.dump = out;
+  V.dumpQ = Q;
+  V.counters = s.counters.as<unsigned long long>();
+  V.status = reinterpret_cast<int*>(s.counters.as<unsigned long long>() + 8);
+  int rc = launch_vscan(ix, V, st);
+  if (!rc) rc = cudaStreamSynchronize(st) == cudaSuccess ? 0 : fail(SOFA_ERR_CUDA, "sofa_value_bounds failed");
+  du.release();
+  dl.release();
+  dn.release();
+  if (margin) *margin = ix->tc_margin;
+  return rc;
+}

@@ -47,7 +47,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("cand_cap", ctypes.c_int32), ("seed_count", ctypes.c_int32),
                 ("seed_window", ctypes.c_int32), ("bound_precision", ctypes.c_int32), ("pool_cap", ctypes.c_int64),
                 ("refine_filter", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("cand_budget", ctypes.c_int64),
-                ("dense", ctypes.c_int32), ("approximate", ctypes.c_int32)]
+                ("dense", ctypes.c_int32), ("approximate", ctypes.c_int32), ("series_bound", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -115,6 +115,7 @@ def load():
         "sofa_lower_bounds": (ctypes.c_int, [P, P, i64, P, P]),
         "sofa_lower_bounds_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "sofa_dense_sqdist": (ctypes.c_int, [P, P, i64, P, ctypes.POINTER(ctypes.c_float), P]),
+        "sofa_value_bounds": (ctypes.c_int, [P, P, i64, P, ctypes.POINTER(ctypes.c_float), P]),
         "sofa_save": (ctypes.c_int, [P, ctypes.c_char_p]),
         "sofa_load": (P, [ctypes.c_char_p, P]),
         "sofa_znorm": (ctypes.c_int, [P, i64, i32, P, P]),
@@ -241,9 +242,9 @@ class Index:
         return ids, d2, cnt
 
     def set_tuning(self, group=0, cand_cap=0, seed_count=0, seed_window=0, bound_precision=0, pool_cap=0,
-                   refine_filter=0, use_graph=0, cand_budget=0, dense=0, approximate=0):
+                   refine_filter=0, use_graph=0, cand_budget=0, dense=0, approximate=0, series_bound=0):
         t = Tuning(group, cand_cap, seed_count, seed_window, bound_precision, pool_cap, refine_filter, use_graph,
-                   cand_budget, dense, approximate)
+                   cand_budget, dense, approximate, series_bound)
         _check(load().sofa_set_tuning(self.h, ctypes.byref(t)))
 
     def autotune(self, q: torch.Tensor, k: int = 1, cache_path: str | None = None, stream=None) -> dict:
@@ -318,6 +319,16 @@ def dense_sqdist(index: "Index", q: torch.Tensor, stream=None):
     out = torch.empty((q.shape[0], index.N), dtype=torch.float32, device=q.device)
     m = ctypes.c_float(0.0)
     _check(load().sofa_dense_sqdist(index.h, _ptr(q), q.shape[0], _ptr(out), ctypes.byref(m), _stream(stream)))
+    return out, m.value
+
+
+def value_bounds(index: "Index", q: torch.Tensor, stream=None):
+    """sofa_value_bounds: (Q x N lower bounds of the tensor-core series bound
+    in original row order, the rounding margin M')."""
+    q = q.contiguous()
+    out = torch.empty((q.shape[0], index.N), dtype=torch.float32, device=q.device)
+    m = ctypes.c_float(0.0)
+    _check(load().sofa_value_bounds(index.h, _ptr(q), q.shape[0], _ptr(out), ctypes.byref(m), _stream(stream)))
     return out, m.value
 
 
