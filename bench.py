@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n-train", type=int, default=1 << 20)
     ap.add_argument("--classes", type=int, default=4096)
+    ap.add_argument("--top-m", type=int, default=4, help="proposal-network blocks probed by the learned seed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", type=int, default=1, choices=[1, 2],
@@ -75,7 +76,7 @@ def parse():
 # launch's traffic is scaled from it: reads by the tile loads (each loads a
 # tile's words), writes by the candidates emitted.  Reported only while the
 # kernel's source is the one that was captured (sha256 of its template text).
-SCAN_CAPTURE = None
+SCAN_CAPTURE = {}
 
 
 def kernel_source_sha(name="k_scan", path=None):
@@ -89,11 +90,15 @@ def kernel_source_sha(name="k_scan", path=None):
     return hashlib.sha256(s[a:b].encode()).hexdigest()[:16]
 
 
-def scaled_scan_traffic(tile_loads, candidates):
-    """Per-launch DRAM bytes of the scan scaled from the stored small-case
-    capture, or None when there is none for the current kernel source."""
-    c = SCAN_CAPTURE
-    if not c or kernel_source_sha("k_scan") != c["source_sha"]:
+KERNEL_FILES = {"k_scan": "query_kernels.cu", "k_vscan": "vscan.cu"}
+
+
+def scaled_scan_traffic(tile_loads, candidates, kernel="k_scan"):
+    """Per-launch DRAM bytes of a scan kernel scaled from its stored
+    small-case capture, or None when there is none for its current source."""
+    c = SCAN_CAPTURE.get(kernel)
+    path = os.path.join(ROOT, "paper_2411_17483_gb300", "csrc", KERNEL_FILES[kernel])
+    if not c or kernel_source_sha(kernel, path) != c["source_sha"]:
         return None
     return (c["dram_read"] * tile_loads / c["tile_loads"]
             + c["dram_write"] * candidates / max(1, c["candidates"]))
@@ -566,7 +571,8 @@ def run_sofa(a, ws, rank, local):
     if a.seed_mode in ("chosen", "learned"):
         torch.cuda.synchronize()
         tt0 = time.perf_counter()
-        ix.train_proposal(n_train=a.n_train, n_classes=min(a.classes, a.N), epochs=4, batch=4096, seed=2, top_m=4)
+        ix.train_proposal(n_train=a.n_train, n_classes=min(a.classes, a.N), epochs=4, batch=4096, seed=2,
+                          top_m=a.top_m)
         torch.cuda.synchronize()
         inf2 = ix.info()
         train = {"seconds": round(time.perf_counter() - tt0, 2), "pairs": inf2["proposal_train"],
@@ -658,7 +664,16 @@ def run_sofa(a, ws, rank, local):
     LW = info["word_bytes"]
     dense_pairs = stats.get("dense_pairs", 0)
     scan_units = None
-    if phase == "scan" and dense_pairs == 0:
+    tc_scan = phase == "scan" and dense_pairs == 0 and chosen_tuning.get("series_bound", 0) == 1
+    NB = 2 * LW
+    if tc_scan:
+        # the tensor-core bound: the unit of work is a (work unit, tile) load,
+        # which reads the tile's 256 FP16 code rows (2 NB bytes each) and
+        # per-series constants (16 bytes each) once for up to 64 queries;
+        # plus the tile envelopes checked (2 LW bytes each)
+        alg_bytes = (prof["scan_tile_loads"] * 256 * (2 * NB + 16) + prof["scan_tile_checks"] * 2 * LW) / launches
+        scan_units = dict(tile_loads=prof["scan_tile_loads"] / launches, candidates=stats["candidates"] / launches)
+    elif phase == "scan" and dense_pairs == 0:
         # algorithmic bytes: the word of every (query, series) pair bounded
         # (LW bytes each) and the tile envelopes checked (2 LW bytes each);
         # above 1 means the queries of a work unit share each tile's read
@@ -676,12 +691,17 @@ def run_sofa(a, ws, rank, local):
         ach = alg_bytes / per_launch_s / 1e9
         hbm.update(achieved=ach, frac=ach / hbm_peak, algorithmic_bytes_per_launch=alg_bytes)
     if scan_units is not None:
-        hbm["kernel"] = "k_scan"
-        hbm["note"] = ("logical bytes: LW bytes per (query, series) pair bounded plus 2 LW per tile envelope "
-                       "checked; the queries of a work unit share each tile's read, so frac can exceed 1")
-        hbm["traffic"] = scaled_scan_traffic(scan_units["tile_loads"], scan_units["candidates"])
+        kname = "k_vscan" if tc_scan else "k_scan"
+        hbm["kernel"] = kname
+        if tc_scan:
+            hbm["note"] = ("bytes a (work unit, tile) load must move: 256 x (2 NB bytes of FP16 codes + 16 bytes "
+                           "of constants), plus 2 LW per tile envelope checked")
+        else:
+            hbm["note"] = ("logical bytes: LW bytes per (query, series) pair bounded plus 2 LW per tile envelope "
+                           "checked; the queries of a work unit share each tile's read, so frac can exceed 1")
+        hbm["traffic"] = scaled_scan_traffic(scan_units["tile_loads"], scan_units["candidates"], kname)
         if hbm["traffic"] is not None:
-            hbm["traffic_kind"] = ("scaled from the stored ncu capture of " + SCAN_CAPTURE["case"] +
+            hbm["traffic_kind"] = ("scaled from the stored ncu capture of " + SCAN_CAPTURE[kname]["case"] +
                                    ": reads by tile loads, writes by candidates")
     roof = hbm
     alu = None
@@ -713,6 +733,19 @@ def run_sofa(a, ws, rank, local):
                 "flops_per_launch": flops, "launch_ms": per_dense_s * 1e3,
                 "note": "launch_ms is the dense phase's time per k_dense launch, including the query-side "
                         "helper kernels of the phase"}
+    elif tc_scan:
+        # the tensor pipe's share: per tile load 2 halves x NB/16 MMAs of
+        # 128 x 64 x 16, i.e. 2 x 256 x 64 x NB FLOP, against the FP16 rate
+        # (the measured bf16 burst peak; FP16 runs at the BF16 rate)
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16 = float(json.load(f)["bf16_tflops"])
+        except (OSError, KeyError, ValueError):
+            bf16 = 1900.0
+        flops = prof["scan_tile_loads"] * 2.0 * 256 * 64 * NB / launches
+        alu = {"kernel": "k_vscan", "view": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": bf16,
+               "unit": "TFLOP/s", "frac": flops / per_launch_s / 1e12 / bf16,
+               "peak_kind": "measured bf16 burst (fp16 = bf16 rate)"}
     elif phase == "scan":
         # a second view of the same kernel: its own instruction mix is 3 FP32
         # lane operations per value (q - c, the scaled clamp, the

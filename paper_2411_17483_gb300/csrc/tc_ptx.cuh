@@ -35,9 +35,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 }
 
 // Wait for the completion of the phase with the given parity; false when the
-// wait ran out (2 s).  The clock is read only once the wait has polled 64
+// wait ran out (2 s).  Each try_wait may suspend the thread until the phase
+// completes, for at most MBAR_SUSPEND_NS (a hint), so a waiting warp does
+// not keep polling.  The clock is read only once the wait has polled 64
 // times without success, so a wait that completes promptly never touches
 // the global timer.
+constexpr uint32_t MBAR_SUSPEND_NS = 10000;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
   unsigned long long t0 = 0;
@@ -45,10 +48,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "n"(MBAR_SUSPEND_NS)
         : "memory");
     if (done) return true;
     if (it == 64) t0 = global_ns();

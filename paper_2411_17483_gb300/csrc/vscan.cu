@@ -210,7 +210,9 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
   __shared__ uint16_t stl[MAX_LEAF_TILES_VS];
   __shared__ __align__(16) float sq[VS_N][LW];
   __shared__ float sT[VS_N], sQw[VS_N];
-  __shared__ float2 sAC[VS_N];  // (a, c) of each query: a = sqrt(2 T) rounded up, c = a^2 - ||q~||_w^2
+  // (a, -c) of each query: a = sqrt(2 T) rounded up, c = a^2 - ||q~||_w^2;
+  // slots past the unit's queries hold (0, +inf) and never survive
+  __shared__ __align__(16) float2 sAC[VS_N];
   __shared__ int sslot[VS_N], sqid[VS_N];
   __shared__ unsigned long long smask[MAX_LEAF_TILES_VS];
   __shared__ uint32_t s_tmem;
@@ -285,7 +287,9 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
       }
       const float a = __fsqrt_ru(__fmul_ru(2.0f, sT[tid]));
       sQw[tid] = Qw;
-      sAC[tid] = make_float2(a, __fsub_ru(__fmul_ru(a, a), Qw));
+      sAC[tid] = make_float2(a, -__fsub_ru(__fmul_ru(a, a), Qw));
+    } else if (tid < VS_N) {
+      sAC[tid] = make_float2(0.f, INFINITY);
     }
     // ---- tile envelope checks (every pair when dumping)
     if (dump) {
@@ -408,18 +412,31 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
             }
             continue;
           }
-          uint32_t mine = 0u;  // bit j: this lane's series survives query 32 h32 + j
+          // Survival of query j: fma(-2r, a_j, fma(-2s, D_j, S')) <= c_j, i.e.
+          // x_j = fma(-2r, a_j, fma(-2s, D_j, -c_j)) <= -S'.  The lane first
+          // takes the minimum of x_j over the half's 32 columns (two FMAs and
+          // a min each, no branch; unused slots give +inf); only a lane whose
+          // minimum passes (rare) tests the columns one by one, with the
+          // tile's mask of live queries.
+          const float4* ac4 = reinterpret_cast<const float4*>(sAC + 32 * h32);
+          float xmin = INFINITY;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (m & (1u << j)) {
-              const int g = 32 * h32 + j;
-              const float2 ac = sAC[g];
-              float uu = fmaf(cx.x, v[j], cx.z);
-              uu = fmaf(cx.y, ac.x, uu);
-              if (uu <= ac.y) mine |= 1u << j;
-            }
+          for (int j = 0; j < 32; j += 2) {
+            const float4 ac = ac4[j >> 1];  // (a_j, -c_j, a_j+1, -c_j+1)
+            xmin = fminf(xmin, fmaf(cx.y, ac.x, fmaf(cx.x, v[j], ac.y)));
+            xmin = fminf(xmin, fmaf(cx.y, ac.z, fmaf(cx.x, v[j + 1], ac.w)));
           }
-          if (!valid) mine = 0u;
+          const float negS = -cx.z;
+          uint32_t mine = 0u;  // bit j: this lane's series survives query 32 h32 + j
+          if (valid && xmin <= negS) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const float4 ac = ac4[j >> 1];
+              mine |= (fmaf(cx.y, ac.x, fmaf(cx.x, v[j], ac.y)) <= negS ? 1u : 0u) << j;
+              mine |= (fmaf(cx.y, ac.z, fmaf(cx.x, v[j + 1], ac.w)) <= negS ? 1u : 0u) << (j + 1);
+            }
+            mine &= m;
+          }
           uint32_t any = __reduce_or_sync(0xFFFFFFFFu, mine);
           while (any) {  // rare: the columns where some lane of the warp survives
             const int j = __ffs(any) - 1;

@@ -64,9 +64,13 @@ def test_scan_traffic_scales_from_the_stored_capture(monkeypatch):
     assert len(sha) == 16 and sha == bench.kernel_source_sha("k_scan")
     cap = {"case": "test", "source_sha": sha, "dram_read": 1000.0, "dram_write": 300.0, "tile_loads": 10,
            "candidates": 30}
-    monkeypatch.setattr(bench, "SCAN_CAPTURE", cap)
+    monkeypatch.setattr(bench, "SCAN_CAPTURE", {"k_scan": cap})
     assert bench.scaled_scan_traffic(40, 60) == 1000.0 * 4 + 300.0 * 2
-    monkeypatch.setattr(bench, "SCAN_CAPTURE", {**cap, "source_sha": "0" * 16})
+    assert bench.scaled_scan_traffic(40, 60, "k_vscan") is None          # no capture of that kernel
+    monkeypatch.setattr(bench, "SCAN_CAPTURE", {"k_scan": {**cap, "source_sha": "0" * 16}})
     assert bench.scaled_scan_traffic(40, 60) is None
-    monkeypatch.setattr(bench, "SCAN_CAPTURE", None)
+    monkeypatch.setattr(bench, "SCAN_CAPTURE", {})
     assert bench.scaled_scan_traffic(40, 60) is None
+    import os
+    vs = os.path.join(bench.ROOT, "paper_2411_17483_gb300", "csrc", "vscan.cu")
+    assert len(bench.kernel_source_sha("k_vscan", vs)) == 16
