@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n-train", type=int, default=1 << 20)
     ap.add_argument("--classes", type=int, default=4096)
-    ap.add_argument("--top-m", type=int, default=4, help="proposal-network blocks probed by the learned seed")
+    ap.add_argument("--top-m", type=int, default=2, help="proposal-network blocks probed by the learned seed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", type=int, default=1, choices=[1, 2],
@@ -586,11 +586,12 @@ def run_sofa(a, ws, rank, local):
             raise SystemExit(f"--modes must include the chosen mode ({chosen})")
         modes = {m: modes[m] for m in modes if m in keep}
     # run-time tuning of the tuned modes: the autotuner's pick for each seed
-    # mode, on 2048 queries of a separate stream (seed 100 + rank), never on
-    # the timed queries; both start from the same refinement filters
+    # mode, on one full batch (8192 queries, at most the workload's) of a
+    # separate stream (seed 100 + rank), never on the timed queries; both
+    # start from the same refinement filters
     tunings = {m: dict(refine_filter=2) for m in modes}
     if not a.no_autotune:
-        qt = make_rows(a, 2048, 100 + rank, dev)
+        qt = make_rows(a, min(8192, a.Q), 100 + rank, dev)
         for m, (mode, tuned) in modes.items():
             if not tuned:
                 continue

@@ -210,9 +210,10 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
   __shared__ uint16_t stl[MAX_LEAF_TILES_VS];
   __shared__ __align__(16) float sq[VS_N][LW];
   __shared__ float sT[VS_N], sQw[VS_N];
-  // (a, -c) of each query: a = sqrt(2 T) rounded up, c = a^2 - ||q~||_w^2;
-  // slots past the unit's queries hold (0, +inf) and never survive
-  __shared__ __align__(16) float2 sAC[VS_N];
+  // per pair of query slots (2i, 2i+1): (a_2i, a_2i+1, -c_2i, -c_2i+1), with
+  // a = sqrt(2 T) rounded up and c = a^2 - ||q~||_w^2; slots past the unit's
+  // queries hold a = 0, -c = +inf and never survive
+  __shared__ __align__(16) float4 sAC[VS_N / 2];
   __shared__ int sslot[VS_N], sqid[VS_N];
   __shared__ unsigned long long smask[MAX_LEAF_TILES_VS];
   __shared__ uint32_t s_tmem;
@@ -287,9 +288,13 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
       }
       const float a = __fsqrt_ru(__fmul_ru(2.0f, sT[tid]));
       sQw[tid] = Qw;
-      sAC[tid] = make_float2(a, -__fsub_ru(__fmul_ru(a, a), Qw));
+      float* acf = reinterpret_cast<float*>(&sAC[tid >> 1]);
+      acf[tid & 1] = a;
+      acf[2 + (tid & 1)] = -__fsub_ru(__fmul_ru(a, a), Qw);
     } else if (tid < VS_N) {
-      sAC[tid] = make_float2(0.f, INFINITY);
+      float* acf = reinterpret_cast<float*>(&sAC[tid >> 1]);
+      acf[tid & 1] = 0.f;
+      acf[2 + (tid & 1)] = INFINITY;
     }
     // ---- tile envelope checks (every pair when dumping)
     if (dump) {
@@ -418,13 +423,17 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
           // a min each, no branch; unused slots give +inf); only a lane whose
           // minimum passes (rare) tests the columns one by one, with the
           // tile's mask of live queries.
-          const float4* ac4 = reinterpret_cast<const float4*>(sAC + 32 * h32);
+          // two columns per step with packed FP32x2 FMAs (each lane of the
+          // pair rounds exactly as fmaf does)
+          const float4* ac4 = sAC + 16 * h32;
+          const float2 A2 = make_float2(cx.x, cx.x), B2 = make_float2(cx.y, cx.y);
           float xmin = INFINITY;
 #pragma unroll
           for (int j = 0; j < 32; j += 2) {
-            const float4 ac = ac4[j >> 1];  // (a_j, -c_j, a_j+1, -c_j+1)
-            xmin = fminf(xmin, fmaf(cx.y, ac.x, fmaf(cx.x, v[j], ac.y)));
-            xmin = fminf(xmin, fmaf(cx.y, ac.z, fmaf(cx.x, v[j + 1], ac.w)));
+            const float4 ac = ac4[j >> 1];  // (a_j, a_j+1, -c_j, -c_j+1)
+            const float2 x2 = __ffma2_rn(B2, make_float2(ac.x, ac.y),
+                                         __ffma2_rn(A2, make_float2(v[j], v[j + 1]), make_float2(ac.z, ac.w)));
+            xmin = fminf(xmin, fminf(x2.x, x2.y));
           }
           const float negS = -cx.z;
           uint32_t mine = 0u;  // bit j: this lane's series survives query 32 h32 + j
@@ -432,8 +441,10 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
               const float4 ac = ac4[j >> 1];
-              mine |= (fmaf(cx.y, ac.x, fmaf(cx.x, v[j], ac.y)) <= negS ? 1u : 0u) << j;
-              mine |= (fmaf(cx.y, ac.z, fmaf(cx.x, v[j + 1], ac.w)) <= negS ? 1u : 0u) << (j + 1);
+              const float2 x2 = __ffma2_rn(B2, make_float2(ac.x, ac.y),
+                                           __ffma2_rn(A2, make_float2(v[j], v[j + 1]), make_float2(ac.z, ac.w)));
+              mine |= (x2.x <= negS ? 1u : 0u) << j;
+              mine |= (x2.y <= negS ? 1u : 0u) << (j + 1);
             }
             mine &= m;
           }
