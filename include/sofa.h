@@ -27,6 +27,10 @@
  *     lower bounds, training, autotuning, the dense contraction) returns
  *     SOFA_ERR_INVALID_ARG when another device is current.
  *   - There is no CPU fallback: every step runs in this library's CUDA kernels.
+ *   - Testing hook: when the environment variable SOFA_TEST_MEM_CAP holds a
+ *     byte count, every device allocation of the library larger than it fails
+ *     as if the device were full (calls return SOFA_ERR_OOM, constructors
+ *     NULL), so the out-of-memory paths can be tested without exhausting a GPU.
  */
 #ifndef SOFA_H_
 #define SOFA_H_
@@ -366,6 +370,13 @@ int sofa_dense_sqdist(sofa_handle h, const float* queries, int64_t Q, float* out
  * index with the value codes (precision >= 1). */
 int sofa_value_bounds(sofa_handle h, const float* queries, int64_t Q, float* out, float* margin,
                       sofa_stream stream);
+
+/* The bounded device wait every tensor-core kernel uses (a test aid; the
+ * paper has no counterpart): one warp waits on a barrier that nothing ever
+ * completes; the wait gives up after limit_ms (1..2000) and the kernel returns
+ * normally.  Returns SOFA_ERR_TIMEOUT when the wait ran out as intended, and
+ * the context stays usable. */
+int sofa_wait_selftest(int32_t limit_ms, sofa_stream stream);
 
 /* Canonical z-normalisation of R rows (Sec. II Def. z-ED) as the index uses
  * it: device pointers, R x n fp32 in and out. */

@@ -84,7 +84,11 @@ def measures(lb2: torch.Tensor, d2: torch.Tensor) -> tuple[float, float]:
     return tlb, prune
 
 
-def run(N=1_000_000, n=256, Q=100, l=16, alphabet=256, ratios=(0.001, 0.01, 0.1), isax_segments=16,
+# sampling ratios of Table IV (Sec. V): 0.1 % to 20 %
+TABLE_IV_RATIOS = (0.001, 0.005, 0.01, 0.05, 0.1, 0.15, 0.2)
+
+
+def run(N=1_000_000, n=256, Q=100, l=16, alphabet=256, ratios=TABLE_IV_RATIOS, isax_segments=16,
         seed=0, device="cuda:0", chunk=200_000):
     from . import datagen, sofa
     x = datagen.random_walks(N, n, seed=seed, device=device)

@@ -1,5 +1,6 @@
 // C ABI entry points: argument checks, handle lifetime, host/device buffers.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -29,7 +30,7 @@ int DevBuf::ensure(size_t want) {
   p = nullptr;
   bytes = 0;
   size_t grow = want + want / 4 + 256;
-  cudaError_t e = cudaMalloc(&p, grow);
+  cudaError_t e = dev_malloc(&p, grow);
   if (e != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
@@ -107,6 +108,18 @@ void Prof::release() {
   collect();
   for (cudaEvent_t e : pool) cudaEventDestroy(e);
   pool.clear();
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (const char* cap = std::getenv("SOFA_TEST_MEM_CAP")) {
+    char* end = nullptr;
+    const unsigned long long c = std::strtoull(cap, &end, 10);
+    if (end != cap && bytes > c) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(p, bytes);
 }
 
 bool is_device_ptr(const void* p) {
@@ -209,7 +222,7 @@ sofa_handle sofa_build_ex(const float* data, int64_t N, int32_t n, int32_t l, in
   const float* x = data;
   float* owned = nullptr;
   if (!is_device_ptr(data)) {
-    cudaError_t e = cudaMalloc(&owned, (size_t)N * n * sizeof(float));
+    cudaError_t e = dev_malloc((void**)&owned, (size_t)N * n * sizeof(float));
     if (e != cudaSuccess) {
       cudaGetLastError();
       destroy_index(ix);
@@ -272,7 +285,7 @@ int sofa_insert(sofa_handle h, const float* data, int64_t N_add, sofa_stream str
   const float* x = data;
   float* owned = nullptr;
   if (!is_device_ptr(data)) {
-    cudaError_t e = cudaMalloc(&owned, (size_t)N_add * h->n * sizeof(float));
+    cudaError_t e = dev_malloc((void**)&owned, (size_t)N_add * h->n * sizeof(float));
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(SOFA_ERR_OOM, "device allocation for the input copy failed; the index is unchanged");

@@ -746,7 +746,7 @@ template <class T>
 static int dalloc(T** p, int64_t count, int64_t* acct) {
   *p = nullptr;
   if (count <= 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
+  cudaError_t e = dev_malloc((void**)p, (size_t)count * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(SOFA_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +

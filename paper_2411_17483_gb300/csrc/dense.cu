@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
                                                        unsigned long long* __restrict__ counters,
                                                        int* __restrict__ status) {
   extern __shared__ uint8_t dsm_raw[];
-  __shared__ __align__(8) uint64_t full[DSTAGES], empty[DSTAGES], tfull[DACC], tempty[DACC];
+  __shared__ __align__(8) uint64_t full[DSTAGES], empty[DSTAGES], tfull[DACC], tempty[DACC], drain;
   __shared__ __align__(16) float s_x[4][DN];  // per epilogue warp: ||x||^2 of the tile's series
   __shared__ float s_v[4][32][32];             // per epilogue warp: 32 accumulator columns x 32 lanes
   __shared__ uint32_t s_tmem;
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], 4 * 32);  // every epilogue thread
     }
+    mbar_init(&drain, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -350,6 +351,18 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
     }
     if (emitted) atomicAdd(counters + 2, emitted);
   }
+  // drain: after a timed-out wait, the MMAs and the copies already issued
+  // finish (bounded) before the tensor memory is freed and the CTA exits
+  __syncthreads();
+  if (*vfail) {
+    if (warp == 1 && lane == 0) {
+      mma_commit(&drain);
+      mbar_wait(&drain, 0u);
+    }
+    if (warp == 0 && lane == 0)
+      for (int64_t idx = total > DSTAGES ? total - DSTAGES : 0; idx < total; ++idx)
+        mbar_wait(&full[idx % DSTAGES], (uint32_t)((idx / DSTAGES) & 1));
+  }
   __syncthreads();
   if (tid == 0) {
     if (*vfail) atomicExch(status, SOFA_ERR_TIMEOUT);
@@ -360,6 +373,21 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
     tc_fence_after();
     tmem_dealloc(tmem, DN * DACC);
   }
+}
+
+// The bounded wait itself (a test aid): one warp waits on an mbarrier that
+// nothing ever arrives on; the wait gives up after limit_ns and the kernel
+// returns normally with SOFA_ERR_TIMEOUT in *status.  Nothing is in flight
+// when it gives up (no copy, no MMA, no tensor memory).
+__global__ void k_wait_probe(unsigned long long limit_ns, int* __restrict__ status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u, limit_ns);
+  if (threadIdx.x == 0) *status = ok ? 0 : SOFA_ERR_TIMEOUT;
 }
 
 // ------------------------------------------------------------------------
@@ -543,6 +571,22 @@ int launch_dense(Index* ix, const DenseArgs& A, cudaStream_t st) {
 }  // namespace sofa
 
 using namespace sofa;
+
+extern "C" int sofa_wait_selftest(int32_t limit_ms, sofa_stream stream) {
+  if (limit_ms < 1 || limit_ms > 2000) return fail(SOFA_ERR_INVALID_ARG, "limit_ms must lie in [1, 2000]");
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d = nullptr;
+  SOFA_CUDA(dev_malloc((void**)&d, sizeof(int)));
+  int h = 0;
+  k_wait_probe<<<1, 32, 0, st>>>((unsigned long long)limit_ms * 1000000ull, d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(SOFA_ERR_CUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+  if (h == SOFA_ERR_TIMEOUT) return fail(SOFA_ERR_TIMEOUT, "the bounded wait ran out, as the self-test intends");
+  return h;
+}
 
 extern "C" int sofa_dense_sqdist(sofa_handle h, const float* queries, int64_t Q, float* out, float* margin,
                                  sofa_stream stream) {

@@ -397,13 +397,13 @@ struct Mlp {
     layout();
     float** fs[] = {&P, &G, &Mo, &Ve};
     for (float** f : fs) {
-      if (cudaMalloc((void**)f, total * sizeof(float)) != cudaSuccess) {
+      if (dev_malloc((void**)f, total * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SOFA_ERR_OOM, "proposal network allocation failed");
       }
       cudaMemset(*f, 0, total * sizeof(float));
     }
-    if (cudaMalloc((void**)&Pb, total * sizeof(bf16)) != cudaSuccess) {
+    if (dev_malloc((void**)&Pb, total * sizeof(bf16)) != cudaSuccess) {
       cudaGetLastError();
       return fail(SOFA_ERR_OOM, "proposal network allocation failed");
     }

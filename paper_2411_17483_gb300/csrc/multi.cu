@@ -1,4 +1,7 @@
 // Mixed workload: queries of different lengths and k over several indexes.
+// The queries of each index form one batch through that index's pipeline,
+// each query with its own k (the batch's largest k sizes its buffers), and
+// every query's results go straight to its output offset.
 #include <algorithm>
 #include <map>
 #include <string>
@@ -15,18 +18,6 @@ __global__ void k_gather_rows(const float* __restrict__ src, const int64_t* __re
   if (r >= R) return;
   const float* s = src + offs[sel[r]];
   for (int t = threadIdx.x; t < n; t += blockDim.x) dst[r * n + t] = s[t];
-}
-
-__global__ void k_scatter_out(const int64_t* __restrict__ gi, const float* __restrict__ gd, int64_t R, int k,
-                              const int32_t* __restrict__ sel, const int64_t* __restrict__ out_off,
-                              int64_t* __restrict__ idx, float* __restrict__ dist) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= R * k) return;
-  int64_t r = e / k;
-  int j = (int)(e - r * k);
-  int64_t o = out_off[sel[r]] + j;
-  idx[o] = gi[e];
-  dist[o] = gd[e];
 }
 
 static bool dev_ptr(const void* p) { return is_device_ptr(p); }
@@ -69,7 +60,8 @@ extern "C" int sofa_query_multi(const sofa_handle* hs, int32_t nh, const float* 
   if (int rc = to_host(q_k, Q, kk)) return rc;
   if (int rc = to_host(out_offsets, Q, oo)) return rc;
   int64_t qfloats = 0, outs = 0;
-  std::map<std::pair<int, int>, std::vector<int32_t>> groups;
+  // one group per index: its queries, each with its own k, in one pipeline
+  std::map<int, std::vector<int32_t>> groups;
   for (int64_t i = 0; i < Q; ++i) {
     int h = -1;
     for (int j = 0; j < nh; ++j)
@@ -82,13 +74,13 @@ extern "C" int sofa_query_multi(const sofa_handle* hs, int32_t nh, const float* 
     if (off[i] < 0 || oo[i] < 0) return fail(SOFA_ERR_INVALID_ARG, "negative offset");
     qfloats = std::max(qfloats, off[i] + len[i]);
     outs = std::max(outs, oo[i] + kk[i]);
-    groups[{h, kk[i]}].push_back((int32_t)i);
+    groups[h].push_back((int32_t)i);
   }
   // device copies of the packed queries, offsets and outputs when given host memory
-  DevVec dq, doff, doo, dsel, dgi, dgd, dgq, didx, ddist;
+  DevVec dq, doff, dsel, dgq, didx, ddist, dgk, dgo;
   const float* qdev = queries;
   if (!dev_ptr(queries)) {
-    SOFA_CUDA(cudaMalloc(&dq.p, qfloats * sizeof(float)));
+    SOFA_CUDA(dev_malloc(&dq.p, qfloats * sizeof(float)));
     SOFA_CUDA(cudaMemcpyAsync(dq.p, queries, qfloats * sizeof(float), cudaMemcpyHostToDevice, st));
     qdev = (const float*)dq.p;
   }
@@ -96,40 +88,46 @@ extern "C" int sofa_query_multi(const sofa_handle* hs, int32_t nh, const float* 
   int64_t* idev = idx;
   float* ddev = dist;
   if (host_out) {
-    SOFA_CUDA(cudaMalloc(&didx.p, outs * sizeof(int64_t)));
-    SOFA_CUDA(cudaMalloc(&ddist.p, outs * sizeof(float)));
+    SOFA_CUDA(dev_malloc(&didx.p, outs * sizeof(int64_t)));
+    SOFA_CUDA(dev_malloc(&ddist.p, outs * sizeof(float)));
     idev = (int64_t*)didx.p;
     ddev = (float*)ddist.p;
   }
-  SOFA_CUDA(cudaMalloc(&doff.p, Q * sizeof(int64_t)));
-  SOFA_CUDA(cudaMalloc(&doo.p, Q * sizeof(int64_t)));
+  SOFA_CUDA(dev_malloc(&doff.p, Q * sizeof(int64_t)));
   SOFA_CUDA(cudaMemcpyAsync(doff.p, off.data(), Q * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  SOFA_CUDA(cudaMemcpyAsync(doo.p, oo.data(), Q * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  int64_t maxR = 0, maxRow = 0;
-  for (auto& g : groups) {
-    maxR = std::max<int64_t>(maxR, (int64_t)g.second.size());
-    maxRow = std::max<int64_t>(maxRow, (int64_t)g.second.size() * hs[g.first.first]->n);
-  }
-  SOFA_CUDA(cudaMalloc(&dsel.p, Q * sizeof(int32_t)));
-  SOFA_CUDA(cudaMalloc(&dgq.p, maxRow * sizeof(float)));
-  SOFA_CUDA(cudaMalloc(&dgi.p, maxR * SOFA_MAX_K * sizeof(int64_t)));
-  SOFA_CUDA(cudaMalloc(&dgd.p, maxR * SOFA_MAX_K * sizeof(float)));
-  std::vector<int32_t> allsel;
+  int64_t maxRow = 0;
+  for (auto& g : groups) maxRow = std::max<int64_t>(maxRow, (int64_t)g.second.size() * hs[g.first]->n);
+  // per group, in group order: the queries' ids, their k and their output offsets
+  std::vector<int32_t> allsel, allk;
+  std::vector<int64_t> allo;
   allsel.reserve(Q);
-  for (auto& g : groups) allsel.insert(allsel.end(), g.second.begin(), g.second.end());
+  allk.reserve(Q);
+  allo.reserve(Q);
+  for (auto& g : groups)
+    for (int32_t i : g.second) {
+      allsel.push_back(i);
+      allk.push_back(kk[i]);
+      allo.push_back(oo[i]);
+    }
+  SOFA_CUDA(dev_malloc(&dsel.p, Q * sizeof(int32_t)));
+  SOFA_CUDA(dev_malloc(&dgk.p, Q * sizeof(int32_t)));
+  SOFA_CUDA(dev_malloc(&dgo.p, Q * sizeof(int64_t)));
+  SOFA_CUDA(dev_malloc(&dgq.p, maxRow * sizeof(float)));
   SOFA_CUDA(cudaMemcpyAsync(dsel.p, allsel.data(), Q * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  SOFA_CUDA(cudaMemcpyAsync(dgk.p, allk.data(), Q * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  SOFA_CUDA(cudaMemcpyAsync(dgo.p, allo.data(), Q * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   int64_t base = 0;
   for (auto& g : groups) {
-    Index* ix = hs[g.first.first];
-    const int k = g.first.second;
+    Index* ix = hs[g.first];
     const int64_t R = (int64_t)g.second.size();
+    int kmax = 1;
+    for (int32_t i : g.second) kmax = std::max(kmax, kk[i]);
     const int32_t* sel = (const int32_t*)dsel.p + base;
     k_gather_rows<<<(unsigned)R, 256, 0, st>>>(qdev, (const int64_t*)doff.p, sel, R, ix->n, (float*)dgq.p);
     SOFA_CUDA(cudaGetLastError());
-    if (int rc = run_query(ix, (const float*)dgq.p, R, k, (int64_t*)dgi.p, (float*)dgd.p, st)) return rc;
-    k_scatter_out<<<(unsigned)ceil_div(R * k, 256), 256, 0, st>>>((const int64_t*)dgi.p, (const float*)dgd.p, R, k,
-                                                                   sel, (const int64_t*)doo.p, idev, ddev);
-    SOFA_CUDA(cudaGetLastError());
+    if (int rc = run_query(ix, (const float*)dgq.p, R, kmax, idev, ddev, st, (const int*)dgk.p + base,
+                           (const int64_t*)dgo.p + base))
+      return rc;
     base += R;
   }
   if (host_out) {

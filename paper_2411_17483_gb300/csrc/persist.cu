@@ -67,7 +67,7 @@ int read_array(FILE* f, Staging& sg, T** dev, size_t bytes, bool optional, int64
   if (fread(&b, sizeof(b), 1, f) != 1) return fail(SOFA_ERR_INVALID_ARG, "truncated index file");
   if (b == 0 && optional) return 0;
   if (b != bytes) return fail(SOFA_ERR_INVALID_ARG, "index file section has an unexpected size");
-  if (cudaMalloc((void**)dev, b) != cudaSuccess) {
+  if (dev_malloc((void**)dev, b) != cudaSuccess) {
     cudaGetLastError();
     return fail(SOFA_ERR_OOM, "device allocation failed while loading an index");
   }

@@ -27,7 +27,16 @@ struct QueryParams {
   int n, NB, leaf_tiles, k, cap, group, seed_count, seed_window;
   float f_prune;  // threshold = d2_kth * f_prune / 2 (half units)
   float f_keep;   // kept list: d2 <= d2_kth * f_keep
+  // per-query k of a mixed batch (nullptr: every query has k), and the
+  // element offset of each query's k results in idx / dist
+  const int* qk;
+  const int64_t* qo;
 };
+
+// k of query q of the batch (k is the batch's largest, which sizes every
+// buffer and, in the dense contraction, sets a threshold that is valid for
+// every smaller k).
+__device__ __forceinline__ int kq(const QueryParams& P, int64_t q) { return P.qk ? P.qk[q] : P.k; }
 
 // Series bound from a word: m_j = max(|q_j - c_j| - h_j, 0) with (c, h) the
 // symbol's widened interval as centre / half-width.
@@ -166,13 +175,14 @@ __device__ __forceinline__ unsigned long long pack_key(float v, uint32_t p) {
 __device__ inline bool emit_list(const unsigned long long* key, int len, const QueryParams& P, int64_t q,
                                  float* list_d, uint32_t* list_p, int* list_n, float* thr) {
   __shared__ int s_cnt;
-  const float dk = __uint_as_float((uint32_t)(key[P.k - 1] >> 32));
+  const int K = kq(P, q);
+  const float dk = __uint_as_float((uint32_t)(key[K - 1] >> 32));
   const float lim = __fmul_ru(dk, P.f_keep);
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
     float d = __uint_as_float((uint32_t)(key[i] >> 32));
-    if (i < P.k || d <= lim) atomicMax(&s_cnt, i + 1);
+    if (i < K || d <= lim) atomicMax(&s_cnt, i + 1);
   }
   __syncthreads();
   const int cnt = s_cnt;
@@ -308,7 +318,8 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
     skey[i] = valid ? pack_key(word_bound<LW, NYQ>(c, h, sq), (uint32_t)p) : ~0ull;
   }
   block_bitonic(skey, P.seed_window);
-  int cnt = P.seed_count > P.k ? P.seed_count : P.k;
+  const int Kq = kq(P, q);
+  int cnt = P.seed_count > Kq ? P.seed_count : Kq;
   if (cnt > W) cnt = (int)W;
   // learned seeding: every series of the proposal network's top-m blocks whose
   // bound beats the window's cnt-th joins the candidates (up to LEARN_CAP)
@@ -406,7 +417,7 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
   block_bitonic(skey, TILE);
   if (!emit_list(skey, cnt, P, q, list_d, list_p, list_n, thr) && tid == 0) atomicExch(status, SOFA_ERR_TIE_OVERFLOW);
   if (tid == 0)
-    atomicAdd(counters + 6, (unsigned long long)(1e6 * sqrt((double)__uint_as_float((uint32_t)(skey[P.k - 1] >> 32)))));
+    atomicAdd(counters + 6, (unsigned long long)(1e6 * sqrt((double)__uint_as_float((uint32_t)(skey[Kq - 1] >> 32)))));
 }
 
 // ------------------------------------------------------------------------
@@ -894,6 +905,7 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
   const int slot_q = chunk_q[ch];
   const int c = ch - choff[slot_q];
   const int64_t q = qof ? qof[slot_q] : slot_q;
+  const int K = kq(P, q);
   const int r = cand_n[slot_q] < P.cap ? cand_n[slot_q] : P.cap;
   const int total = r + qpool_cnt[slot_q];
   const int c0 = c * RSORT;
@@ -983,16 +995,16 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
       }
       if (nl < KCAP) ++nl;
       else s_lost = 1;
-      if (nl >= P.k) {
-        lim = __fmul_ru(sld[P.k - 1], P.f_keep);
-        while (nl > P.k && sld[nl - 1] > lim) --nl;  // drop entries that left the window
+      if (nl >= K) {
+        lim = __fmul_ru(sld[K - 1], P.f_keep);
+        while (nl > K && sld[nl - 1] > lim) --nl;  // drop entries that left the window
       }
     }
     s_nacc = 0;
     s_nl = nl;
     s_lim = lim;
-    if (nl >= P.k) {
-      const float t = __fmul_ru(__fmul_ru(sld[P.k - 1], P.f_prune), 0.5f);
+    if (nl >= K) {
+      const float t = __fmul_ru(__fmul_ru(sld[K - 1], P.f_prune), 0.5f);
       atomicMin(reinterpret_cast<int*>(thr) + q, __float_as_int(t));  // t >= 0: int order = float order
     }
   };
@@ -1236,6 +1248,7 @@ __global__ void __launch_bounds__(256) k_merge(QueryParams P, const int* __restr
   const int64_t q = blockIdx.x;
   if (qsel && !qsel[q]) return;
   const int tid = threadIdx.x;
+  const int K = kq(P, q);
   const int64_t slot_q = qslot ? qslot[q] : q;
   const int all = cand_n[slot_q];
   if (all == 0) return;
@@ -1259,7 +1272,7 @@ __global__ void __launch_bounds__(256) k_merge(QueryParams P, const int* __restr
   for (int c = c_first + tid; c < c_first + nch; c += blockDim.x) atomicAdd(&s_total, chunk_n[c]);
   __syncthreads();
   float lim_c = INFINITY;
-  if (s_total >= P.k) {
+  if (s_total >= K) {
     uint32_t lo = 0u, hi = 0x7F800000u;  // count(<= hi) >= k holds for hi = +inf
     while (lo < hi) {
       const uint32_t mid = lo + ((hi - lo) >> 1);
@@ -1279,21 +1292,21 @@ __global__ void __launch_bounds__(256) k_merge(QueryParams P, const int* __restr
       }
       if (cnt) atomicAdd(&s_count, cnt);
       __syncthreads();
-      if (s_count >= (unsigned)P.k) hi = mid;
+      if (s_count >= (unsigned)K) hi = mid;
       else lo = mid + 1;
       __syncthreads();
     }
     lim_c = __uint_as_float(hi);
   }
   const int nl = list_n[q];
-  const float lim_k = nl >= P.k ? list_d[q * KCAP + P.k - 1] : INFINITY;
+  const float lim_k = nl >= K ? list_d[q * KCAP + K - 1] : INFINITY;
   const float lim = fminf(__fmul_ru(__fdiv_ru(__fmul_ru(thr[q], 2.0f), P.f_prune), P.f_keep),
                           __fmul_ru(fminf(lim_c, lim_k), P.f_keep));
   if (tid == 0) s_cnt = 0;
   __syncthreads();
   for (int i = tid; i < nl; i += blockDim.x) {
     const float d = list_d[q * KCAP + i];
-    if (i < P.k || d <= lim) {
+    if (i < K || d <= lim) {
       const int a = atomicAdd(&s_cnt, 1);
       if (a < MSORT) skey[a] = pack_key(d, list_p[q * KCAP + i]);
     }
@@ -1390,9 +1403,10 @@ __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __res
     }
   }
   __syncthreads();
+  const int K = kq(P, q);
   if (tid == 0) {
     int i = 0;
-    while (i < nl && i < P.k) {
+    while (i < nl && i < K) {
       const double d0 = sd[i];
       const double lim = __dadd_rn(d0, __dmul_rn(1e-6, d0));
       int j = i;
@@ -1413,10 +1427,11 @@ __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __res
     }
   }
   __syncthreads();
-  if (tid == 0 && nl >= P.k) atomicAdd(counters + 7, (unsigned long long)(1e6 * sd[P.k - 1]));
-  if (tid < P.k) {
-    idx[q * P.k + tid] = tid < nl ? (int64_t)sid[tid] : -1;
-    dist[q * P.k + tid] = tid < nl ? (float)sd[tid] : INFINITY;
+  if (tid == 0 && nl >= K) atomicAdd(counters + 7, (unsigned long long)(1e6 * sd[K - 1]));
+  const int64_t o = P.qo ? P.qo[q] : q * P.k;
+  if (tid < K) {
+    idx[o + tid] = tid < nl ? (int64_t)sid[tid] : -1;
+    dist[o + tid] = tid < nl ? (float)sd[tid] : INFINITY;
   }
 }
 
@@ -1487,7 +1502,8 @@ __global__ void __launch_bounds__(128) k_window(QueryParams P, const float* __re
     }
   }
   __syncthreads();
-  const int kk = P.k < nl ? P.k : nl;
+  const int K = kq(P, q);
+  const int kk = K < nl ? K : nl;
   const double dk = kk > 0 ? sd[kk - 1] : INFINITY;
   const double lim = __dadd_rn(dk, __dmul_rn(1e-6, dk));
   if (tid < nl && sid[tid] != 0xFFFFFFFFu && (tid < kk || sd[tid] <= lim)) atomicMax(&s_cnt, tid + 1);
@@ -1521,6 +1537,8 @@ static QueryParams make_params(const Index* ix, int k) {
   P.NB = ix->NB;
   P.leaf_tiles = ix->leaf_tiles;
   P.k = k;
+  P.qk = nullptr;
+  P.qo = nullptr;
   P.cap = ix->cand_cap;
   P.group = ix->group;
   P.seed_count = ix->seed_count;
@@ -1571,11 +1589,14 @@ static int final_launch(Index* ix, const QueryParams& P, int64_t Q, const float*
 
 template <int LW, bool NYQ>
 static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* idx, float* dist,
-                       cudaStream_t st, bool capturing = false, const WindowOut& wo = WindowOut()) {
+                       cudaStream_t st, bool capturing = false, const WindowOut& wo = WindowOut(),
+                       const int* qk = nullptr, const int64_t* qo = nullptr) {
   QueryScratch& s = ix->qs;
   const int n = ix->n, NB = ix->NB;
   const int64_t L = ix->L;
   QueryParams P = make_params(ix, k);
+  P.qk = qk;
+  P.qo = qo;
   TRYQ(s.zq.ensure(Q * n * sizeof(float)));
   TRYQ(s.qv.ensure(Q * NB * sizeof(float)));
   TRYQ(s.llb.ensure(Q * L * sizeof(float)));
@@ -1884,12 +1905,13 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
 }
 
 static int dispatch_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* ip, float* dp, cudaStream_t st,
-                          bool capturing, const WindowOut& wo = WindowOut()) {
+                          bool capturing, const WindowOut& wo = WindowOut(), const int* qk = nullptr,
+                          const int64_t* qo = nullptr) {
   if (ix->LW == 16)
-    return ix->nyq_first ? query_batch<16, true>(ix, qp, qb, k, ip, dp, st, capturing, wo)
-                         : query_batch<16, false>(ix, qp, qb, k, ip, dp, st, capturing, wo);
-  return ix->nyq_first ? query_batch<32, true>(ix, qp, qb, k, ip, dp, st, capturing, wo)
-                       : query_batch<32, false>(ix, qp, qb, k, ip, dp, st, capturing, wo);
+    return ix->nyq_first ? query_batch<16, true>(ix, qp, qb, k, ip, dp, st, capturing, wo, qk, qo)
+                         : query_batch<16, false>(ix, qp, qb, k, ip, dp, st, capturing, wo, qk, qo);
+  return ix->nyq_first ? query_batch<32, true>(ix, qp, qb, k, ip, dp, st, capturing, wo, qk, qo)
+                       : query_batch<32, false>(ix, qp, qb, k, ip, dp, st, capturing, wo, qk, qo);
 }
 
 // A batch through a recorded CUDA graph.  The first batch of a shape runs
@@ -1970,7 +1992,8 @@ static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* i
   return 0;
 }
 
-int run_query(Index* ix, const float* q, int64_t Q, int k, int64_t* idx, float* dist, cudaStream_t st) {
+int run_query(Index* ix, const float* q, int64_t Q, int k, int64_t* idx, float* dist, cudaStream_t st,
+              const int* qk, const int64_t* qo) {
   NvtxScope range(ix->prof, "sofa_query");
   QueryScratch& s = ix->qs;
   const bool fresh = s.counters.p == nullptr;
@@ -1982,6 +2005,10 @@ int run_query(Index* ix, const float* q, int64_t Q, int k, int64_t* idx, float* 
   for (int64_t q0 = 0; q0 < Q; q0 += QB) {
     const int64_t qb = std::min(QB, Q - q0);
     const float* qp = q + q0 * ix->n;
+    if (qk) {  // mixed k: each query's results at its own offset (absolute); eager batches
+      TRYQ(dispatch_batch(ix, qp, qb, k, idx, dist, st, false, WindowOut(), qk + q0, qo + q0));
+      continue;
+    }
     int64_t* ip = idx + q0 * k;
     float* dp = dist + q0 * k;
     const bool graph = ix->use_graph && !ix->prof.on && qb * ix->L <= ((int64_t)1 << 28);

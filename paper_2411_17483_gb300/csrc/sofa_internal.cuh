@@ -24,6 +24,11 @@ void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 // True for device or managed memory (host memory, or an unknown pointer: false).
 bool is_device_ptr(const void* p);
+// Every device allocation of the library.  For testing the out-of-memory
+// paths without exhausting a GPU: when the environment variable
+// SOFA_TEST_MEM_CAP holds a byte count, any single allocation larger than it
+// fails with cudaErrorMemoryAllocation, as if the device were full.
+cudaError_t dev_malloc(void** p, size_t bytes);
 // SOFA_ERR_INVALID_ARG unless the calling thread's current device is the one
 // the index was built or loaded on: its buffers and the kernels launched for
 // it must be on the same GPU.
@@ -275,8 +280,11 @@ void destroy_index(Index* ix);
 int mlp_save(const Index* ix, void* file);   // FILE*; 0 or an error code
 int mlp_load(Index* ix, void* file, cudaStream_t st);
 
+// With qk (device, Q ints) each query has its own k <= k, and its results go
+// to idx / dist at element offset qo[i] (device, Q int64); otherwise query i's
+// k results go to offset i * k.
 int run_query(Index* ix, const float* q_dev, int64_t Q, int k, int64_t* idx_dev, float* dist_dev,
-              cudaStream_t st);
+              cudaStream_t st, const int* qk = nullptr, const int64_t* qo = nullptr);
 int run_query_window(Index* ix, const float* q_dev, int64_t Q, int k, int cap, int64_t* wid, double* wd2, int* wcnt,
                      cudaStream_t st);
 int launch_qprep(Index* ix, const float* q_dev, int64_t Q, float* zq, float* qv, cudaStream_t st);

@@ -41,7 +41,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 // times without success, so a wait that completes promptly never touches
 // the global timer.
 constexpr uint32_t MBAR_SUSPEND_NS = 10000;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = WAIT_NS) {
   const uint32_t a = smem_u32(bar);
   unsigned long long t0 = 0;
   for (uint32_t it = 0;; ++it) {
@@ -55,7 +55,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     if (done) return true;
     if (it == 64) t0 = global_ns();
-    else if (it > 64 && (it & 63) == 0 && global_ns() - t0 > WAIT_NS) return false;
+    else if (it > 64 && (it & 63) == 0 && global_ns() - t0 > limit_ns) return false;
   }
 }
 

@@ -147,7 +147,7 @@ int make_tc_codes(Index* ix, cudaStream_t st) {
   if (!ix->VC || !ix->vsr || !ix->vw) return 0;
   release_tc_codes(ix);
   const size_t hb = (size_t)ix->N * ix->NB * sizeof(__half), xb = (size_t)ix->N * sizeof(float4);
-  if (cudaMalloc((void**)&ix->VH, hb) != cudaSuccess || cudaMalloc((void**)&ix->vcx, xb) != cudaSuccess) {
+  if (dev_malloc((void**)&ix->VH, hb) != cudaSuccess || dev_malloc((void**)&ix->vcx, xb) != cudaSuccess) {
     cudaGetLastError();
     release_tc_codes(ix);
     return fail(SOFA_ERR_OOM, "allocation of the tensor-core value codes failed");
@@ -427,14 +427,15 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
           // pair rounds exactly as fmaf does)
           const float4* ac4 = sAC + 16 * h32;
           const float2 A2 = make_float2(cx.x, cx.x), B2 = make_float2(cx.y, cx.y);
-          float xmin = INFINITY;
+          float xm[4] = {INFINITY, INFINITY, INFINITY, INFINITY};  // four independent chains
 #pragma unroll
           for (int j = 0; j < 32; j += 2) {
             const float4 ac = ac4[j >> 1];  // (a_j, a_j+1, -c_j, -c_j+1)
             const float2 x2 = __ffma2_rn(B2, make_float2(ac.x, ac.y),
                                          __ffma2_rn(A2, make_float2(v[j], v[j + 1]), make_float2(ac.z, ac.w)));
-            xmin = fminf(xmin, fminf(x2.x, x2.y));
+            xm[(j >> 1) & 3] = fminf(xm[(j >> 1) & 3], fminf(x2.x, x2.y));
           }
+          const float xmin = fminf(fminf(xm[0], xm[1]), fminf(xm[2], xm[3]));
           const float negS = -cx.z;
           uint32_t mine = 0u;  // bit j: this lane's series survives query 32 h32 + j
           if (valid && xmin <= negS) {

@@ -116,6 +116,7 @@ def load():
         "sofa_lower_bounds_noalloc": (ctypes.c_int, [P, P, i64, P, P]),
         "sofa_dense_sqdist": (ctypes.c_int, [P, P, i64, P, ctypes.POINTER(ctypes.c_float), P]),
         "sofa_value_bounds": (ctypes.c_int, [P, P, i64, P, ctypes.POINTER(ctypes.c_float), P]),
+        "sofa_wait_selftest": (ctypes.c_int, [i32, P]),
         "sofa_save": (ctypes.c_int, [P, ctypes.c_char_p]),
         "sofa_load": (P, [ctypes.c_char_p, P]),
         "sofa_znorm": (ctypes.c_int, [P, i64, i32, P, P]),

@@ -73,3 +73,43 @@ def test_ablation_harness_small():
         assert 0.0 < r["tlb"] <= 1.0 + 1e-9 and 0.0 <= r["pruning"] <= 1.0
     text = ablation.table(rows, "t")
     assert text.count("\n| ") == 6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("binning,select", [("equi-depth", "variance"), ("equi-width", "first")])
+def test_ablation_sfa_measures_match_oracle(binning, select):
+    """The harness's SFA measures (the library's bounds, the GPU's FP64
+    distances) against the oracle's: its Eq. (1) SFA bound (orc.lb2) on the
+    oracle's words under the same summary, and its brute-force distances."""
+    from paper_2411_17483_gb300 import datagen, sofa
+    N, n, Q, l = 20000, 64, 10, 8
+    dev = "cuda:0"
+    x = datagen.random_walks(N, n, seed=71, device=dev)
+    q = datagen.random_walks(Q, n, seed=72, device=dev)
+    ix = sofa.Index(x, l, 256, sample_ratio=0.1, binning=binning, select=select)
+    z_gpu = sofa.znorm(x)
+    zq_gpu = sofa.znorm(q)
+    d2 = ablation.exact_sqdist(zq_gpu, z_gpu)
+    tlb_g, prune_g = ablation.measures(ix.lower_bounds(q).double(), d2)
+    # the oracle under the GPU's summary
+    sel, var, beta = ix.summary()
+    tab = orc.value_table(n, 0)
+    ids = sel.numpy().astype(np.int32)
+    ks = np.array([tab[c][0] for c in ids], np.int32)
+    parts = np.array([tab[c][1] for c in ids], np.int32)
+    summ = dict(ids=ids, ks=ks, parts=parts, w=np.array([orc.weight(n, int(k)) for k in ks]),
+                var=var.numpy(), beta=beta.numpy(), n=n, l=l, alpha=256)
+    z, _, _ = orc.znorm(x.cpu().numpy())
+    zq, _, _ = orc.znorm(q.cpu().numpy())
+    W = orc.words(z, summ)
+    qv = orc.selected_values(zq, summ)[:, :l]
+    olb2 = np.stack([orc.lb2(qv[i], W, summ) for i in range(Q)])
+    od2 = np.stack([orc.sqdist(z, zq[i]) for i in range(Q)])
+    # the harness's distances are the oracle's
+    assert np.allclose(d2.cpu().numpy(), od2, rtol=1e-9, atol=1e-9)
+    tlb_o, prune_o = ablation.measures(torch.from_numpy(olb2), torch.from_numpy(od2))
+    # the library's bounds carry the projection margins: never above the
+    # oracle's, and within a hair of them
+    assert tlb_g <= tlb_o + 1e-6 and tlb_g >= tlb_o - 2e-3, (tlb_g, tlb_o)
+    assert prune_g <= prune_o + 1e-3 and prune_g >= prune_o - 5e-3, (prune_g, prune_o)
+    ix.close()
