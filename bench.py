@@ -369,6 +369,12 @@ def multi_oracle_rate(a, rows_per_set, packed, qo, which, seconds):
     return 1.0 / per_query_s, cores, sample, el_all
 
 
+def precision_multi(tunings) -> str:
+    tc = any(t.get("series_bound") for t in tunings)
+    return ("fp32 SFA bounds" + (", tensor-core FP16 value-code series bound (derived margin)" if tc else "") +
+            ", int8 value-code and int8 row filters (derived margins), fp32 refine, fp64 final re-score")
+
+
 def run_sofa_multi(a, ws, rank, local):
     """Four random-walk indexes answered together by sofa_query_multi: plain
     FP32 refinement vs the refinement filters (both exact, same answers)."""
@@ -393,13 +399,28 @@ def run_sofa_multi(a, ws, rank, local):
         torch.cuda.empty_cache()
     packed, qo, ql, qk, oo, total, which = multi_queries(a, rank, dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-    modes = {"plain": {}, "filters": dict(refine_filter=2)}
+    # plain FP32 refinement; the refinement filters; and each index with the
+    # autotuner's pick, made on fresh queries of its own length (as many as
+    # the workload sends it, stream seed 200 + 1000 rank + dataset, k = 10),
+    # never on the timed ones
+    modes = {"plain": [{}] * len(ixs), "filters": [dict(refine_filter=2)] * len(ixs)}
     chosen = "filters"
+    if not a.no_autotune:
+        tuned = []
+        for si, ((N, n), ix) in enumerate(zip(MULTI_SETS, ixs)):
+            qt = datagen.random_walks(max(64, int((which == si).sum())), n, seed=200 + 1000 * rank + si, device=dev)
+            ix.set_seed_mode(0)
+            ix.set_tuning(refine_filter=2)
+            t = ix.autotune(qt, 10)
+            tuned.append({k: v for k, v in t.items() if v})
+            del qt
+        modes["tuned"] = tuned
+        chosen = "tuned"
     results, answers = {}, {}
     for name, tun in modes.items():
-        for ix in ixs:
+        for ix, t in zip(ixs, tun):
             ix.set_seed_mode(0)
-            ix.set_tuning(**tun)
+            ix.set_tuning(**t)
         for _ in range(a.warmup):
             sofa.query_multi(ixs, packed, qo, ql, qk, oo, total)
         torch.cuda.synchronize()
@@ -435,10 +456,12 @@ def run_sofa_multi(a, ws, rank, local):
                 "launches": {k: sum(p["launches"][k] for p in profs) for k in profs[0]["launches"]},
                 "scan_tile_loads": sum(p["scan_tile_loads"] for p in profs),
                 "scan_tile_checks": sum(p["scan_tile_checks"] for p in profs)}
-        results[name] = dict(ms=max_over_ranks(tot_ms / a.steps, ws, dev), prof=prof, stats=stats, clocks=clocks)
+        results[name] = dict(ms=max_over_ranks(tot_ms / a.steps, ws, dev), prof=prof, profs=profs, stats=stats,
+                             clocks=clocks)
         answers[name] = idx.clone()
-    if not torch.equal(answers["plain"], answers["filters"]):
-        raise RuntimeError("the two modes gave different answers")
+    for name in modes:
+        if not torch.equal(answers["plain"], answers[name]):
+            raise RuntimeError(f"modes plain and {name} gave different answers")
     r = results[chosen]
     value = ws * a.Q / (r["ms"] / 1e3)
     prof = r["prof"]
@@ -450,22 +473,35 @@ def run_sofa_multi(a, ws, rank, local):
             "traffic": None}
     alu = None
     if phase == "scan":
+        # each index's scan is the word bound (k_scan: LW bytes per (query,
+        # series) pair bounded) or the tensor-core bound (k_vscan: 256 x
+        # (2 NB + 16) bytes per (work unit, tile) load), by its own tuning;
+        # both add 2 LW bytes per tile envelope checked
+        tc = [bool(t.get("series_bound")) for t in modes[chosen]]
         tile_pairs = sum(s_["tile_pairs"] for s_ in r["stats"])
-        alg = (tile_pairs * 256 * LW + prof["scan_tile_checks"] * 2 * LW) / launches
+        alg = 0.0
+        for use_tc, p_, s_ in zip(tc, r["profs"], r["stats"]):
+            alg += p_["scan_tile_checks"] * 2 * LW
+            alg += p_["scan_tile_loads"] * 256 * (4 * LW + 16) if use_tc else s_["tile_pairs"] * 256 * LW
+        alg /= launches
         ach = alg / per_launch_s / 1e9
-        roof = {"kernel": "k_scan", "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+        kname = "k_vscan" if all(tc) else ("k_scan" if not any(tc) else "k_vscan+k_scan")
+        roof = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak, "traffic": None, "algorithmic_bytes_per_launch": alg,
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "note": "logical bytes: LW bytes per (query, series) pair bounded plus 2 LW per tile envelope "
-                        "checked; the queries of a work unit share each tile's read, so frac can exceed 1"}
-        clk = (r["clocks"].get("sm_mhz") or 1920.0) * 1e6
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_b = sms * 128 * clk / (3 * LW) / 1e9
-        ach_b = tile_pairs * 256 / launches / per_launch_s / 1e9
-        alu = {"kernel": "k_scan", "achieved": ach_b, "peak": peak_b, "unit": "G (query, series) bounds/s",
-               "frac": ach_b / peak_b,
-               "peak_kind": f"derived from the kernel's own 3 FP32 lane operations per value: {sms} SMs x 128 "
-                            f"lanes x {clk / 1e6:.0f} MHz / (3 x {LW})"}
+                "note": "per index: k_vscan moves 256 x (2 NB bytes of FP16 codes + 16 bytes of constants) per "
+                        "(work unit, tile) load; k_scan counts LW logical bytes per (query, series) pair "
+                        "bounded (the queries of a work unit share each tile's read, so its frac can exceed 1); "
+                        "plus 2 LW per tile envelope checked"}
+        if not any(tc):
+            clk = (r["clocks"].get("sm_mhz") or 1920.0) * 1e6
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak_b = sms * 128 * clk / (3 * LW) / 1e9
+            ach_b = tile_pairs * 256 / launches / per_launch_s / 1e9
+            alu = {"kernel": "k_scan", "achieved": ach_b, "peak": peak_b, "unit": "G (query, series) bounds/s",
+                   "frac": ach_b / peak_b,
+                   "peak_kind": f"derived from the kernel's own 3 FP32 lane operations per value: {sms} SMs x "
+                                f"128 lanes x {clk / 1e6:.0f} MHz / (3 x {LW})"}
     step_bytes = 0.0
     for (N, n), s_ in zip(MULTI_SETS, r["stats"]):
         vf, f8, rf = s_.get("value_filtered", 0), s_.get("filtered", 0), s_["refined"]
@@ -504,8 +540,7 @@ def run_sofa_multi(a, ws, rank, local):
             "config": {"workload": workload_name(a), "datasets": [f"{N}x{n}" for N, n in MULTI_SETS],
                        "Q_per_gpu": a.Q, "k": "uniform in {1, 5, 10, 50}", "l": a.l, "alphabet": a.alphabet,
                        "seed_mode": "plain", "tuning": modes[chosen],
-                       "precision": "fp32 SFA bounds, int8 value-code and int8 row filters (derived margins), "
-                                    "fp32 refine, fp64 final re-score",
+                       "precision": precision_multi(modes[chosen]),
                        "l2": "flushed between timed steps (256 MB write)", "build_s": round(build_s, 3),
                        "gen_s": round(gen_s, 3), "parallelism": f"replicas x{ws}"},
             "roofline": roof,

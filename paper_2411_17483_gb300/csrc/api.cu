@@ -148,7 +148,7 @@ static int num_candidates_host(int n, int pool) {
 void destroy_index(Index* ix) {
   if (!ix) return;
   void* ptrs[] = {ix->sel, ix->sel_k, ix->sel_part, ix->var, ix->basis, ix->beta, ix->edge, ix->ch, ix->ch16,
-                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->VC, ix->vsr, ix->vw, ix->xn, ix->Zh, ix->VH, ix->vcx, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
+                  ix->words, ix->Z, ix->Z8, ix->s8, ix->e8, ix->VC, ix->vsr, ix->vw, ix->xn, ix->Zh, ix->VH, ix->VK, ix->perm, ix->keys, ix->keyorder, ix->tenv, ix->lenv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   DevBuf* bufs[] = {&ix->qs.zq, &ix->qs.qv, &ix->qs.qn, &ix->qs.zqh, &ix->qs.llb, &ix->qs.thr, &ix->qs.list_d, &ix->qs.list_p,

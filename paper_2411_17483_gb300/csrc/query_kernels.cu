@@ -1739,8 +1739,12 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     // When the leaf bounds pass more than half of the (query, leaf block)
     // pairs, the series bounds would prune little: the batch is bounded by the
     // dense tensor-core contraction instead (same candidate store).
+    // A graph's recording takes the decision its shape's eager batch made
+    // (that batch reads the totals back even with upper-bound buffers).
     bool dense = false;
-    if (!(upper && pass == 0)) {
+    if (capturing && pass == 0) {
+      dense = ix->graph_dense;
+    } else if (!(upper && pass == 0) || ix->graph_probe) {
       if (capturing) return fail(SOFA_ERR_CUDA, "capture needs upper-bound buffers");
       int* tot = h_over + 2;
       SOFA_CUDA(cudaMemcpyAsync(&tot[0], s.leaf_off.as<int>() + L, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1754,6 +1758,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
         TRYQ(s.units.ensure(((size_t)tot[1] + 1) * sizeof(int4)));
       }
     }
+    if (pass == 0 && !capturing) ix->last_dense = dense;
     if (dense) {
       // the FP16 query copy (FP16 operands only), the query norms, the contraction
       ix->prof.begin(3, st, ix->Zh ? 3 : 2);
@@ -1944,7 +1949,11 @@ static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* i
   if (!e) {
     TRYQ(s.graph_in.ensure((size_t)qb * ix->n * sizeof(float)));
     TRYQ(s.graph_out.ensure((size_t)qb * k * (sizeof(int64_t) + sizeof(float))));
-    TRYQ(dispatch_batch(ix, qp, qb, k, ip, dp, st, false));  // sizes every buffer; the answers
+    ix->graph_probe = true;  // the eager batch decides dense or scan for the recording
+    const int rc0 = dispatch_batch(ix, qp, qb, k, ip, dp, st, false);  // sizes every buffer; the answers
+    ix->graph_probe = false;
+    TRYQ(rc0);
+    ix->graph_dense = ix->last_dense;
     SOFA_CUDA(cudaStreamSynchronize(st));
     const unsigned long long gen0 = g_buf_generation;
     Index::GraphEntry ne;

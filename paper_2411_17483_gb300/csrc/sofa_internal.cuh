@@ -158,9 +158,13 @@ struct Index {
   float* xn = nullptr;         // [N] ||x||^2 of each canonical series (dense path)
   __half* Zh = nullptr;        // [N][n] FP16 copy of the canonical series (dense path, precision 2)
   __half* VH = nullptr;        // [N][NB] the value codes as FP16 (tensor-core series bound), with VC
-  float4* vcx = nullptr;       // [N] (-2 s, -2 r, s^2 ||c||_w^2 - r^2 - M', 0) of the value codes
+  uint4* VK = nullptr;         // [N] 8 FP16 folded constants of the tensor-core test (alpha, beta, phi split)
   float tc_margin = 0.f;       // M': rounding margin of the tensor-core series bound
-  int64_t tc_bytes = 0;        // device bytes of VH and vcx
+  bool graph_probe = false;    // the eager batch before a graph recording reads the routed totals back
+  bool graph_dense = false;    // that batch's first pass took the dense contraction (the recording does too)
+  bool last_dense = false;     // the last eager batch's first pass took the dense contraction
+  float tc_amax = 0.f;         // A: the tensor-core test clamps sqrt(2 T) to A (it prunes nothing above)
+  int64_t tc_bytes = 0;        // device bytes of VH and VK
   uint32_t* perm = nullptr;    // [N] sorted position -> original row
   uint64_t* keys = nullptr;    // [N] sorted layout keys
   uint8_t* keyorder = nullptr; // [64] key bit order (dim << 3 | bit)
@@ -275,6 +279,7 @@ void release_tc_codes(Index* ix);
 bool vscan_supported(const Index* ix);
 int launch_vscan(Index* ix, const VscanArgs& a, cudaStream_t st);
 double tc_margin(const Index* ix);
+double tc_amax(const Index* ix);
 
 void destroy_index(Index* ix);
 int mlp_save(const Index* ix, void* file);   // FILE*; 0 or an error code

@@ -43,6 +43,8 @@ struct VsCfg {
   static constexpr int ROWB = NB * 2;             // bytes of one operand row (64 or 128)
   static constexpr int ATILE = TILE * ROWB;       // codes of one tile (16 KB or 32 KB)
   static constexpr int BTILE = VS_N * ROWB;       // query operand of one unit (4 KB or 8 KB)
+  static constexpr int KTILE = TILE * 16;         // folded constants of one tile: 8 FP16 per series
+  static constexpr int STAGE = ATILE + KTILE;     // one pipeline stage (multiple of 1024 bytes)
   static constexpr int STAGES = NB == 32 ? 3 : 2; // TMA pipeline depth (two CTAs per SM at NB = 32)
   static constexpr int MIN_CTAS = NB == 32 ? 2 : 1;
   static constexpr int KSTEPS = NB / 16;          // MMAs of K = 16 per half
@@ -99,12 +101,38 @@ __device__ __forceinline__ void tmem_ld1x4(uint32_t a0, uint32_t a1, uint32_t a2
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ------------------------------------------------------------------------
+// The folded test.  With D = (w o q~) . c (the MMA over the codes), the pair
+// survives iff  -2 s D - 2 r a - c_q <= -S'  (a = sqrt(2 T) of the query,
+// c_q = a^2 - ||q~||_w^2, S' = s^2 ||c||_w^2 - r^2 - M'), i.e. after dividing
+// by -2 s < 0:
+//   y = D + alpha a + beta c_q + phi >= 0,  alpha = r / s, beta = 1 / (2 s),
+//   phi = -S' / (2 s).
+// The three rank-one terms are one more K = 16 step of the same MMA: the
+// series side holds (alpha_h, alpha_h, alpha_l, beta_h, beta_h, beta_l,
+// phi_h, phi_l) and the query side (a_h, a_l, a_h, c_h, c_l, c_h, 1, 1),
+// each value split into an FP16 high part and an FP16 remainder, so that the
+// three products of each term carry its value to about 2^-21 (the low x low
+// product is dropped); the K step's other 8 columns are zero on the query
+// side.  The epilogue's test is then the sign of y: no per-pair arithmetic.
+// A series whose constants do not fit FP16 (scale s near 0) gets
+// (0, 0, 0, 0, 0, 0, FP16_MAX, FP16_MAX): y > 0 for every live query, so it
+// always survives (and its emitted bound is 0).
+constexpr float VK_LIMIT = 30000.f;  // |alpha|, |beta|, |phi| below this fit FP16 with their remainders
+constexpr float VK_ALWAYS = 65504.f; // FP16 max: the always-survive constant
+constexpr float VK_UNUSED_C = -60000.f;  // c of a query slot past the unit's queries: y < 0
+
+// FP16 high part and remainder of v (v - h is exact in FP32)
+__device__ __forceinline__ void split_f16(float v, __half& h, __half& l) {
+  h = __float2half_rn(v);
+  l = __float2half_rn(v - __half2float(h));
+}
+
 // Derived per-series arrays of the tensor-core bound, from the value codes:
-// VH[p] = the codes as FP16 (exact); vcx[p] = (-2 s, -2 r, S', 0) with
+// VH[p] = the codes as FP16 (exact); VK[p] = the folded constants above, with
 // S = s^2 ||c||_w^2 (FP64, rounded down) and S' = S - r^2 - M' rounded down.
 __global__ void k_vcodes_tc(const int8_t* __restrict__ VC, const float2* __restrict__ vsr,
                             const float* __restrict__ vw, int64_t N, int NB, float Mp, __half* __restrict__ VH,
-                            float4* __restrict__ vcx) {
+                            uint4* __restrict__ VK) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   double cw = 0.0;
@@ -117,37 +145,82 @@ __global__ void k_vcodes_tc(const int8_t* __restrict__ VC, const float2* __restr
   const double S = (double)sr.x * (double)sr.x * cw;
   const float r2 = __fmul_ru(sr.y, sr.y);
   const float Sp = __fsub_rd(__fsub_rd(__double2float_rd(S), r2), Mp);
-  vcx[p] = make_float4(-2.0f * sr.x, -2.0f * sr.y, Sp, 0.f);
+  __align__(16) __half h[8];
+  bool always = true;
+  if (sr.x > 0.f) {
+    const float al = __fdiv_rn(sr.y, sr.x), be = __fdiv_rn(0.5f, sr.x), ph = -__fmul_rn(Sp, be);
+    always = !(al >= 0.f && al < VK_LIMIT && be >= 0.25f && be < VK_LIMIT && fabsf(ph) < VK_LIMIT);
+    if (!always) {
+      split_f16(al, h[0], h[2]);
+      h[1] = h[0];
+      split_f16(be, h[3], h[5]);
+      h[4] = h[3];
+      split_f16(ph, h[6], h[7]);
+    }
+  }
+  if (always) {
+    for (int i = 0; i < 6; ++i) h[i] = __float2half_rn(0.f);
+    h[6] = h[7] = __float2half_rn(VK_ALWAYS);
+  }
+  VK[p] = *reinterpret_cast<const uint4*>(h);
 }
 
-// The margin M' >= |e~ - ||q~ - y||_w^2| of the tensor-core form plus the
-// rounding of the epilogue.  With R = sqrt(n) (1 + 2^-20) + sqrt(W) (delta_d
-// + delta_q) >= ||q~||_w, ||v~||_w (Parseval; W <= 2 nsel) and ||y||_w <= 1.04 R
-// (||v~ - y||_w <= sqrt(W) s / 2, s = max|v~| / 127):
+// The margin M' >= the error of the folded test, in squared-distance units
+// (multiply an error of y by 2 s).  With R = sqrt(n) (1 + 2^-20) + sqrt(W)
+// (delta_d + delta_q) >= ||q~||_w, ||v~||_w (Parseval; W <= 2 nsel),
+// Y = 1.04 R >= ||y||_w (||v~ - y||_w <= sqrt(W) s / 2, s = max|v~| / 127),
+// r <= Y, a <= A = 2.1 R + 1 (larger thresholds are clamped to A, which
+// prunes nothing either: sqrt(e) - r <= R + Y < A) and |c_q| <= C =
+// max(A^2, R^2):
 //  * query operand rounded to FP16: |fl(b) - b| <= 2^-11 |b| (+2^-25 below the
-//    normal range), so |2 s (fl(b) - b) . c| <= 2 (2^-11 + 2^-24) ||y||_w ||q~||_w
+//    normal range), so |2 s (fl(b) - b) . c| <= 2 (2^-11 + 2^-24) Y R
 //    + 2 s 127 NB 2^-25;
-//  * FP32 accumulation of NB products, up to 2 ulps each:
-//    2 NB 2^-22 ||y||_w ||q~||_w (1 + 2^-10);
-//  * ||q~||_w^2 summed in FP32 over NB terms: (NB + 1) 2^-24 R^2;
-//  * the epilogue (stored S, r^2, two FMAs and the comparison's terms, each
-//    at most 8 R^2 in magnitude): 64 2^-24 R^2.
+//  * FP32 accumulation of the NB + 16 products of the MMA, at most 2 ulps
+//    (2^-22) of the sum of their magnitudes per product: those magnitudes
+//    sum (times 2 s) to at most 2 Y R + 2 Y A + C + 2 Y^2;
+//  * the split constants: alpha a to 2^-19 Y A + 2^-23 (Y + 8 A), beta c_q to
+//    2^-19 C + 2^-24, phi to 2^-20 (2 Y^2 + 1) + 2^-21 (divisions, products
+//    and splits correctly rounded; remainders below the FP16 normal range
+//    lose at most 2^-25; s <= 8);
+//  * ||q~||_w^2 summed in FP32 over NB terms, S' and c_q:
+//    (64 + NB + 1) 2^-24 R^2.
 double tc_margin(const Index* ix) {
+  const double n = ix->n, W = 2.0 * ix->nsel, NB = ix->NB;
+  const double R = std::sqrt(n) * (1.0 + std::ldexp(1.0, -20)) + std::sqrt(W) * (ix->delta_d + ix->delta_q);
+  const double Y = 1.04 * R, A = tc_amax(ix), C = std::max(A * A, R * R);
+  const double m_tc = 2.0 * (std::ldexp(1.0, -11) + std::ldexp(1.0, -24)) * Y * R +
+                      2.0 * (R / 127.0) * 127.0 * NB * std::ldexp(1.0, -25);
+  const double m_acc = (NB + 16.0) * std::ldexp(1.0, -22) * (2.0 * Y * R + 2.0 * Y * A + C + 2.0 * Y * Y) *
+                       (1.0 + std::ldexp(1.0, -10));
+  const double m_split = std::ldexp(1.0, -19) * Y * A + std::ldexp(1.0, -23) * (Y + 8.0 * A) +
+                         std::ldexp(1.0, -19) * C + std::ldexp(1.0, -24) +
+                         std::ldexp(1.0, -20) * (2.0 * Y * Y + 1.0) + std::ldexp(1.0, -21);
+  const double m_ep = (64.0 + NB + 1) * std::ldexp(1.0, -24) * R * R;
+  return (m_tc + m_acc + m_split + m_ep) * 1.01;
+}
+
+// Threshold clamp A = 2.1 R + 1 (R as in tc_margin).
+double tc_amax(const Index* ix) {
   const double n = ix->n, W = 2.0 * ix->nsel;
   const double R = std::sqrt(n) * (1.0 + std::ldexp(1.0, -20)) + std::sqrt(W) * (ix->delta_d + ix->delta_q);
-  const double Y = 1.04 * R;
-  const double m_tc = 2.0 * (std::ldexp(1.0, -11) + std::ldexp(1.0, -24)) * Y * R +
-                      2.0 * (R / 127.0) * 127.0 * ix->NB * std::ldexp(1.0, -25);
-  const double m_acc = 2.0 * ix->NB * std::ldexp(1.0, -22) * Y * R * (1.0 + std::ldexp(1.0, -10));
-  const double m_ep = (64.0 + ix->NB + 1) * std::ldexp(1.0, -24) * R * R;
-  return (m_tc + m_acc + m_ep) * 1.01;
+  return 2.1 * R + 1.0;
+}
+
+// The folded test needs C = max(A^2, R^2) and |D| <= 127 sqrt(W) R to stay
+// well inside FP16 (c_q) and below the always-survive offset 2 FP16_MAX.
+static bool tc_fits(const Index* ix) {
+  const double n = ix->n, W = 2.0 * ix->nsel;
+  const double R = std::sqrt(n) * (1.0 + std::ldexp(1.0, -20)) + std::sqrt(W) * (ix->delta_d + ix->delta_q);
+  const double A = tc_amax(ix);
+  return std::max(A * A, R * R) < 30000.0 && 127.0 * std::sqrt(W) * R * 1.01 < 2.0 * 65504.0 - 1.0;
 }
 
 int make_tc_codes(Index* ix, cudaStream_t st) {
   if (!ix->VC || !ix->vsr || !ix->vw) return 0;
   release_tc_codes(ix);
-  const size_t hb = (size_t)ix->N * ix->NB * sizeof(__half), xb = (size_t)ix->N * sizeof(float4);
-  if (dev_malloc((void**)&ix->VH, hb) != cudaSuccess || dev_malloc((void**)&ix->vcx, xb) != cudaSuccess) {
+  if (!tc_fits(ix)) return 0;  // the folded test's constants would not fit FP16: no tensor-core bound
+  const size_t hb = (size_t)ix->N * ix->NB * sizeof(__half), xb = (size_t)ix->N * sizeof(uint4);
+  if (dev_malloc((void**)&ix->VH, hb) != cudaSuccess || dev_malloc((void**)&ix->VK, xb) != cudaSuccess) {
     cudaGetLastError();
     release_tc_codes(ix);
     return fail(SOFA_ERR_OOM, "allocation of the tensor-core value codes failed");
@@ -155,17 +228,18 @@ int make_tc_codes(Index* ix, cudaStream_t st) {
   ix->tc_bytes = (int64_t)(hb + xb);
   ix->device_bytes += ix->tc_bytes;
   ix->tc_margin = (float)tc_margin(ix);
+  ix->tc_amax = (float)tc_amax(ix);
   k_vcodes_tc<<<(unsigned)ceil_div(ix->N, 256), 256, 0, st>>>(ix->VC, ix->vsr, ix->vw, ix->N, ix->NB,
-                                                               ix->tc_margin, ix->VH, ix->vcx);
+                                                               ix->tc_margin, ix->VH, ix->VK);
   SOFA_CUDA(cudaGetLastError());
   return 0;
 }
 
 void release_tc_codes(Index* ix) {
   if (ix->VH) cudaFree(ix->VH);
-  if (ix->vcx) cudaFree(ix->vcx);
+  if (ix->VK) cudaFree(ix->VK);
   ix->VH = nullptr;
-  ix->vcx = nullptr;
+  ix->VK = nullptr;
   ix->device_bytes -= ix->tc_bytes;
   ix->tc_bytes = 0;
 }
@@ -174,46 +248,117 @@ void release_tc_codes(Index* ix) {
 // The tensor-core series scan.  A persistent CTA takes work units (leaf
 // block, up to 64 queries).  All warps first stage the unit: the queries'
 // SFA values (for the tile envelope checks), their FP16 operand w o q~ in the
-// swizzled layout the MMA reads, and their constants a = sqrt(2 T) rounded up
-// and c = a^2 - ||q~||_w^2; then the tile envelope checks give each tile its
-// mask of live queries (as in the word scan) and a list of live tiles.  Then:
-// warp 8 streams the live tiles' FP16 codes by TMA into a ring of stages;
-// warp 9 issues per tile 2 halves x NB/16 MMAs (M = 128 series, N = 64
-// queries, K = 16) into one of two TMEM accumulators; warps 0-7 (thread i =
-// series i of the tile) read, per live query, its accumulator column and
-// test  fma(-2r, a, fma(-2s, D, S')) <= c,  emitting survivors into the
+// swizzled layout the MMA reads, their folded-test operand (a, c_q split) and
+// a = min(sqrt(2 T) rounded up, A); then the tile envelope checks give each
+// tile its mask of live queries (as in the word scan) and a list of live
+// tiles.  Then: warp 8 streams the live tiles' FP16 codes and folded
+// constants by TMA into a ring of stages; warp 9 issues per tile 2 halves x
+// (NB/16 + 1) MMAs (M = 128 series, N = 64 queries, K = 16) into one of two
+// TMEM accumulators; warps 0-7 (thread i = series i of the tile) read the
+// accumulator rows, take the maximum of y over the columns (three-input max,
+// no other arithmetic), and only where some y >= 0 walk the surviving
+// columns, computing each survivor's lower bound and emitting it into the
 // candidate store with warp-aggregated atomics.  Every wait is bounded; a
 // wait that runs out stops all roles, lets issued copies and MMAs finish,
 // and sets SOFA_ERR_TIMEOUT.  With `dump` the kernel instead writes every
 // pair's lower bound (Q x N, original order) and emits nothing.
+
+// No-swizzle K-major shared-memory descriptor: core matrices of 8 rows x 16
+// bytes, `lbo` bytes apart along K and `sbo` bytes apart along M (or N),
+// descriptor version 1, layout type 0.
+__device__ __forceinline__ uint64_t nosw_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// 2 x 32 consecutive fp32 columns of this thread's TMEM lane, one wait.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t t0, uint32_t t1, float* v) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, "
+      "%45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%65];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(t0), "r"(t1)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The squared lower bound of a pair from its folded-test value y, the
+// query's a and the series' constants (k).  Algebra: with the true s and r,
+// (a + r)^2 - 2 s y = ||q~||_w^2 + S - 2 s D - M' - (the test's errors) <=
+// ||q~ - y||_w^2 = e, since M' covers those errors.  Here s and r come from
+// the split constants (s^ = 1 / (2 beta~), r^ = alpha~ s^, each within
+// 2^-18 relative (+2^-25 s absolute) of the true values); mu covers that and
+// the FP32 rounding of (a + r^)^2 - 2 s^ y, and r is rounded up before the
+// square root's difference, so the result is <= (sqrt(e) - r)^2 when
+// sqrt(e) >= r, and 0 otherwise.  A series with the always-survive
+// constants (beta~ = 0) gets 0.
+__device__ __forceinline__ float folded_lb2(float y, float a, uint4 k) {
+  const __half2 k0 = *reinterpret_cast<const __half2*>(&k.x);  // (alpha_h, alpha_h)
+  const __half2 k1 = *reinterpret_cast<const __half2*>(&k.y);  // (alpha_l, beta_h)
+  const __half2 k2 = *reinterpret_cast<const __half2*>(&k.z);  // (beta_h, beta_l)
+  const float be = __half2float(__low2half(k2)) + __half2float(__high2half(k2));  // exact in FP32
+  if (!(be > 0.f)) return 0.f;
+  const float al = __half2float(__low2half(k0)) + __half2float(__low2half(k1));
+  const float s_ = __fdiv_rn(0.5f, be);
+  const float r_ = al * s_;
+  const float ar = a + r_;
+  const float A2 = ar * ar;
+  const float Y2 = 2.0f * s_ * y;
+  const float mu = __fmul_ru(__fadd_ru(__fadd_ru(A2, fabsf(Y2)), 1.0f), 0x1.0p-15f);
+  const float el = __fsub_rd(__fsub_rd(A2, Y2), mu);
+  const float r_up = __fadd_ru(__fmul_ru(r_, 1.0f + 0x1.0p-17f), 0x1.0p-24f);
+  const float m = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(el, 0.f)), r_up), 0.f);
+  return __fmul_rd(m, m);
+}
+
 template <int NB, bool NYQ>
 __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
-    k_vscan(const __grid_constant__ CUtensorMap tmA, int64_t N, int64_t T, int n_leaf_tiles, int NBq,
-            const int4* __restrict__ units, const int* __restrict__ n_units_ptr, const int* __restrict__ leaf_q,
-            const float* __restrict__ qv, const float* __restrict__ thr, const uint8_t* __restrict__ tenv,
-            const float2* __restrict__ ch, const float4* __restrict__ vcx, const float* __restrict__ vw,
-            int cap, const int* __restrict__ qslot, uint32_t* __restrict__ cand_p, float* __restrict__ cand_lb,
-            int* __restrict__ cand_n, int64_t pool_cap, int* __restrict__ pool_n, int* __restrict__ pool_q,
-            uint32_t* __restrict__ pool_p, float* __restrict__ pool_lb, int* __restrict__ qpool_cnt,
-            float* __restrict__ dump, int64_t dumpQ, const uint32_t* __restrict__ perm,
-            unsigned long long* __restrict__ counters, int* __restrict__ status) {
+    k_vscan(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmK, int64_t N, int64_t T,
+            int n_leaf_tiles, int NBq, const int4* __restrict__ units, const int* __restrict__ n_units_ptr,
+            const int* __restrict__ leaf_q, const float* __restrict__ qv, const float* __restrict__ thr,
+            const uint8_t* __restrict__ tenv, const float2* __restrict__ ch, const uint4* __restrict__ VK,
+            const float* __restrict__ vw, float amax, int cap, const int* __restrict__ qslot,
+            uint32_t* __restrict__ cand_p, float* __restrict__ cand_lb, int* __restrict__ cand_n, int64_t pool_cap,
+            int* __restrict__ pool_n, int* __restrict__ pool_q, uint32_t* __restrict__ pool_p,
+            float* __restrict__ pool_lb, int* __restrict__ qpool_cnt, float* __restrict__ dump, int64_t dumpQ,
+            const uint32_t* __restrict__ perm, unsigned long long* __restrict__ counters, int* __restrict__ status) {
   constexpr int LW = NB / 2;
   using C = VsCfg<NB>;
   extern __shared__ __align__(16) uint8_t vsm[];
   float2* sch = reinterpret_cast<float2*>(vsm);  // LW x 256 (tile checks)
   const uint32_t raw = smem_u32(vsm);
   const uint32_t tab_end = raw + (uint32_t)(LW * MAX_ALPHA * sizeof(float2));
-  uint8_t* stages = vsm + (((tab_end + 1023u) & ~1023u) - raw);  // 1024-byte aligned swizzle atoms
-  uint8_t* sB = stages + C::STAGES * C::ATILE;
+  // [tables | pad to 1024 | folded-test operand of the unit: 64 x 16 B, then
+  // 1 KB of zeros | stages (1024-byte aligned swizzle atoms) | code operand]
+  uint8_t* sBK = vsm + (((tab_end + 1023u) & ~1023u) - raw);
+  uint8_t* stages = sBK + 2048;
+  uint8_t* sB = stages + C::STAGES * C::STAGE;  // the unit's code operand (swizzled)
   __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], tfull[2], tempty[2], drain;
   __shared__ uint16_t s_off[MAX_LEAF_TILES_VS + 1];
   __shared__ uint16_t stl[MAX_LEAF_TILES_VS];
   __shared__ __align__(16) float sq[VS_N][LW];
-  __shared__ float sT[VS_N], sQw[VS_N];
-  // per pair of query slots (2i, 2i+1): (a_2i, a_2i+1, -c_2i, -c_2i+1), with
-  // a = sqrt(2 T) rounded up and c = a^2 - ||q~||_w^2; slots past the unit's
-  // queries hold a = 0, -c = +inf and never survive
-  __shared__ __align__(16) float4 sAC[VS_N / 2];
+  __shared__ float sT[VS_N], sA[VS_N];
   __shared__ int sslot[VS_N], sqid[VS_N];
   __shared__ unsigned long long smask[MAX_LEAF_TILES_VS];
   __shared__ uint32_t s_tmem;
@@ -221,6 +366,8 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   volatile int* vfail = &s_fail;
   for (int e = tid; e < LW * MAX_ALPHA; e += blockDim.x) sch[e] = ch[e];
+  // the zero half (K columns 8-15) of the folded-test operand, written once
+  for (int e = tid; e < 1024 / 16; e += blockDim.x) reinterpret_cast<uint4*>(sBK + 1024)[e] = make_uint4(0, 0, 0, 0);
   if (warp == 9) tmem_alloc(&s_tmem, VS_TMEM);
   if (tid == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -275,27 +422,39 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
       }
       *reinterpret_cast<uint4*>(sB + g * C::ROWB + vs_chunk<NB>(g, c) * 16) = *reinterpret_cast<const uint4*>(hv);
     }
-    fence_proxy_async();  // the operand's generic stores, before the MMAs read it
     for (int t = tid; t < nt; t += blockDim.x) smask[t] = 0ull;
     __syncthreads();
-    if (tid < cnt) {
-      // ||q~||_w^2 in FP32 (its rounding, <= (NB + 1) 2^-24 ||q~||_w^2, is part of M')
-      const int qq = sqid[tid];
-      float Qw = 0.f;
-      for (int j = 0; j < NB; ++j) {
-        const float v = qv[(int64_t)qq * NBq + j];
-        Qw = fmaf(__ldg(vw + j) * v, v, Qw);
+    if (tid < VS_N) {
+      // the folded-test operand of query slot tid: (a_h, a_l, a_h, c_h, c_l,
+      // c_h, 1, 1) with a = min(sqrt(2 T) rounded up, A) and c_q = a^2 -
+      // ||q~||_w^2 rounded up (||q~||_w^2 in FP32; its rounding is part of
+      // M'); a slot past the unit's queries gets a = 0, c = -60000 and -1's,
+      // which make y negative for every series
+      __align__(16) __half hk[8];
+      if (tid < cnt) {
+        const int qq = sqid[tid];
+        float Qw = 0.f;
+        for (int j = 0; j < NB; ++j) {
+          const float v = qv[(int64_t)qq * NBq + j];
+          Qw = fmaf(__ldg(vw + j) * v, v, Qw);
+        }
+        const float a = fminf(__fsqrt_ru(__fmul_ru(2.0f, sT[tid])), amax);
+        const float c = __fsub_ru(__fmul_ru(a, a), Qw);
+        sA[tid] = a;
+        split_f16(a, hk[0], hk[1]);
+        hk[2] = hk[0];
+        split_f16(c, hk[3], hk[4]);
+        hk[5] = hk[3];
+        hk[6] = hk[7] = __float2half_rn(1.0f);
+      } else {
+        hk[0] = hk[1] = hk[2] = hk[4] = __float2half_rn(0.f);
+        hk[3] = hk[5] = __float2half_rn(VK_UNUSED_C);
+        hk[6] = hk[7] = __float2half_rn(-1.0f);
+        sA[tid] = 0.f;
       }
-      const float a = __fsqrt_ru(__fmul_ru(2.0f, sT[tid]));
-      sQw[tid] = Qw;
-      float* acf = reinterpret_cast<float*>(&sAC[tid >> 1]);
-      acf[tid & 1] = a;
-      acf[2 + (tid & 1)] = -__fsub_ru(__fmul_ru(a, a), Qw);
-    } else if (tid < VS_N) {
-      float* acf = reinterpret_cast<float*>(&sAC[tid >> 1]);
-      acf[tid & 1] = 0.f;
-      acf[2 + (tid & 1)] = INFINITY;
+      *reinterpret_cast<uint4*>(sBK + 16 * tid) = *reinterpret_cast<const uint4*>(hk);
     }
+    fence_proxy_async();  // the operands' generic stores, before the MMAs read them
     // ---- tile envelope checks (every pair when dumping)
     if (dump) {
       const unsigned long long all = cnt >= 64 ? ~0ull : ((1ull << cnt) - 1ull);
@@ -334,7 +493,7 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
     __syncthreads();
     const int ntl = s_ntl;
     if (warp == 8) {
-      if (lane == 0) {  // TMA producer
+      if (lane == 0) {  // TMA producer: codes and folded constants of each live tile
         for (int i = 0; i < ntl; ++i) {
           const long long g_ = gi + i;
           const int s = (int)(g_ % C::STAGES);
@@ -343,13 +502,15 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
             break;
           }
           if (*vfail) break;
-          mbar_expect_tx(&full[s], C::ATILE);
-          tma_load_2d(stages + s * C::ATILE, &tmA, 0, (int)((t0 + stl[i]) * TILE), &full[s]);
+          const int row = (int)((t0 + stl[i]) * TILE);
+          mbar_expect_tx(&full[s], C::ATILE + C::KTILE);
+          tma_load_2d(stages + s * C::STAGE, &tmA, 0, row, &full[s]);
+          tma_load_2d(stages + s * C::STAGE + C::ATILE, &tmK, 0, row, &full[s]);
         }
       }
     } else if (warp == 9) {
       if (lane == 0) {  // MMA issuer
-        const uint32_t sb = smem_u32(sB);
+        const uint32_t sb = smem_u32(sB), sbk = smem_u32(sBK);
         for (int i = 0; i < ntl; ++i) {
           const long long g_ = gi + i;
           const int s = (int)(g_ % C::STAGES), acc = (int)(g_ & 1);
@@ -362,13 +523,17 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(stages + s * C::ATILE);
+          const uint32_t sa = smem_u32(stages + s * C::STAGE), sk = sa + C::ATILE;
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t d = tmem + (uint32_t)(acc * 128 + h * 64);
 #pragma unroll
             for (int kk = 0; kk < C::KSTEPS; ++kk)
-              mma_f16_n64(tmem + (uint32_t)(acc * 128 + h * 64), vs_desc<NB>(sa + h * 128 * C::ROWB) + 2 * kk,
-                          vs_desc<NB>(sb) + 2 * kk, kk > 0 ? 1u : 0u);
+              mma_f16_n64(d, vs_desc<NB>(sa + h * 128 * C::ROWB) + 2 * kk, vs_desc<NB>(sb) + 2 * kk, kk > 0 ? 1u : 0u);
+            // the folded constants: the series side's K columns 8-15 repeat
+            // columns 0-7 (LBO 0; the query side is zero there)
+            mma_f16_n64(d, nosw_desc(sk + h * 128 * 16, 0, 128), nosw_desc(sbk, 1024, 128), 1u);
+          }
           mma_commit(&empty[s]);
           mma_commit(&tfull[acc]);
         }
@@ -385,7 +550,9 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
         const int o0 = s_off[t], o1 = s_off[t + 1];
         const int64_t p = (t0 + t) * TILE + tid;
         const bool valid = p < N;
-        const float4 cx = valid ? __ldg(vcx + p) : make_float4(0.f, 0.f, INFINITY, 0.f);
+        // the series' folded constants (for the bounds of its survivors; the
+        // tile's TMA copy brought the line into L2), loaded before the wait
+        const uint4 kx = valid ? __ldg(VK + p) : make_uint4(0, 0, 0, 0);
         if (!__all_sync(0xFFFFFFFFu, mbar_wait(&tfull[acc], (uint32_t)((g_ >> 1) & 1)))) {
           *vfail = 1;
           break;
@@ -397,60 +564,61 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
           n_loads += 1;
         }
         const unsigned long long tmask = smask[t];
-        // the tile's live queries, 32 accumulator columns at a time: one TMEM
-        // load per half, then a walk over the mask bits (uniform in the CTA)
+        if (dump) {  // every live pair's bound, 32 columns at a time
 #pragma unroll 1
-        for (int h32 = 0; h32 < 2; ++h32) {
-          const uint32_t m = (uint32_t)(tmask >> (32 * h32));
-          if (m == 0u) continue;
-          float v[32];
-          tmem_ld32(tb + (uint32_t)(32 * h32), v);  // warp-collective
-          if (dump) {
+          for (int h32 = 0; h32 < 2; ++h32) {
+            float w[32];
+            tmem_ld32(tb + (uint32_t)(32 * h32), w);  // warp-collective
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              if (!(m & (1u << j)) || !valid) continue;
               const int g = 32 * h32 + j;
-              const float rr = -0.5f * cx.y;
-              const float el = fmaf(cx.x, v[j], cx.z) + sQw[g] + __fmul_rd(rr, rr);
-              const float mm = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(el, 0.f)), rr), 0.f);
-              dump[(int64_t)sqid[g] * N + perm[p]] = __fmul_rd(mm, mm);
+              if (((tmask >> g) & 1ull) && valid) dump[(int64_t)sqid[g] * N + perm[p]] = folded_lb2(w[j], sA[g], kx);
             }
-            continue;
           }
-          // Survival of query j: fma(-2r, a_j, fma(-2s, D_j, S')) <= c_j, i.e.
-          // x_j = fma(-2r, a_j, fma(-2s, D_j, -c_j)) <= -S'.  The lane first
-          // takes the minimum of x_j over the half's 32 columns (two FMAs and
-          // a min each, no branch; unused slots give +inf); only a lane whose
-          // minimum passes (rare) tests the columns one by one, with the
-          // tile's mask of live queries.
-          // two columns per step with packed FP32x2 FMAs (each lane of the
-          // pair rounds exactly as fmaf does)
-          const float4* ac4 = sAC + 16 * h32;
-          const float2 A2 = make_float2(cx.x, cx.x), B2 = make_float2(cx.y, cx.y);
-          float xm[4] = {INFINITY, INFINITY, INFINITY, INFINITY};  // four independent chains
+        }
+        float mx[2];  // the lane's maximum of y over each 32 columns
+        {
+          float v[64];
+          tmem_ld32x2(tb, tb + 32u, v);  // warp-collective
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const float4 ac = ac4[j >> 1];  // (a_j, a_j+1, -c_j, -c_j+1)
-            const float2 x2 = __ffma2_rn(B2, make_float2(ac.x, ac.y),
-                                         __ffma2_rn(A2, make_float2(v[j], v[j + 1]), make_float2(ac.z, ac.w)));
-            xm[(j >> 1) & 3] = fminf(xm[(j >> 1) & 3], fminf(x2.x, x2.y));
+          for (int h32 = 0; h32 < 2; ++h32) {
+            const float* w = v + 32 * h32;
+            float c0 = fmax3(w[0], w[1], w[2]), c1 = fmax3(w[3], w[4], w[5]);
+            float c2 = fmax3(w[6], w[7], w[8]), c3 = fmax3(w[9], w[10], w[11]);
+            c0 = fmax3(c0, w[12], w[13]);
+            c1 = fmax3(c1, w[14], w[15]);
+            c2 = fmax3(c2, w[16], w[17]);
+            c3 = fmax3(c3, w[18], w[19]);
+            c0 = fmax3(c0, w[20], w[21]);
+            c1 = fmax3(c1, w[22], w[23]);
+            c2 = fmax3(c2, w[24], w[25]);
+            c3 = fmax3(c3, w[26], w[27]);
+            c0 = fmax3(c0, w[28], w[29]);
+            c1 = fmax3(c1, w[30], w[31]);
+            mx[h32] = fmax3(c0, c1, fmaxf(c2, c3));
           }
-          const float xmin = fminf(fminf(xm[0], xm[1]), fminf(xm[2], xm[3]));
-          const float negS = -cx.z;
-          uint32_t mine = 0u;  // bit j: this lane's series survives query 32 h32 + j
-          if (valid && xmin <= negS) {
+        }
+        // a series survives a query iff its y >= 0: a lane whose maxima are
+        // negative is done with the tile
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              const float4 ac = ac4[j >> 1];
-              const float2 x2 = __ffma2_rn(B2, make_float2(ac.x, ac.y),
-                                           __ffma2_rn(A2, make_float2(v[j], v[j + 1]), make_float2(ac.z, ac.w)));
-              mine |= (x2.x <= negS ? 1u : 0u) << j;
-              mine |= (x2.y <= negS ? 1u : 0u) << (j + 1);
+        for (int h32 = 0; h32 < 2; ++h32) {
+          const uint32_t m = (uint32_t)(tmask >> (32 * h32));
+          const bool maybe = !dump && valid && m != 0u && mx[h32] >= 0.f;
+          if (!__any_sync(0xFFFFFFFFu, maybe)) continue;
+          // rare: this lane's surviving columns of the half (its 32 columns
+          // reloaded), then a walk over the columns where some lane survives
+          uint32_t mine = 0u;
+          {
+            float w[32];
+            tmem_ld32(tb + (uint32_t)(32 * h32), w);  // warp-collective
+            if (maybe) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) mine |= (w[j] >= 0.f ? 1u : 0u) << j;
+              mine &= m;
             }
-            mine &= m;
           }
           uint32_t any = __reduce_or_sync(0xFFFFFFFFu, mine);
-          while (any) {  // rare: the columns where some lane of the warp survives
+          while (any) {
             const int j = __ffs(any) - 1;
             any &= any - 1u;
             const int g = 32 * h32 + j;
@@ -458,13 +626,8 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
             const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
             float dcol[4];
             tmem_ld1x4(tb + (uint32_t)g, tb + (uint32_t)g, tb + (uint32_t)g, tb + (uint32_t)g, dcol);
-            float acc_lb = 0.f;
-            if (live) {  // the pair's lower bound in half units, rounded down
-              const float rr = -0.5f * cx.y;
-              const float el = fmaf(cx.x, dcol[0], cx.z) + sQw[g] + __fmul_rd(rr, rr);
-              const float mm = fmaxf(__fsub_rd(__fsqrt_rd(fmaxf(el, 0.f)), rr), 0.f);
-              acc_lb = __fmul_rd(__fmul_rd(mm, mm), 0.5f);
-            }
+            // the pair's lower bound in half units, rounded down
+            const float acc_lb = live ? __fmul_rd(folded_lb2(dcol[0], sA[g], kx), 0.5f) : 0.f;
             const int qs = sslot[g];
             const int npop = __popc(hit);
             int base = 0, pbase = 0;
@@ -533,20 +696,21 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
 static size_t vscan_smem(const Index* ix) {
   const int LW = ix->LW;
   const size_t tab = (size_t)LW * MAX_ALPHA * sizeof(float2);
-  const size_t stage = ix->NB == 32 ? (size_t)VsCfg<32>::STAGES * VsCfg<32>::ATILE + VsCfg<32>::BTILE
-                                    : (size_t)VsCfg<64>::STAGES * VsCfg<64>::ATILE + VsCfg<64>::BTILE;
-  return tab + 1024 + stage;
+  const size_t stage = ix->NB == 32 ? (size_t)VsCfg<32>::STAGES * VsCfg<32>::STAGE + VsCfg<32>::BTILE
+                                    : (size_t)VsCfg<64>::STAGES * VsCfg<64>::STAGE + VsCfg<64>::BTILE;
+  return tab + 1024 + stage + 2048;  // + the folded-test operand (1 KB) and its zero half (1 KB)
 }
 
 bool vscan_supported(const Index* ix) {
-  return ix->VH && ix->vcx && (ix->NB == 32 || ix->NB == 64) && ix->leaf_tiles <= MAX_LEAF_TILES_VS &&
+  return ix->VH && ix->VK && (ix->NB == 32 || ix->NB == 64) && ix->leaf_tiles <= MAX_LEAF_TILES_VS &&
          ix->group <= VS_N;
 }
 
 template <int NB, bool NYQ>
 static int launch_vscan_t(Index* ix, const VscanArgs& A, cudaStream_t st) {
-  CUtensorMap tm;
+  CUtensorMap tm, tk;
   if (int rc = make_tensor_map_2d(&tm, ix->VH, ix->N, NB, 2, NB, TILE, NB == 32 ? 64 : 128)) return rc;
+  if (int rc = make_tensor_map_2d(&tk, ix->VK, ix->N, 8, 2, 8, TILE, 0)) return rc;  // 16-byte rows, no swizzle
   const size_t smem = vscan_smem(ix);
   auto fn = k_vscan<NB, NYQ>;
   SOFA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -568,8 +732,9 @@ static int launch_vscan_t(Index* ix, const VscanArgs& A, cudaStream_t st) {
   int per_sm = (int)std::min<int64_t>(smem_sm / smem_cta, regs_sm / std::max<int64_t>(1, regs_cta));
   per_sm = std::max(1, std::min(per_sm, 512 / VS_TMEM));
   const int grid = sms * per_sm;
-  fn<<<grid, VS_THREADS, smem, st>>>(tm, ix->N, ix->T, ix->leaf_tiles, ix->NB, A.units, A.n_units, A.leaf_q, A.qv,
-                                     A.thr, ix->tenv, ix->ch, ix->vcx, ix->vw, A.cap, A.qslot, A.cand_p, A.cand_lb,
+  fn<<<grid, VS_THREADS, smem, st>>>(tm, tk, ix->N, ix->T, ix->leaf_tiles, ix->NB, A.units, A.n_units, A.leaf_q,
+                                     A.qv, A.thr, ix->tenv, ix->ch, ix->VK, ix->vw, ix->tc_amax, A.cap, A.qslot,
+                                     A.cand_p, A.cand_lb,
                                      A.cand_n, A.pool_cap, A.pool_n, A.pool_q, A.pool_p, A.pool_lb, A.qpool_cnt,
                                      A.dump, A.dumpQ, ix->perm, A.counters, A.status);
   SOFA_CUDA(cudaGetLastError());

@@ -114,3 +114,30 @@ def test_dense_chosen_when_bounds_fail(sofa):
     oi, od = oracle_knn(x, q, 1)
     assert np.array_equal(gi.cpu().numpy(), oi)
     ix.close()
+
+
+def test_graph_recording_takes_the_dense_decision(sofa):
+    """A recorded graph replays the decision of its shape's eager batch: on
+    high-frequency data that batch takes the dense form, so the replays do too
+    (the device counters see Q x N dense pairs per execution and no scanned
+    tile), with the same exact answers as the eager batches."""
+    N, n, Q = 40000, 512, 32
+    x = datagen.sinusoid_mix(N, n, seed=79, device=DEV)
+    batches = [datagen.sinusoid_mix(Q, n, seed=80 + i, device=DEV) for i in range(3)]
+    ix = sofa.Index(x, 16, 256)
+    eager = [ix.query(q, 2) for q in batches]
+    ix.set_tuning(use_graph=1)
+    ix.stats(reset=True)
+    for _ in range(2):                      # first call records, later calls replay
+        for q, (ei, ed) in zip(batches, eager):
+            gi, gd = ix.query(q, 2)
+            torch.cuda.synchronize()
+            assert torch.equal(gi, ei) and torch.equal(gd, ed)
+    assert ix.status() == 0
+    st = ix.stats()
+    assert st["graphs_recorded"] == 1 and st["graph_replays"] == 5
+    # executions: the recording's eager batch and 5 replays (a capture runs nothing)
+    assert st["dense_pairs"] == 6 * Q * N and st["tile_pairs"] == 0, st
+    oi, od = oracle_knn(x, batches[0], 2)
+    assert np.array_equal(eager[0][0].cpu().numpy(), oi)
+    ix.close()
