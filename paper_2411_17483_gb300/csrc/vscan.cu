@@ -45,6 +45,14 @@ struct VsCfg {
   static constexpr int BTILE = VS_N * ROWB;       // query operand of one unit (4 KB or 8 KB)
   static constexpr int KTILE = TILE * 16;         // folded constants of one tile: 8 FP16 per series
   static constexpr int STAGE = ATILE + KTILE;     // one pipeline stage (multiple of 1024 bytes)
+  // staging area of a unit (the queries' SFA values, value-major; up to 64
+  // tile envelopes; the intervals of 16 tiles), reused during its tiles as
+  // the candidate list (10 bytes an entry)
+  static constexpr int SQ_BYTES = VS_N * (NB / 2) * 4;
+  static constexpr int ENV_BYTES = 64 * NB;
+  static constexpr int IVL_BYTES = 16 * (NB / 2) * 8;
+  static constexpr int UNION = SQ_BYTES + ENV_BYTES + IVL_BYTES;
+  static constexpr int SC = (UNION / 10 & ~31) < 1024 ? (UNION / 10 & ~31) : 1024;
   static constexpr int STAGES = NB == 32 ? 3 : 2; // TMA pipeline depth (two CTAs per SM at NB = 32)
   static constexpr int MIN_CTAS = NB == 32 ? 2 : 1;
   static constexpr int KSTEPS = NB / 16;          // MMAs of K = 16 per half
@@ -80,22 +88,16 @@ __device__ __forceinline__ void mma_f16_n64(uint32_t d_tmem, uint64_t adesc, uin
       "l"(adesc), "l"(bdesc), "r"(vscan_idesc()), "r"(accumulate));
 }
 
-// Four accumulator columns of this thread's TMEM lane, one wait.
-__device__ __forceinline__ void tmem_ld1x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, float* v) {
-  uint32_t r0, r1, r2, r3;
+// One accumulator column of this thread's TMEM lane (load and wait).
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+  uint32_t r;
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%4];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%1}, [%5];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%2}, [%6];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%3}, [%7];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n\t"
       "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+      : "=r"(r)
+      : "r"(taddr)
       : "memory");
-  v[0] = __uint_as_float(r0);
-  v[1] = __uint_as_float(r1);
-  v[2] = __uint_as_float(r2);
-  v[3] = __uint_as_float(r3);
+  return __uint_as_float(r);
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -257,8 +259,9 @@ void release_tc_codes(Index* ix) {
 // TMEM accumulators; warps 0-7 (thread i = series i of the tile) read the
 // accumulator rows, take the maximum of y over the columns (three-input max,
 // no other arithmetic), and only where some y >= 0 walk the surviving
-// columns, computing each survivor's lower bound and emitting it into the
-// candidate store with warp-aggregated atomics.  Every wait is bounded; a
+// columns, computing each survivor's lower bound and appending it to the
+// unit's candidate list in shared memory; at the end of the unit the list
+// goes to the candidate store with one global reservation per query.  Every wait is bounded; a
 // wait that runs out stops all roles, lets issued copies and MMAs finish,
 // and sets SOFA_ERR_TIMEOUT.  With `dump` the kernel instead writes every
 // pair's lower bound (Q x N, original order) and emits nothing.
@@ -357,7 +360,18 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
   __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], tfull[2], tempty[2], drain;
   __shared__ uint16_t s_off[MAX_LEAF_TILES_VS + 1];
   __shared__ uint16_t stl[MAX_LEAF_TILES_VS];
-  __shared__ __align__(16) float sq[VS_N][LW];
+  // staging: sqT (the queries' SFA values, value-major), s_env (64 tile
+  // envelopes) and s_ivl (the intervals of 16 tiles); during the tiles: the
+  // candidate list (positions, bounds, query slot << 10 | rank in its query)
+  __shared__ __align__(16) uint8_t s_union[C::UNION];
+  float(*sqT)[VS_N] = reinterpret_cast<float(*)[VS_N]>(s_union);
+  uint8_t* s_env = s_union + C::SQ_BYTES;
+  float2* s_ivl = reinterpret_cast<float2*>(s_union + C::SQ_BYTES + C::ENV_BYTES);
+  uint32_t* s_cp = reinterpret_cast<uint32_t*>(s_union);
+  float* s_cl = reinterpret_cast<float*>(s_union + 4 * C::SC);
+  uint16_t* s_cgr = reinterpret_cast<uint16_t*>(s_union + 8 * C::SC);
+  __shared__ int s_qn[VS_N], s_qbase[VS_N], s_qpbase[VS_N];
+  __shared__ int s_cn, s_clim;
   __shared__ float sT[VS_N], sA[VS_N];
   __shared__ int sslot[VS_N], sqid[VS_N];
   __shared__ unsigned long long smask[MAX_LEAF_TILES_VS];
@@ -397,73 +411,122 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
     const int cnt = un.z;
     const int64_t t0 = b * n_leaf_tiles;
     const int nt = (int)((T - t0) < n_leaf_tiles ? (T - t0) : n_leaf_tiles);
-    // ---- stage the unit's queries
-    for (int e = tid; e < cnt * LW; e += blockDim.x) {
-      const int g = e / LW, j = e - g * LW;
-      const int qq = leaf_q[un.y + g];
-      sq[g][j] = qv[(int64_t)qq * NBq + j];
-      if (j == 0) {
-        sqid[g] = qq;
-        sslot[g] = qslot ? qslot[qq] : qq;
-        sT[g] = dump ? 0.f : thr[qq];
-      }
-    }
+    // ---- stage the unit's queries: CH threads per query slot, 8 values each
+    // (two 16-byte loads after the query's id); the FP16 operand w o q~ in
+    // the swizzled layout, the SFA values for the envelope checks, ||q~||_w^2
+    // (FP32, partial sums over the CH threads; its rounding is part of M'),
+    // and the folded-test operand (a_h, a_l, a_h, c_h, c_l, c_h, 1, 1) with
+    // a = min(sqrt(2 T) rounded up, A) and c_q = a^2 - ||q~||_w^2 rounded up;
+    // a slot past the unit's queries gets a = 0, c = -60000 and -1's, which
+    // make y negative for every series
     constexpr int CH = NB / 8;  // 16-byte chunks of an operand row
-    for (int e = tid; e < VS_N * CH; e += blockDim.x) {
+    if (tid < VS_N) s_qn[tid] = 0;
+    if (tid == 0) {
+      s_cn = 0;
+      s_clim = C::SC;
+    }
+    for (int e = tid; e < VS_N * CH; e += blockDim.x) {  // whole warps: VS_N * CH is a multiple of 32
       const int g = e / CH, c = e - g * CH;
-      __align__(16) __half hv[8];
+      float v[8];
+      float T_ = 0.f;
+      int qq = 0, qs = 0;
       if (g < cnt) {
-        const int qq = leaf_q[un.y + g];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) hv[i] = __float2half_rn(__ldg(vw + 8 * c + i) * qv[(int64_t)qq * NBq + 8 * c + i]);
+        qq = leaf_q[un.y + g];
+        const float4* src = reinterpret_cast<const float4*>(qv + (int64_t)qq * NBq + 8 * c);
+        const float4 v0 = src[0], v1 = src[1];
+        v[0] = v0.x, v[1] = v0.y, v[2] = v0.z, v[3] = v0.w, v[4] = v1.x, v[5] = v1.y, v[6] = v1.z, v[7] = v1.w;
+        if (c == 0) {
+          T_ = dump ? 0.f : thr[qq];
+          qs = qslot ? qslot[qq] : qq;
+        }
       } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) hv[i] = __float2half_rn(0.f);
+        for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      }
+      __align__(16) __half hv[8];
+      float part = 0.f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float wv = __ldg(vw + 8 * c + i) * v[i];
+        hv[i] = __float2half_rn(wv);
+        part = fmaf(wv, v[i], part);
       }
       *reinterpret_cast<uint4*>(sB + g * C::ROWB + vs_chunk<NB>(g, c) * 16) = *reinterpret_cast<const uint4*>(hv);
+      if (8 * c < LW) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sqT[8 * c + i][g] = v[i];
+      }
+#pragma unroll
+      for (int o = 1; o < CH; o <<= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+      if (c == 0) {
+        __align__(16) __half hk[8];
+        if (g < cnt) {
+          const float a = fminf(__fsqrt_ru(__fmul_ru(2.0f, T_)), amax);
+          const float cq = __fsub_ru(__fmul_ru(a, a), part);
+          sA[g] = a;
+          sT[g] = T_;
+          sqid[g] = qq;
+          sslot[g] = qs;
+          split_f16(a, hk[0], hk[1]);
+          hk[2] = hk[0];
+          split_f16(cq, hk[3], hk[4]);
+          hk[5] = hk[3];
+          hk[6] = hk[7] = __float2half_rn(1.0f);
+        } else {
+          hk[0] = hk[1] = hk[2] = hk[4] = __float2half_rn(0.f);
+          hk[3] = hk[5] = __float2half_rn(VK_UNUSED_C);
+          hk[6] = hk[7] = __float2half_rn(-1.0f);
+          sA[g] = 0.f;
+        }
+        *reinterpret_cast<uint4*>(sBK + 16 * g) = *reinterpret_cast<const uint4*>(hk);
+      }
     }
     for (int t = tid; t < nt; t += blockDim.x) smask[t] = 0ull;
-    __syncthreads();
-    if (tid < VS_N) {
-      // the folded-test operand of query slot tid: (a_h, a_l, a_h, c_h, c_l,
-      // c_h, 1, 1) with a = min(sqrt(2 T) rounded up, A) and c_q = a^2 -
-      // ||q~||_w^2 rounded up (||q~||_w^2 in FP32; its rounding is part of
-      // M'); a slot past the unit's queries gets a = 0, c = -60000 and -1's,
-      // which make y negative for every series
-      __align__(16) __half hk[8];
-      if (tid < cnt) {
-        const int qq = sqid[tid];
-        float Qw = 0.f;
-        for (int j = 0; j < NB; ++j) {
-          const float v = qv[(int64_t)qq * NBq + j];
-          Qw = fmaf(__ldg(vw + j) * v, v, Qw);
-        }
-        const float a = fminf(__fsqrt_ru(__fmul_ru(2.0f, sT[tid])), amax);
-        const float c = __fsub_ru(__fmul_ru(a, a), Qw);
-        sA[tid] = a;
-        split_f16(a, hk[0], hk[1]);
-        hk[2] = hk[0];
-        split_f16(c, hk[3], hk[4]);
-        hk[5] = hk[3];
-        hk[6] = hk[7] = __float2half_rn(1.0f);
-      } else {
-        hk[0] = hk[1] = hk[2] = hk[4] = __float2half_rn(0.f);
-        hk[3] = hk[5] = __float2half_rn(VK_UNUSED_C);
-        hk[6] = hk[7] = __float2half_rn(-1.0f);
-        sA[tid] = 0.f;
-      }
-      *reinterpret_cast<uint4*>(sBK + 16 * tid) = *reinterpret_cast<const uint4*>(hk);
-    }
     fence_proxy_async();  // the operands' generic stores, before the MMAs read them
-    // ---- tile envelope checks (every pair when dumping)
+    // ---- tile envelope checks (every pair when dumping).  The envelopes of
+    // up to 64 tiles are staged by one coalesced pass; then, 16 tiles at a
+    // time, each tile's LW intervals [c(lo) - h(lo), c(hi) + h(hi)] (rounded
+    // outward) are formed once, and a warp checks one tile against 32 query
+    // slots (lane = slot; interval reads are broadcasts, the values are
+    // stored value-major): the bound of env_bound_ch, term for term.
     if (dump) {
+      __syncthreads();
       const unsigned long long all = cnt >= 64 ? ~0ull : ((1ull << cnt) - 1ull);
       for (int t = tid; t < nt; t += blockDim.x) smask[t] = all;
     } else {
-      for (int e = tid; e < nt * cnt; e += blockDim.x) {
-        const int t = e / cnt, g = e - t * cnt;
-        const float a = env_bound_ch<LW, NYQ>(tenv + (t0 + t) * 2 * LW, sq[g], sch);
-        if (a <= sT[g]) atomicOr(&smask[t], 1ull << g);
+      const int npass = (cnt + 31) >> 5;
+      for (int tb0 = 0; tb0 < nt; tb0 += 64) {
+        const int nc = nt - tb0 < 64 ? nt - tb0 : 64;
+        constexpr int EV = 2 * LW / 16;  // 16-byte pieces of one tile's envelope
+        const uint4* src = reinterpret_cast<const uint4*>(tenv + (t0 + tb0) * 2 * LW);
+        for (int e = tid; e < nc * EV; e += blockDim.x) reinterpret_cast<uint4*>(s_env)[e] = src[e];
+        __syncthreads();
+        for (int cb = 0; cb < nc; cb += 16) {
+          const int nk = nc - cb < 16 ? nc - cb : 16;
+          for (int e = tid; e < nk * LW; e += blockDim.x) {
+            const int t = e / LW, j = e - t * LW;
+            const uint8_t* env = s_env + (cb + t) * 2 * LW;
+            const float2 vl = sch[j * MAX_ALPHA + env[j]], vh = sch[j * MAX_ALPHA + env[LW + j]];
+            s_ivl[e] = make_float2(__fsub_rd(vl.x, vl.y), __fadd_ru(vh.x, vh.y));
+          }
+          __syncthreads();
+          for (int w = warp; w < nk * npass; w += VS_WARPS) {
+            const int t = w / npass, g0 = (w - t * npass) << 5, g = g0 + lane;
+            const int gg = g < cnt ? g : 0;
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < LW; ++j) {
+              const float2 iv = s_ivl[t * LW + j];
+              const float qj = sqT[j][gg];
+              const float m = fmaxf(fmaxf(iv.x - qj, qj - iv.y), 0.f);
+              const float mm = (NYQ && j == 0) ? 0.5f * m : m;
+              acc = fmaf(mm, m, acc);
+            }
+            const unsigned live = __ballot_sync(0xFFFFFFFFu, g < cnt && acc <= sT[gg]);
+            if (lane == 0 && live) atomicOr(&smask[tb0 + cb + t], (unsigned long long)live << g0);
+          }
+          __syncthreads();
+        }
       }
       n_checks += (tid == 0) ? (unsigned long long)nt : 0ull;
     }
@@ -624,36 +687,54 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
             const int g = 32 * h32 + j;
             const bool live = (mine >> j) & 1u;
             const unsigned hit = __ballot_sync(0xFFFFFFFFu, live);
-            float dcol[4];
-            tmem_ld1x4(tb + (uint32_t)g, tb + (uint32_t)g, tb + (uint32_t)g, tb + (uint32_t)g, dcol);
+            const float yg = tmem_ld1(tb + (uint32_t)g);  // warp-collective
             // the pair's lower bound in half units, rounded down
-            const float acc_lb = live ? __fmul_rd(folded_lb2(dcol[0], sA[g], kx), 0.5f) : 0.f;
-            const int qs = sslot[g];
+            const float acc_lb = live ? __fmul_rd(folded_lb2(yg, sA[g], kx), 0.5f) : 0.f;
             const int npop = __popc(hit);
-            int base = 0, pbase = 0;
-            if (lane == 0) base = atomicAdd(cand_n + qs, npop);
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            const int over0 = base > cap ? base : cap;
-            const int nover = base + npop - over0;
-            if (lane == 0 && nover > 0) {
-              // the pool counter grows only while the pool has room (it cannot wrap)
-              pbase = *reinterpret_cast<volatile int*>(pool_n) < pool_cap ? atomicAdd(pool_n, nover) : (int)pool_cap;
-              const int64_t room = pool_cap - pbase;
-              const int written = room <= 0 ? 0 : (room < nover ? (int)room : nover);
-              if (written > 0) atomicAdd(qpool_cnt + qs, written);
+            const int rank = __popc(hit & ((1u << lane) - 1u));
+            // into the unit's candidate list (shared-memory atomics only);
+            // a column that does not fit goes straight to the global store
+            int lb0 = 0, rb0 = -1;
+            if (lane == 0) {
+              lb0 = atomicAdd(&s_cn, npop);
+              if (lb0 + npop <= C::SC) rb0 = atomicAdd(&s_qn[g], npop);
+              else atomicMin(&s_clim, lb0);
             }
-            pbase = __shfl_sync(0xFFFFFFFFu, pbase, 0);
-            if (live) {
-              const int slot = base + __popc(hit & ((1u << lane) - 1u));
-              if (slot < cap) {
-                cand_p[(int64_t)qs * cap + slot] = (uint32_t)p;
-                cand_lb[(int64_t)qs * cap + slot] = acc_lb;
-              } else {
-                const int64_t pi = (int64_t)pbase + (slot - over0);
-                if (pi < pool_cap) {
-                  pool_q[pi] = qs;
-                  pool_p[pi] = (uint32_t)p;
-                  pool_lb[pi] = acc_lb;
+            lb0 = __shfl_sync(0xFFFFFFFFu, lb0, 0);
+            rb0 = __shfl_sync(0xFFFFFFFFu, rb0, 0);
+            if (rb0 >= 0) {
+              if (live) {
+                s_cp[lb0 + rank] = (uint32_t)p;
+                s_cl[lb0 + rank] = acc_lb;
+                s_cgr[lb0 + rank] = (uint16_t)((g << 10) | (rb0 + rank));
+              }
+            } else {
+              const int qs = sslot[g];
+              int base = 0, pbase = 0;
+              if (lane == 0) base = atomicAdd(cand_n + qs, npop);
+              base = __shfl_sync(0xFFFFFFFFu, base, 0);
+              const int over0 = base > cap ? base : cap;
+              const int nover = base + npop - over0;
+              if (lane == 0 && nover > 0) {
+                // the pool counter grows only while the pool has room (it cannot wrap)
+                pbase = *reinterpret_cast<volatile int*>(pool_n) < pool_cap ? atomicAdd(pool_n, nover) : (int)pool_cap;
+                const int64_t room = pool_cap - pbase;
+                const int written = room <= 0 ? 0 : (room < nover ? (int)room : nover);
+                if (written > 0) atomicAdd(qpool_cnt + qs, written);
+              }
+              pbase = __shfl_sync(0xFFFFFFFFu, pbase, 0);
+              if (live) {
+                const int slot = base + rank;
+                if (slot < cap) {
+                  cand_p[(int64_t)qs * cap + slot] = (uint32_t)p;
+                  cand_lb[(int64_t)qs * cap + slot] = acc_lb;
+                } else {
+                  const int64_t pi = (int64_t)pbase + (slot - over0);
+                  if (pi < pool_cap) {
+                    pool_q[pi] = qs;
+                    pool_p[pi] = (uint32_t)p;
+                    pool_lb[pi] = acc_lb;
+                  }
                 }
               }
             }
@@ -662,6 +743,47 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
         }
         tc_fence_before();
         mbar_arrive(&tempty[acc]);  // the accumulator is free for the MMA warp
+      }
+      // flush the unit's candidate list: one global reservation per query
+      // (and one pool reservation per query that overflows its slots), then
+      // every entry to its slot; the epilogue warps only (named barrier 1)
+      asm volatile("bar.sync 1, %0;" ::"n"(VS_EPI) : "memory");
+      if (tid < VS_N) {
+        const int cnt_g = s_qn[tid];
+        int base = 0, pbase = 0;
+        if (cnt_g > 0) {
+          const int qs = sslot[tid];
+          base = atomicAdd(cand_n + qs, cnt_g);
+          const int over0 = base > cap ? base : cap;
+          const int nover = base + cnt_g - over0;
+          if (nover > 0) {
+            pbase = *reinterpret_cast<volatile int*>(pool_n) < pool_cap ? atomicAdd(pool_n, nover) : (int)pool_cap;
+            const int64_t room = pool_cap - pbase;
+            const int written = room <= 0 ? 0 : (room < nover ? (int)room : nover);
+            if (written > 0) atomicAdd(qpool_cnt + qs, written);
+          }
+        }
+        s_qbase[tid] = base;
+        s_qpbase[tid] = pbase;
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(VS_EPI) : "memory");
+      // entries below the first reservation that did not fit are all written
+      const int ncl = s_cn < s_clim ? s_cn : s_clim;
+      for (int i = tid; i < ncl; i += VS_EPI) {
+        const int g = s_cgr[i] >> 10, slot = s_qbase[g] + (s_cgr[i] & 1023);
+        const int qs = sslot[g];
+        if (slot < cap) {
+          cand_p[(int64_t)qs * cap + slot] = s_cp[i];
+          cand_lb[(int64_t)qs * cap + slot] = s_cl[i];
+        } else {
+          const int over0 = s_qbase[g] > cap ? s_qbase[g] : cap;
+          const int64_t pi = (int64_t)s_qpbase[g] + (slot - over0);
+          if (pi < pool_cap) {
+            pool_q[pi] = qs;
+            pool_p[pi] = s_cp[i];
+            pool_lb[pi] = s_cl[i];
+          }
+        }
       }
     }
     gi += ntl;
