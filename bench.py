@@ -503,11 +503,12 @@ def run_sofa_multi(a, ws, rank, local):
                    "peak_kind": f"derived from the kernel's own 3 FP32 lane operations per value: {sms} SMs x "
                                 f"128 lanes x {clk / 1e6:.0f} MHz / (3 x {LW})"}
     step_bytes = 0.0
-    for (N, n), s_ in zip(MULTI_SETS, r["stats"]):
+    for (N, n), s_, p_, t_ in zip(MULTI_SETS, r["stats"], r["profs"], modes[chosen]):
         vf, f8, rf = s_.get("value_filtered", 0), s_.get("filtered", 0), s_["refined"]
         value_checked = vf + f8 + rf if vf else 0
         int8_rows = f8 + rf if (vf or f8) else 0
-        step_bytes += (s_["tile_pairs"] * 256 * LW + value_checked * (2 * LW + 8) + int8_rows * n + rf * n * 4)
+        bound = p_["scan_tile_loads"] * 256 * (4 * LW + 16) if t_.get("series_bound") else s_["tile_pairs"] * 256 * LW
+        step_bytes += (bound + value_checked * (2 * LW + 8) + int8_rows * n + rf * n * 4)
     step_bytes /= a.steps
     step_roof = step_bytes / (r["ms"] / 1e3) / 1e9
 
@@ -770,15 +771,16 @@ def run_sofa(a, ws, rank, local):
                 "note": "launch_ms is the dense phase's time per k_dense launch, including the query-side "
                         "helper kernels of the phase"}
     elif tc_scan:
-        # the tensor pipe's share: per tile load 2 halves x NB/16 MMAs of
-        # 128 x 64 x 16, i.e. 2 x 256 x 64 x NB FLOP, against the FP16 rate
-        # (the measured bf16 burst peak; FP16 runs at the BF16 rate)
+        # the tensor pipe's share: per tile load 2 halves x (NB/16 + 1) MMAs
+        # of 128 x 64 x 16 (the codes' K steps and the folded test's), i.e.
+        # 2 x 256 x 64 x (NB + 16) FLOP, against the FP16 rate (the measured
+        # bf16 burst peak; FP16 runs at the BF16 rate)
         try:
             with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
                 bf16 = float(json.load(f)["bf16_tflops"])
         except (OSError, KeyError, ValueError):
             bf16 = 1900.0
-        flops = prof["scan_tile_loads"] * 2.0 * 256 * 64 * NB / launches
+        flops = prof["scan_tile_loads"] * 2.0 * 256 * 64 * (NB + 16) / launches
         alu = {"kernel": "k_vscan", "view": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": bf16,
                "unit": "TFLOP/s", "frac": flops / per_launch_s / 1e12 / bf16,
                "peak_kind": "measured bf16 burst (fp16 = bf16 rate)"}
@@ -797,14 +799,17 @@ def run_sofa(a, ws, rank, local):
                "frac": ach_b / peak_b,
                "peak_kind": f"derived from the kernel's own 3 FP32 lane operations per value: {sms} SMs x 128 "
                             f"lanes x {clk / 1e6:.0f} MHz / (3 x {LW})"}
-    # whole-step algorithmic bytes: SFA words of every bounded series; for
+    # whole-step algorithmic bytes: the series bound's reads (the word
+    # scan: the SFA word of every bounded (query, series) pair, logical; the
+    # tensor-core scan: 256 x (2 NB + 16) bytes per (unit, tile) load); for
     # each candidate reaching a filter, its value codes (2 LW bytes + scale
     # and margin) and / or its int8 row; the fp32 rows refined
     vf, f8, rf = stats.get("value_filtered", 0), stats.get("filtered", 0), stats["refined"]
     value_checked = vf + f8 + rf if vf else 0
     int8_rows = f8 + rf if (vf or f8) else 0
-    step_bytes = ((stats["tile_pairs"] * 256 * LW) + value_checked * (2 * LW + 8) + int8_rows * a.n
-                  + rf * a.n * 4) / a.steps
+    bound_bytes = (prof["scan_tile_loads"] * 256 * (2 * NB + 16) if tc_scan
+                   else stats["tile_pairs"] * 256 * LW)
+    step_bytes = (bound_bytes + value_checked * (2 * LW + 8) + int8_rows * a.n + rf * a.n * 4) / a.steps
     step_roof = step_bytes / (r["ms"] / 1e3) / 1e9
 
     # end to end through the public API with host buffers, in the chosen mode
@@ -913,7 +918,9 @@ def run_sofa(a, ws, rank, local):
             "learned_vs_plain_seed": seed_gain,
             "tunings": {m: (tunings[m] if modes[m][1] else "defaults") for m in modes},
             "step_roofline": {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_roof,
-                              "frac": step_roof / hbm_peak, "peak": hbm_peak},
+                              "frac": step_roof / hbm_peak, "peak": hbm_peak,
+                              "series_bound_bytes": "tensor-core scan: 256 x (2 NB + 16) per (unit, tile) load"
+                              if tc_scan else "word scan: LW per (query, series) pair bounded (logical)"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": r["clocks"],
