@@ -233,16 +233,29 @@ typedef struct {
                            FP16 rounding margin (needs precision >= 1).  Both
                            are lower bounds of the distance: answers do not
                            change                                               */
+  int32_t tile_checks;  /* with series_bound = 1: 0 (default) every tile of a
+                           leaf block that passed the leaf check is bounded on
+                           the tensor cores for every query of its unit; 1 the
+                           tiles are first checked against each query's SFA
+                           symbol envelope (Eq. 1 with Eq. dist_i), and a tile
+                           no query passes is not loaded.  Both are exact; the
+                           per-series bound is tighter than a tile envelope, so
+                           the checks pay only where whole tiles fail them.
+                           Ignored with series_bound = 0 (the word scan always
+                           checks its tiles)                                    */
 } sofa_tuning;
 int sofa_set_tuning(sofa_handle h, const sofa_tuning* t);
 
 /* Autotuner: times candidate tunings (unit size, seed window and count, the
- * refinement filter when the index has its int8 copy) on Q sample queries
- * (device memory) at this k, keeps the fastest and applies it to the handle.
- * Every candidate returns the same exact answers.  cache_path (may be NULL):
- * a text file of earlier choices, one line per (device, N, n, l, k bucket,
- * Q bucket, filter, seed mode) key; a hit applies the stored choice without
- * timing, a miss appends the new one.  chosen (may be NULL) receives it. */
+ * refinement filter when the index has its int8 copy, the series bound when
+ * it has its value codes) on Q sample queries (device memory) at this k,
+ * keeps the fastest and, when that uses the tensor-core bound, times it once
+ * more with tile_checks flipped; applies the winner to the handle.  Every
+ * candidate returns the same exact answers.  cache_path (may be NULL): a
+ * text file of earlier choices, one line per (device, N, n, l, k bucket,
+ * Q bucket, filter, tensor-core bound available, seed mode) key; a hit
+ * applies the stored choice without timing, a miss appends the new one.
+ * chosen (may be NULL) receives it. */
 int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int32_t k, const char* cache_path,
                   sofa_tuning* chosen, sofa_stream stream);
 

@@ -446,6 +446,7 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   if (t->series_bound < 0 || t->series_bound > 1) return fail(SOFA_ERR_INVALID_ARG, "series_bound must be 0 or 1");
   if (t->series_bound == 1 && !vscan_supported(h))
     return fail(SOFA_ERR_INVALID_ARG, "series_bound 1 needs an index built with precision >= 1");
+  if (t->tile_checks < 0 || t->tile_checks > 1) return fail(SOFA_ERR_INVALID_ARG, "tile_checks must be 0 or 1");
   h->group = t->group ? t->group : 64;
   h->cand_cap = t->cand_cap ? t->cand_cap : 65536;
   h->seed_count = t->seed_count ? t->seed_count : 128;
@@ -458,6 +459,7 @@ int sofa_set_tuning(sofa_handle h, const sofa_tuning* t) {
   h->dense_mode = t->dense;
   h->approximate = t->approximate;
   h->series_bound = t->series_bound;
+  h->tile_checks = t->tile_checks;
   return 0;
 }
 

@@ -1933,7 +1933,7 @@ static int graph_batch(Index* ix, const float* qp, int64_t qb, int k, int64_t* i
   }
   const int64_t key[16] = {qb, k, ix->bound_precision, ix->refine_filter, ix->seed_mode, ix->group, ix->cand_cap,
                            ix->seed_count, ix->seed_window, ix->pool_cap, ix->LW, ix->nyq_first, ix->approximate,
-                           ix->dense_mode, ix->cand_budget, ix->series_bound};
+                           ix->dense_mode, ix->cand_budget, ix->series_bound | (ix->tile_checks << 1)};
   Index::GraphEntry* e = nullptr;
   for (auto& g : ix->graphs)
     if (std::equal(key, key + 16, g.key)) e = &g;

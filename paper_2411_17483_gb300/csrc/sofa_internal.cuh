@@ -183,6 +183,7 @@ struct Index {
   int64_t cand_budget = (int64_t)1 << 30;  // candidate-region entries of one overflow pass
   int approximate = 0;         // 1: answers from the seed alone
   int dense_mode = 0;          // 0: dense contraction when the leaf bound prunes little, 1: never, 2: always
+  int tile_checks = 0;         // series_bound 1: per-tile envelope checks before the tensor-core bound
   int series_bound = 0;        // 0: SFA word bound (k_scan); 1: value codes on the tensor cores (k_vscan)
   struct GraphEntry {
     int64_t key[16];

@@ -44,8 +44,9 @@ static bool cache_lookup(const char* path, const std::string& key, const sofa_tu
     if (ls >> k >> c.group >> c.cand_cap >> c.seed_count >> c.seed_window >> c.bound_precision >> pool >>
         c.refine_filter) {
       c.pool_cap = pool;
-      int sb = 0;
+      int sb = 0, tc = 0;
       if (ls >> sb) c.series_bound = sb;  // absent in lines written before this knob
+      if (ls >> tc) c.tile_checks = tc;   // likewise
       if (k == key) {
         *t = c;
         return true;
@@ -60,7 +61,7 @@ static void cache_store(const char* path, const std::string& key, const sofa_tun
   std::ofstream out(path, std::ios::app);
   out << key << " " << c.group << " " << c.cand_cap << " " << c.seed_count << " " << c.seed_window << " "
       << c.bound_precision << " " << (long long)c.pool_cap << " " << c.refine_filter << " " << c.series_bound
-      << "\n";
+      << " " << c.tile_checks << "\n";
 }
 
 static void apply(Index* ix, const sofa_tuning& t) {
@@ -76,6 +77,7 @@ static void apply(Index* ix, const sofa_tuning& t) {
   ix->dense_mode = t.dense;
   ix->approximate = t.approximate;
   ix->series_bound = t.series_bound == 1 && vscan_supported(ix) ? 1 : 0;
+  ix->tile_checks = t.tile_checks;
 }
 
 }  // namespace sofa
@@ -105,6 +107,7 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
   cur.dense = ix->dense_mode;
   cur.approximate = ix->approximate;
   cur.series_bound = ix->series_bound;
+  cur.tile_checks = ix->tile_checks;
   sofa_tuning best = cur;
   if (cache_lookup(cache_path, key, cur, &best)) {
     apply(ix, best);
@@ -130,6 +133,7 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
             t.refine_filter = f;
             t.bound_precision = 0;
             t.series_bound = sb;
+            t.tile_checks = 0;
             cands.push_back(t);
           }
   DevBuf outi, outd;
@@ -140,23 +144,40 @@ extern "C" int sofa_autotune(sofa_handle h, const float* queries, int64_t Q, int
   SOFA_CUDA(cudaEventCreate(&e1));
   float best_ms = 1e30f;
   int rc = 0;
-  for (const sofa_tuning& t : cands) {
+  // one warm-up and the better of two timed runs of a candidate
+  auto time_one = [&](const sofa_tuning& t, float* ms_out) {
     apply(ix, t);
-    rc = run_query(ix, queries, Q, k, outi.as<int64_t>(), outd.as<float>(), st);  // warm-up
-    if (rc) break;
+    int r = run_query(ix, queries, Q, k, outi.as<int64_t>(), outd.as<float>(), st);  // warm-up
     float ms_min = 1e30f;
-    for (int rep = 0; rep < 2 && !rc; ++rep) {
+    for (int rep = 0; rep < 2 && !r; ++rep) {
       cudaEventRecord(e0, st);
-      rc = run_query(ix, queries, Q, k, outi.as<int64_t>(), outd.as<float>(), st);
+      r = run_query(ix, queries, Q, k, outi.as<int64_t>(), outd.as<float>(), st);
       cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(SOFA_ERR_CUDA, "autotune timing failed");
+      if (cudaEventSynchronize(e1) != cudaSuccess) r = fail(SOFA_ERR_CUDA, "autotune timing failed");
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       ms_min = std::min(ms_min, ms);
     }
-    if (rc) break;
-    if (ms_min < best_ms) {
-      best_ms = ms_min;
+    *ms_out = ms_min;
+    return r;
+  };
+  for (const sofa_tuning& t : cands) {
+    float ms = 0;
+    if ((rc = time_one(t, &ms))) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  // second stage: the winner with the tensor-core bound, with and without
+  // the per-tile envelope checks
+  if (!rc && best.series_bound == 1) {
+    sofa_tuning t = best;
+    t.tile_checks = 1 - best.tile_checks;
+    float ms = 0;
+    rc = time_one(t, &ms);
+    if (!rc && ms < best_ms) {
+      best_ms = ms;
       best = t;
     }
   }

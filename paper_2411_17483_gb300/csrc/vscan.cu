@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
             int n_leaf_tiles, int NBq, const int4* __restrict__ units, const int* __restrict__ n_units_ptr,
             const int* __restrict__ leaf_q, const float* __restrict__ qv, const float* __restrict__ thr,
             const uint8_t* __restrict__ tenv, const float2* __restrict__ ch, const uint4* __restrict__ VK,
-            const float* __restrict__ vw, float amax, int cap, const int* __restrict__ qslot,
+            const float* __restrict__ vw, float amax, int tile_checks, int cap, const int* __restrict__ qslot,
             uint32_t* __restrict__ cand_p, float* __restrict__ cand_lb, int* __restrict__ cand_n, int64_t pool_cap,
             int* __restrict__ pool_n, int* __restrict__ pool_q, uint32_t* __restrict__ pool_p,
             float* __restrict__ pool_lb, int* __restrict__ qpool_cnt, float* __restrict__ dump, int64_t dumpQ,
@@ -483,13 +483,14 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
     }
     for (int t = tid; t < nt; t += blockDim.x) smask[t] = 0ull;
     fence_proxy_async();  // the operands' generic stores, before the MMAs read them
-    // ---- tile envelope checks (every pair when dumping).  The envelopes of
+    // ---- tile envelope checks (with tile_checks; otherwise, and when
+    // dumping, every tile is live for every query of the unit).  The envelopes of
     // up to 64 tiles are staged by one coalesced pass; then, 16 tiles at a
     // time, each tile's LW intervals [c(lo) - h(lo), c(hi) + h(hi)] (rounded
     // outward) are formed once, and a warp checks one tile against 32 query
     // slots (lane = slot; interval reads are broadcasts, the values are
     // stored value-major): the bound of env_bound_ch, term for term.
-    if (dump) {
+    if (dump || !tile_checks) {
       __syncthreads();
       const unsigned long long all = cnt >= 64 ? ~0ull : ((1ull << cnt) - 1ull);
       for (int t = tid; t < nt; t += blockDim.x) smask[t] = all;
@@ -855,7 +856,8 @@ static int launch_vscan_t(Index* ix, const VscanArgs& A, cudaStream_t st) {
   per_sm = std::max(1, std::min(per_sm, 512 / VS_TMEM));
   const int grid = sms * per_sm;
   fn<<<grid, VS_THREADS, smem, st>>>(tm, tk, ix->N, ix->T, ix->leaf_tiles, ix->NB, A.units, A.n_units, A.leaf_q,
-                                     A.qv, A.thr, ix->tenv, ix->ch, ix->VK, ix->vw, ix->tc_amax, A.cap, A.qslot,
+                                     A.qv, A.thr, ix->tenv, ix->ch, ix->VK, ix->vw, ix->tc_amax, ix->tile_checks,
+                                     A.cap, A.qslot,
                                      A.cand_p, A.cand_lb,
                                      A.cand_n, A.pool_cap, A.pool_n, A.pool_q, A.pool_p, A.pool_lb, A.qpool_cnt,
                                      A.dump, A.dumpQ, ix->perm, A.counters, A.status);

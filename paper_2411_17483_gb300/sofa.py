@@ -47,7 +47,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int32), ("cand_cap", ctypes.c_int32), ("seed_count", ctypes.c_int32),
                 ("seed_window", ctypes.c_int32), ("bound_precision", ctypes.c_int32), ("pool_cap", ctypes.c_int64),
                 ("refine_filter", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("cand_budget", ctypes.c_int64),
-                ("dense", ctypes.c_int32), ("approximate", ctypes.c_int32), ("series_bound", ctypes.c_int32)]
+                ("dense", ctypes.c_int32), ("approximate", ctypes.c_int32), ("series_bound", ctypes.c_int32),
+                ("tile_checks", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -243,9 +244,10 @@ class Index:
         return ids, d2, cnt
 
     def set_tuning(self, group=0, cand_cap=0, seed_count=0, seed_window=0, bound_precision=0, pool_cap=0,
-                   refine_filter=0, use_graph=0, cand_budget=0, dense=0, approximate=0, series_bound=0):
+                   refine_filter=0, use_graph=0, cand_budget=0, dense=0, approximate=0, series_bound=0,
+                   tile_checks=0):
         t = Tuning(group, cand_cap, seed_count, seed_window, bound_precision, pool_cap, refine_filter, use_graph,
-                   cand_budget, dense, approximate, series_bound)
+                   cand_budget, dense, approximate, series_bound, tile_checks)
         _check(load().sofa_set_tuning(self.h, ctypes.byref(t)))
 
     def autotune(self, q: torch.Tensor, k: int = 1, cache_path: str | None = None, stream=None) -> dict:

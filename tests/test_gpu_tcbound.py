@@ -109,7 +109,8 @@ def test_knn_with_tensor_core_bound_matches_oracle(sofa, N, n, l, k, Q, gen):
     oi, od = orc.knn(z, zq, k)
     for t in (dict(series_bound=1, dense=1), dict(series_bound=1, dense=1, refine_filter=2),
               dict(series_bound=1, dense=1, refine_filter=1, cand_cap=3, pool_cap=7, group=5),
-              dict(series_bound=1, dense=1, group=64, cand_cap=1)):
+              dict(series_bound=1, dense=1, group=64, cand_cap=1),
+              dict(series_bound=1, dense=1, tile_checks=1), dict(series_bound=1, dense=1, tile_checks=1, group=7)):
         ix.set_tuning(**t)
         gi, gd = ix.query(q, k)
         torch.cuda.synchronize()
@@ -125,7 +126,7 @@ def test_tensor_core_bound_prunes_more_than_the_word_bound(sofa):
     ix = sofa.Index(x, 16, 256, precision=1)
     res = {}
     for sb in (0, 1):
-        ix.set_tuning(series_bound=sb, dense=1)
+        ix.set_tuning(series_bound=sb, dense=1, tile_checks=1)
         ix.stats(reset=True)
         gi, gd = ix.query(q, 1)
         torch.cuda.synchronize()
@@ -175,4 +176,34 @@ def test_series_bound_needs_the_value_codes(sofa):
     assert e.value.code == -1
     with pytest.raises(sofa.SofaError):
         sofa.value_bounds(ix, x[:2])
+    ix.close()
+
+
+def test_tile_checks_keep_answers_and_only_skip_tiles(sofa):
+    """With the tensor-core bound the per-tile envelope checks are optional:
+    on or off, the answers equal the oracle's; with them on, no more tiles
+    are loaded than with them off, and every tile of a routed leaf block is
+    loaded when they are off."""
+    N, n = 60000, 128
+    x = datagen.random_walks(N, n, seed=641, device=DEV)
+    q = datagen.half_perturbed_queries(x, 96, seed=642)
+    ix = sofa.Index(x, 16, 256, precision=1)
+    z, _, _ = orc.znorm(x.cpu().numpy())
+    zq, _, _ = orc.znorm(q.cpu().numpy())
+    oi, od = orc.knn(z, zq, 2)
+    loads = {}
+    for tc in (0, 1):
+        ix.set_tuning(series_bound=1, dense=1, refine_filter=2, tile_checks=tc)
+        ix.stats(reset=True)
+        ix.profile(reset=True)
+        ix.set_profiling(True)
+        gi, gd = ix.query(q, 2)
+        torch.cuda.synchronize()
+        assert ix.status() == 0
+        assert_knn_equal(gi, gd, oi, od)
+        loads[tc] = ix.profile(reset=True)["scan_tile_loads"]
+        ix.set_profiling(False)
+    assert 0 < loads[1] <= loads[0]
+    with pytest.raises(sofa.SofaError):
+        ix.set_tuning(series_bound=1, tile_checks=2)
     ix.close()
