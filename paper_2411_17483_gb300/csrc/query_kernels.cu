@@ -200,11 +200,67 @@ __device__ inline bool emit_list(const unsigned long long* key, int len, const Q
 }
 
 // ------------------------------------------------------------------------
-// Seed (plain approximate search, Sec. IV "Exact Similarity Search": the leaf
-// with the smallest lower bound gives the first best-so-far).  One CTA per
-// query: (1) leaf bounds of every leaf block -> llb; (2) best leaf, then its
-// best tile; (3) the tile's series bounds, the seed_count smallest refined in
-// FP32; (4) kept list and prune threshold.
+// Leaf bounds of every (query, leaf block) pair -> llb, the routing input
+// (Eq. 1 with Eq. dist_i against each leaf block's symbol envelope): the
+// bound of env_bound, term for term.  A CTA takes 256 leaf blocks and 64
+// queries.  Each leaf block's LW intervals [edge(lo).lo, edge(hi).hi] are
+// formed once; then a warp bounds its 32 leaf blocks (lanes) against one
+// query at a time: the query's values are broadcast, the intervals are read
+// value-major (no bank conflicts), the stores are coalesced.
+constexpr int LB_LEAVES = 256, LB_QUERIES = 64;
+template <int LW, bool NYQ>
+__global__ void __launch_bounds__(256) k_leaf_bounds(int64_t Q, int64_t L, int NBq, const float* __restrict__ qv,
+                                                     const uint8_t* __restrict__ lenv,
+                                                     const float2* __restrict__ edge, float* __restrict__ llb) {
+  extern __shared__ float2 s_lint[];  // [LW][LB_LEAVES]
+  __shared__ float s_qv[LB_QUERIES][LW];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t b0 = (int64_t)blockIdx.x * LB_LEAVES, q0 = (int64_t)blockIdx.y * LB_QUERIES;
+  const int nb = (int)(L - b0 < LB_LEAVES ? L - b0 : LB_LEAVES);
+  const int nq = (int)(Q - q0 < LB_QUERIES ? Q - q0 : LB_QUERIES);
+  if (tid < nb) {
+    const uint32_t* e32 = reinterpret_cast<const uint32_t*>(lenv + (b0 + tid) * 2 * LW);
+#pragma unroll
+    for (int w = 0; w < LW / 4; ++w) {
+      const uint32_t lo = e32[w], hi = e32[LW / 4 + w];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int j = 4 * w + b;
+        s_lint[j * LB_LEAVES + tid] = make_float2(edge[j * MAX_ALPHA + ((lo >> (8 * b)) & 0xFFu)].x,
+                                                  edge[j * MAX_ALPHA + ((hi >> (8 * b)) & 0xFFu)].y);
+      }
+    }
+  }
+  for (int e = tid; e < nq * LW; e += blockDim.x) {
+    const int g = e / LW, j = e - g * LW;
+    s_qv[g][j] = qv[(q0 + g) * NBq + j];
+  }
+  __syncthreads();
+  const int leaf = warp * 32 + lane;
+  if (warp * 32 >= nb) return;  // no barrier follows
+  const int lf = leaf < nb ? leaf : 0;
+  for (int g = 0; g < nq; ++g) {
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < LW; ++j) {
+      const float2 iv = s_lint[j * LB_LEAVES + lf];
+      const float qj = s_qv[g][j];
+      const float m = fmaxf(fmaxf(iv.x - qj, qj - iv.y), 0.f);
+      const float mm = (NYQ && j == 0) ? 0.5f * m : m;
+      acc = fmaf(mm, m, acc);
+    }
+    if (leaf < nb) llb[(q0 + g) * L + b0 + leaf] = acc;
+  }
+}
+
+// ------------------------------------------------------------------------
+// Seed (plain approximate search, Sec. IV "Exact Similarity Search": the
+// series nearest the query's own word in the key order, and the proposal
+// network's blocks, give the first best-so-far).  One CTA per query (the
+// leaf bounds, the routing input, come from k_leaf_bounds): (2) the query's
+// key and its insertion point in each key-sorted run; (3) the key window's
+// series bounds, the seed_count smallest refined in FP32; (4) kept list and
+// prune threshold.
 template <int LW, bool NYQ>
 __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __restrict__ qv,
                                               const float* __restrict__ zq, const uint8_t* __restrict__ lenv,
@@ -228,8 +284,6 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
   for (int t = tid; t < P.n; t += blockDim.x) szq[t] = zq[q * P.n + t];
   __syncthreads();
 
-  // (1) leaf bounds of every leaf block (routing input)
-  for (int64_t b = tid; b < P.L; b += blockDim.x) llb[q * P.L + b] = env_bound<LW, NYQ>(lenv + b * 2 * LW, sq, edge);
 
   // (2) approximate search: the query's own SFA word and layout key, and the
   // key-sorted position where it would be inserted (the flat layout's analogue
@@ -1634,7 +1688,13 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     ix->prof.end(st);
     topm = mlp_topm(ix, &top_m, &block);
   }
-  ix->prof.begin(1, st);
+  ix->prof.begin(1, st, 2);
+  {
+    const size_t lsm = (size_t)LW * LB_LEAVES * sizeof(float2);
+    SOFA_CUDA(cudaFuncSetAttribute(k_leaf_bounds<LW, NYQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+    const dim3 lg((unsigned)ceil_div(L, LB_LEAVES), (unsigned)ceil_div(Q, LB_QUERIES));
+    k_leaf_bounds<LW, NYQ><<<lg, 256, lsm, st>>>(Q, L, NB, qv, ix->lenv, ix->edge, llb);
+  }
   k_seed<LW, NYQ><<<(unsigned)Q, 256, nsm, st>>>(P, qv, zq, ix->lenv, ix->tenv, ix->words, ix->Z, ix->edge, ix->ch,
                                                   ix->beta, ix->alpha, ix->l, ix->keys, ix->keyorder, ix->keybits,
                                                   llb, s.list_d.as<float>(), s.list_p.as<uint32_t>(),
