@@ -263,13 +263,13 @@ __global__ void __launch_bounds__(256) k_leaf_bounds(int64_t Q, int64_t L, int N
 // prune threshold.
 template <int LW, bool NYQ>
 __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __restrict__ qv,
-                                              const float* __restrict__ zq, const uint8_t* __restrict__ lenv,
+                                              const float* __restrict__ zq,
                                               const uint8_t* __restrict__ tenv, const uint8_t* __restrict__ words,
                                               const float* __restrict__ Z, const float2* __restrict__ edge,
                                               const float2* __restrict__ ch, const float* __restrict__ beta,
                                               int alpha, int l, const uint64_t* __restrict__ keys,
                                               const uint8_t* __restrict__ keyorder, int keybits,
-                                              float* __restrict__ llb, float* __restrict__ list_d,
+                                              float* __restrict__ list_d,
                                               uint32_t* __restrict__ list_p, int* __restrict__ list_n,
                                               float* __restrict__ thr, int* __restrict__ status,
                                               unsigned long long* __restrict__ counters,
@@ -1695,9 +1695,9 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
     const dim3 lg((unsigned)ceil_div(L, LB_LEAVES), (unsigned)ceil_div(Q, LB_QUERIES));
     k_leaf_bounds<LW, NYQ><<<lg, 256, lsm, st>>>(Q, L, NB, qv, ix->lenv, ix->edge, llb);
   }
-  k_seed<LW, NYQ><<<(unsigned)Q, 256, nsm, st>>>(P, qv, zq, ix->lenv, ix->tenv, ix->words, ix->Z, ix->edge, ix->ch,
+  k_seed<LW, NYQ><<<(unsigned)Q, 256, nsm, st>>>(P, qv, zq, ix->tenv, ix->words, ix->Z, ix->edge, ix->ch,
                                                   ix->beta, ix->alpha, ix->l, ix->keys, ix->keyorder, ix->keybits,
-                                                  llb, s.list_d.as<float>(), s.list_p.as<uint32_t>(),
+                                                  s.list_d.as<float>(), s.list_p.as<uint32_t>(),
                                                   s.list_n.as<int>(), thr, status, counters, topm, top_m, block);
   ix->prof.end(st);
   SOFA_CUDA(cudaGetLastError());
