@@ -165,6 +165,66 @@ __device__ inline void block_bitonic(unsigned long long* key, int len) {
   __syncthreads();
 }
 
+// The kk smallest of key[0, len) in ascending order in key[0, kp), kp = kk
+// rounded up to a power of two; returns the number of leading entries it
+// sorted (kp, or len when it sorted them all).  len is a power of two.  Each
+// warp sorts its len / 8 keys (warp-synchronous bitonic sort), then three
+// tournament levels keep the kp smallest of two sorted runs: with A and B
+// ascending, C_i = min(A_i, B_{kp-1-i}) rises then falls and holds exactly
+// the kp smallest of A and B, so a bitonic merge sorts it.  A run shorter
+// than kp falls back to the full block sort.  All threads of the block call
+// it with the keys in place; the rest of key[] is left unordered.
+__device__ int block_topk(unsigned long long* key, int len, int kk) {
+  int kp = 1;
+  while (kp < kk) kp <<= 1;
+  const int chunk = len >> 3;
+  if (blockDim.x != 256 || len < 256 || chunk < kp) {
+    block_bitonic(key, len);
+    return len;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  unsigned long long* run = key + warp * chunk;
+  for (int size = 2; size <= chunk; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncwarp();
+      for (int i = lane; i < (chunk >> 1); i += 32) {
+        const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const unsigned long long a = run[lo], b = run[hi];
+        if ((a > b) == up) {
+          run[lo] = b;
+          run[hi] = a;
+        }
+      }
+    }
+  for (int step = 1; step < 8; step <<= 1) {
+    const int npair = 4 / step;
+    __syncthreads();
+    for (int e = threadIdx.x; e < npair * kp; e += blockDim.x) {
+      const int pr = e / kp, i = e - pr * kp;
+      unsigned long long* A = key + (2 * pr * step) * chunk;
+      const unsigned long long b = key[(2 * pr * step + step) * chunk + kp - 1 - i];
+      if (b < A[i]) A[i] = b;
+    }
+    for (int stride = kp >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < npair * (kp >> 1); e += blockDim.x) {
+        const int pr = e / (kp >> 1), i = e - pr * (kp >> 1);
+        unsigned long long* A = key + (2 * pr * step) * chunk;
+        const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+        const unsigned long long a = A[lo], b = A[hi];
+        if (a > b) {
+          A[lo] = b;
+          A[hi] = a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return kp;
+}
+
 __device__ __forceinline__ unsigned long long pack_key(float v, uint32_t p) {
   return ((unsigned long long)__float_as_uint(v) << 32) | p;  // v >= 0: bit order = value order
 }
@@ -371,10 +431,11 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
     load_word_bounds<LW>(words, p, valid, ch, c, h);
     skey[i] = valid ? pack_key(word_bound<LW, NYQ>(c, h, sq), (uint32_t)p) : ~0ull;
   }
-  block_bitonic(skey, P.seed_window);
   const int Kq = kq(P, q);
   int cnt = P.seed_count > Kq ? P.seed_count : Kq;
   if (cnt > W) cnt = (int)W;
+  // only the window's cnt smallest bounds are used below
+  block_topk(skey, P.seed_window, cnt);
   // learned seeding: every series of the proposal network's top-m blocks whose
   // bound beats the window's cnt-th joins the candidates (up to LEARN_CAP)
   __shared__ int s_nl2;
@@ -436,16 +497,19 @@ __global__ void __launch_bounds__(256) k_seed(QueryParams P, const float* __rest
   }
   __syncthreads();
   int len = cnt + (s_nl2 < LEARN_CAP ? s_nl2 : LEARN_CAP);
+  int sorted_n = len;  // the leading entries in ascending order
   if (len > cnt) {
     int pw2 = 1;
     while (pw2 < len) pw2 <<= 1;
     for (int i = len + tid; i < pw2; i += blockDim.x) skey[i] = ~0ull;
-    block_bitonic(skey, pw2);
+    // the cnt smallest, with room for repeats of window entries
+    const int sn = block_topk(skey, pw2, 2 * cnt < pw2 ? 2 * cnt : pw2);
+    sorted_n = sn < len ? sn : len;
   }
   __shared__ int s_avail;
   if (tid == 0) {  // a learned block may overlap the key window: drop repeats
     int u = 0;
-    for (int i = 0; i < len && u < cnt; ++i) {
+    for (int i = 0; i < sorted_n && u < cnt; ++i) {
       if (skey[i] == ~0ull) break;
       if (u == 0 || skey[i] != skey[u - 1]) skey[u++] = skey[i];
     }
