@@ -1501,10 +1501,13 @@ __global__ void __launch_bounds__(128) k_final(QueryParams P, const float* __res
   }
   sd[tid] = d;
   sid[tid] = id;
-  for (int size = 2; size <= 128; size <<= 1) {
+  // sort the list's slots only (the next power of two; the rest hold +inf)
+  int pw = 2;
+  while (pw < nl) pw <<= 1;
+  for (int size = 2; size <= pw; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       __syncthreads();
-      if (tid < 64) {
+      if (tid < (pw >> 1)) {
         int lo = 2 * tid - (tid & (stride - 1));
         int hi = lo + stride;
         bool up = ((lo & size) == 0);
