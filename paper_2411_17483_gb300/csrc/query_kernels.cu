@@ -894,7 +894,8 @@ __global__ void __launch_bounds__(256) k_scan(QueryParams P, const int4* __restr
 // the scan one CTA plans the refinement: per slot, r = min(count, cap) region
 // entries plus pool_cnt pool entries, cut into chunks of RSORT; exclusive
 // scans give each slot its pool segment and its first chunk, and the chunk
-// total goes to the device (the refinement is persistent and reads it).
+// total goes to the device (the refinement is persistent and reads it), and
+// the word after it, the refinement's chunk cursor, is zeroed.
 constexpr int RSORT = 4096;
 constexpr uint16_t VDROP = 0xFFFFu;  // ordered slot of a candidate the value codes dropped (RSORT <= 0xFFFF)
 __global__ void __launch_bounds__(1024) k_chunk_plan(int64_t slots, int cap, const int* __restrict__ cand_n,
@@ -930,7 +931,10 @@ __global__ void __launch_bounds__(1024) k_chunk_plan(int64_t slots, int cap, con
     rp += qpool_cnt[q];
     rc += (r + qpool_cnt[q] + RSORT - 1) / RSORT;
   }
-  if (tid == 1023) *n_chunks = (int)s2[1023];
+  if (tid == 1023) {
+    n_chunks[0] = (int)s2[1023];
+    n_chunks[1] = 0;
+  }
 }
 
 // Counting-sort scatter of the pool into per-slot segments (grid-stride).
@@ -996,7 +1000,7 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
                                                 const float* __restrict__ e8, float one_minus_g,
                                                 const float* __restrict__ qv, const int8_t* __restrict__ VC,
                                                 const float2* __restrict__ vsr, const float* __restrict__ vw,
-                                                float one_minus_gv,
+                                                float one_minus_gv, int* __restrict__ next_chunk,
                                                 unsigned long long* __restrict__ counters, int* __restrict__ status) {
   extern __shared__ float4 rsm[];
   float* szq = reinterpret_cast<float*>(rsm);  // n
@@ -1006,6 +1010,7 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
   __shared__ float acc_d[RROUND];
   __shared__ uint32_t acc_p[RROUND];
   __shared__ int s_nacc, s_nl, s_lost, s_nsurv, s_stop0;  // s_stop0: thread 0 only
+  __shared__ int s_ch;
   __shared__ float s_lim, s_T0;
   __shared__ uint32_t surv[FILTER ? 256 : 1];
   __shared__ uint32_t s1[FILTER == 2 ? 256 : 1];      // survivors of the value-code bound
@@ -1018,8 +1023,14 @@ __global__ void __launch_bounds__(256, FILTER ? 4 : 5) k_refine(QueryParams P, c
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned long long refined = 0, filtered = 0, vfiltered = 0;
   const int n_chunks = *n_chunks_ptr;
-  for (int ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+  // chunks differ widely in work (early stop, pool share), so each CTA takes
+  // its next chunk from a cursor instead of a fixed stride
+  for (;;) {
   __syncthreads();
+  if (tid == 0) s_ch = atomicAdd(next_chunk, 1);
+  __syncthreads();
+  const int ch = s_ch;
+  if (ch >= n_chunks) break;
   const int slot_q = chunk_q[ch];
   const int c = ch - choff[slot_q];
   const int64_t q = qof ? qof[slot_q] : slot_q;
@@ -1819,7 +1830,7 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
   TRYQ(s.pool_sp.ensure((size_t)pool_cap * sizeof(uint32_t)));
   TRYQ(s.pool_slb.ensure((size_t)pool_cap * sizeof(float)));
   int* pool_n = status + 3;  // pool appends (stops growing once the pool is full)
-  int* n_chunks = status + 4;
+  int* n_chunks = status + 4;  // and status + 5: the refinement's chunk cursor
   // persistent refinement grid: resident CTAs of the instantiation that runs
   // (with the value-code stage the static and dynamic shared memory may pass
   // 48 KB, so the dynamic part is declared)
@@ -1973,8 +1984,8 @@ static int query_batch(Index* ix, const float* qdev, int64_t Q, int k, int64_t* 
                                              s.qpool_cnt.as<int>(), s.qpool_off.as<int>(), s.pool_sp.as<uint32_t>(),
                                              s.pool_slb.as<float>(), thr, s.chunk_d.as<float>(),
                                              s.chunk_p.as<uint32_t>(), s.chunk_n.as<int>(), ix->Z8, ix->s8, ix->e8,
-                                             one_minus_g, qv, ix->VC, ix->vsr, ix->vw, one_minus_gv, counters,
-                                             status);
+                                             one_minus_g, qv, ix->VC, ix->vsr, ix->vw, one_minus_gv,
+                                             n_chunks + 1, counters, status);
     SOFA_CUDA(cudaGetLastError());
     k_merge<<<(unsigned)Q, 256, 0, st>>>(P, qsel, qslot, s.cand_n.as<int>(), s.qpool_cnt.as<int>(), s.choff.as<int>(),
                                          s.chunk_d.as<float>(), s.chunk_p.as<uint32_t>(), s.chunk_n.as<int>(),
