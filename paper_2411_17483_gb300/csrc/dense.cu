@@ -251,15 +251,20 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
     for (int i = 0; i < KD; ++i) top[i] = INFINITY;
     unsigned long long emitted = 0;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    float xr[DN / 32];  // ||x||^2 of the next tile, prefetched a tile ahead
+    // ||x||^2 of the next tile, prefetched a tile ahead.  The addresses are
+    // clamped and the +inf past N is applied where the values are used, so
+    // nothing waits for the loads before then.
+    float xr[DN / 32];
+    uint32_t xok = 0u;  // bit j: xr[j] is a series of the index
 #pragma unroll
     for (int j = 0; j < DN / 32; ++j) {
       const int64_t sx = t_begin * DN + lane + 32 * j;
-      xr[j] = sx < D.N ? __ldg(xn + sx) : INFINITY;
+      xr[j] = __ldg(xn + (sx < D.N ? sx : (int64_t)0));
+      xok |= (sx < D.N ? 1u : 0u) << j;
     }
     for (int64_t ti = 0; ti < ntiles; ++ti) {
       const int acc = (int)(ti & 1);
-      const float Tg = qa ? vthr[q] : -1.f;  // in flight during the wait below
+      const float Tg = vthr[qa ? q : 0];  // in flight during the wait below (used by active lanes only)
       // warp-uniform: the TMEM loads below are warp-collective
       if (!__all_sync(0xFFFFFFFFu, mbar_wait(&tfull[acc], (uint32_t)((ti / DACC) & 1)))) {
         *vfail = 1;
@@ -269,13 +274,15 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_dense(const __grid_constant__ C
       const int64_t s0 = (t_begin + ti) * DN;
       __syncwarp();
 #pragma unroll
-      for (int j = 0; j < DN / 32; ++j) xs[lane + 32 * j] = xr[j];
+      for (int j = 0; j < DN / 32; ++j) xs[lane + 32 * j] = ((xok >> j) & 1u) ? xr[j] : INFINITY;
       __syncwarp();
       if (ti + 1 < ntiles) {
+        xok = 0u;
 #pragma unroll
         for (int j = 0; j < DN / 32; ++j) {
           const int64_t sx = s0 + DN + lane + 32 * j;
-          xr[j] = sx < D.N ? __ldg(xn + sx) : INFINITY;
+          xr[j] = __ldg(xn + (sx < D.N ? sx : (int64_t)0));
+          xok |= (sx < D.N ? 1u : 0u) << j;
         }
       }
       if (qa) T = fminf(T, Tg);

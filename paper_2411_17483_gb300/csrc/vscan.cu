@@ -615,8 +615,11 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
         const int64_t p = (t0 + t) * TILE + tid;
         const bool valid = p < N;
         // the series' folded constants (for the bounds of its survivors; the
-        // tile's TMA copy brought the line into L2), loaded before the wait
-        const uint4 kx = valid ? __ldg(VK + p) : make_uint4(0, 0, 0, 0);
+        // tile's TMA copy brought the line into L2), loaded before the wait.
+        // The address is clamped rather than the value selected, so nothing
+        // waits for the load before a survivor needs it (a lane past N is
+        // never a survivor).
+        const uint4 kx = __ldg(VK + (valid ? p : (int64_t)0));
         if (!__all_sync(0xFFFFFFFFu, mbar_wait(&tfull[acc], (uint32_t)((g_ >> 1) & 1)))) {
           *vfail = 1;
           break;
