@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
   uint8_t* sBK = vsm + (((tab_end + 1023u) & ~1023u) - raw);
   uint8_t* stages = sBK + 2048;
   uint8_t* sB = stages + C::STAGES * C::STAGE;  // the unit's code operand (swizzled)
-  __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], tfull[2], tempty[2], drain;
+  __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], tfull[4], tempty[4], drain;
   __shared__ uint16_t s_off[MAX_LEAF_TILES_VS + 1];
   __shared__ uint16_t stl[MAX_LEAF_TILES_VS];
   // staging: sqT (the queries' SFA values, value-major), s_env (64 tile
@@ -388,9 +388,11 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    // one pair of barriers per (accumulator, 128-series half): each half is
+    // read by its own four epilogue warps
+    for (int a = 0; a < 4; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], VS_EPI);
+      mbar_init(&tempty[a], VS_EPI / 2);
     }
     mbar_init(&drain, 1);
     s_fail = 0;
@@ -578,18 +580,20 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
         for (int i = 0; i < ntl; ++i) {
           const long long g_ = gi + i;
           const int s = (int)(g_ % C::STAGES), acc = (int)(g_ & 1);
-          if (g_ >= 2 && !mbar_wait(&tempty[acc], (uint32_t)(((g_ >> 1) - 1) & 1))) {
-            *vfail = 1;
-            break;
-          }
           if (!mbar_wait(&full[s], (uint32_t)((g_ / C::STAGES) & 1))) {
             *vfail = 1;
             break;
           }
-          tc_fence_after();
           const uint32_t sa = smem_u32(stages + s * C::STAGE), sk = sa + C::ATILE;
+          bool ok = true;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
+            // this half of the accumulator is free once its four warps released it
+            if (g_ >= 2 && !mbar_wait(&tempty[acc * 2 + h], (uint32_t)(((g_ >> 1) - 1) & 1))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(acc * 128 + h * 64);
 #pragma unroll
             for (int kk = 0; kk < C::KSTEPS; ++kk)
@@ -597,9 +601,13 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
             // the folded constants: the series side's K columns 8-15 repeat
             // columns 0-7 (LBO 0; the query side is zero there)
             mma_f16_n64(d, nosw_desc(sk + h * 128 * 16, 0, 128), nosw_desc(sbk, 1024, 128), 1u);
+            mma_commit(&tfull[acc * 2 + h]);
+          }
+          if (!ok) {
+            *vfail = 1;
+            break;
           }
           mma_commit(&empty[s]);
-          mma_commit(&tfull[acc]);
         }
       }
     } else {
@@ -620,7 +628,7 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
         // waits for the load before a survivor needs it (a lane past N is
         // never a survivor).
         const uint4 kx = __ldg(VK + (valid ? p : (int64_t)0));
-        if (!__all_sync(0xFFFFFFFFu, mbar_wait(&tfull[acc], (uint32_t)((g_ >> 1) & 1)))) {
+        if (!__all_sync(0xFFFFFFFFu, mbar_wait(&tfull[acc * 2 + half], (uint32_t)((g_ >> 1) & 1)))) {
           *vfail = 1;
           break;
         }
@@ -746,7 +754,7 @@ __global__ void __launch_bounds__(VS_THREADS, VsCfg<NB>::MIN_CTAS)
           }
         }
         tc_fence_before();
-        mbar_arrive(&tempty[acc]);  // the accumulator is free for the MMA warp
+        mbar_arrive(&tempty[acc * 2 + half]);  // this half of the accumulator is free for the MMA warp
       }
       // flush the unit's candidate list: one global reservation per query
       // (and one pool reservation per query that overflows its slots), then
